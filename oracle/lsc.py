@@ -1,0 +1,191 @@
+"""Oracle: local spherical convolution (Sec. 2.3 and "Extension to multiple b-values").
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+What the paper fixes (Sec. 2.3): a circular kernel made of an origin plus
+points on a circle at angular distance alpha, stored as a vector of n+1
+weights; every acquired direction's neighbourhood is *resampled* at the kernel
+points through the SH interpolant, giving an m x (n+1) matrix; the layer
+multiplies every row point-wise with the kernel vector and sums (a cross
+correlation), giving m values.  The LSC's own parameters include the output SH
+order and a Laplace-Beltrami lambda, and its example maps SH -> LSC -> SH, so
+the m values are projected back onto SH.  With several b-values, shells act as
+channels with a weight per input shell, and each output shell has its own
+kernels.
+
+Readings where the paper is silent or garbled (all also used by the library):
+
+* Kernel geometry: ``kernel_sizes`` is read as R rings of ``sectors`` points
+  each, ring r (1..R) at polar angle theta_r = r * alpha / R; point q of a
+  ring at azimuth 2 pi q / sectors; vector order [origin, ring 1 (q = 0..),
+  ring 2, ...]; K = 1 + R * sectors.  The paper's case ``[5]``, pi/5 is one
+  ring of 5.
+* Tangent frame at g: a = the coordinate axis with the smallest |g_k| (ties to
+  the lowest k), e1 = normalise(a - (a.g) g), e2 = g x e1,
+  p = cos(theta) g + sin(theta) (cos(phi) e1 + sin(phi) e2).
+* The two parameter descriptions that both read "number of output shells" are
+  taken as: ``lb_lambda`` = lambda of the LSC's output projection,
+  ``angular_distance`` = the kernel's outer radius alpha.
+* Sampled directions: output shell s is sampled on that shell's own directions
+  of the output gradient table.
+* Weights are independent per kernel point (no tying across sectors); layout
+  [C_out, S_out, C_in, S_in, K]; entries outside the shell window are unused.
+* Shell windows: 'same' (s' = s), 'adjacent' (|s - s'| <= 1), 'all'.
+* Neighbour table T3 of direction i: {j : |g_i . g_j| >= cos(alpha)} (antipodal
+  aware, i itself included, ascending j, FP64 comparison, equality inside).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .sh import SHBasisOracle, n_coef, real_sh
+
+WINDOWS = {"same": 0, "adjacent": 1, "all": -1}
+
+
+def tangent_frame(g: np.ndarray):
+    """(e1, e2) of the reading above for one unit vector g."""
+    g = np.asarray(g, np.float64)
+    k = int(np.argmin(np.abs(g)))  # argmin returns the first (lowest) index on ties
+    a = np.zeros(3)
+    a[k] = 1.0
+    e1 = a - np.dot(a, g) * g
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(g, e1)
+    return e1, e2
+
+
+def kernel_points(dirs: np.ndarray, radius: float, rings: int, sectors: int) -> np.ndarray:
+    """Kernel points p[i, k] around every direction g_i, float64 [m, 1 + rings*sectors, 3]."""
+    dirs = np.asarray(dirs, np.float64)
+    K = 1 + rings * sectors
+    out = np.empty((dirs.shape[0], K, 3))
+    for i, g in enumerate(dirs):
+        e1, e2 = tangent_frame(g)
+        out[i, 0] = g
+        for r in range(1, rings + 1):
+            th = r * radius / rings
+            for q in range(sectors):
+                ph = 2.0 * np.pi * q / sectors
+                out[i, 1 + (r - 1) * sectors + q] = (np.cos(th) * g
+                                                     + np.sin(th) * (np.cos(ph) * e1 + np.sin(ph) * e2))
+    return out
+
+
+def kernel_row_index(m_per_shell, K: int):
+    """Table T4: row of kernel point (s, i, k) in the stacked kernel-point list,
+    row = (dir_off[s] + i) * K + k.  Returned as an int64 array [sum m_s, K]."""
+    total = int(np.sum(m_per_shell))
+    return np.arange(total * K, dtype=np.int64).reshape(total, K)
+
+
+def shell_window(s_out: int, s_in: int, mode: str) -> np.ndarray:
+    """Table T2: boolean [S_out, S_in], True where input shell s' feeds output shell s."""
+    if mode == "all":
+        return np.ones((s_out, s_in), bool)
+    if s_out != s_in:
+        raise ValueError("'same' and 'adjacent' windows need as many input as output shells")
+    s = np.arange(s_out)
+    d = np.abs(s[:, None] - s[None, :])
+    return d == 0 if mode == "same" else d <= 1
+
+
+def neighbour_csr(dirs: np.ndarray, radius: float):
+    """Table T3: antipodal-aware neighbours within ``radius``: (indptr, indices) int64."""
+    g = np.asarray(dirs, np.float64)
+    c = np.cos(radius)
+    indptr = [0]
+    idx = []
+    for i in range(g.shape[0]):
+        for j in range(g.shape[0]):
+            if abs(float(np.dot(g[i], g[j]))) >= c:
+                idx.append(j)
+        indptr.append(len(idx))
+    return np.array(indptr, np.int64), np.array(idx, np.int64)
+
+
+def mask_to_index(mask: np.ndarray) -> np.ndarray:
+    """Table T5: ascending C-order linear indices of the True voxels of a volume whose
+    last axis is fastest (the paper's subjects x dirs x H x W x D tensor, Sec. 2.1)."""
+    return np.flatnonzero(np.asarray(mask, bool).reshape(-1)).astype(np.int64)
+
+
+class LSCOracle:
+    """One LSC layer: input SH of order ``order_in`` on ``shells_in`` shells, output SH on
+    the shells of ``out_basis`` (its directions are the sampled directions, its order and
+    lambda those of the output projection)."""
+
+    def __init__(self, out_basis: SHBasisOracle, order_in: int, shells_in: int, radius: float,
+                 rings: int, sectors: int, window: str = "same"):
+        self.ob = out_basis
+        self.order_in = order_in
+        self.n_in = n_coef(order_in)
+        self.n_out = out_basis.n_coef
+        self.s_in = shells_in
+        self.s_out = out_basis.n_shells
+        self.radius = float(radius)
+        self.rings, self.sectors = rings, sectors
+        self.K = 1 + rings * sectors
+        self.win = shell_window(self.s_out, self.s_in, window)
+        self.dirs = [out_basis.dirs[r] for r in out_basis.rows]
+        self.kpts = [kernel_points(d, radius, rings, sectors) for d in self.dirs]
+        # basis of the input order at every kernel point: BK[s][i, k, j]
+        self.BK = [real_sh(order_in, p.reshape(-1, 3)).reshape(p.shape[0], self.K, self.n_in)
+                   for p in self.kpts]
+        self.Pout = out_basis.P
+
+    # ---- literal form: resample -> point-wise product -> projection (Sec. 2.3) ----
+    def resample(self, c_in: np.ndarray, s: int) -> np.ndarray:
+        """U[v, ci, s', i, k]: input shell s' interpolant at output-shell-s kernel points."""
+        return np.einsum("ikj,vcpj->vcpik", self.BK[s], c_in)
+
+    def direction_space(self, c_in, w, b) -> list:
+        """y[s][v, co, i] = sum_{ci, s' in win(s), k} w[co,s,ci,s',k] U[v,ci,s',i,k] + b[co,s]."""
+        ys = []
+        for s in range(self.s_out):
+            U = self.resample(c_in, s)
+            mask = self.win[s].astype(np.float64)
+            ws = w[:, s] * mask[None, None, :, None]  # [co, ci, s', k]
+            ys.append(np.einsum("acpk,vcpik->vai", ws, U) + b[None, :, s, None])
+        return ys
+
+    def forward(self, c_in, w, b) -> np.ndarray:
+        """c_out[v, co, s, :] = P_out,s y[s][v, co, :]."""
+        ys = self.direction_space(c_in, w, b)
+        return np.stack([y @ P.T for y, P in zip(ys, self.Pout)], axis=2)
+
+    # ---- algebraic collapse (linearity), an independent second route ----
+    def collapse_mats(self):
+        """M[s][k] = P_out,s B^K_{s,k} ([N_out, N_in]) and q[s] = P_out,s 1."""
+        M = [np.einsum("ai,ikj->kaj", P, BK) for P, BK in zip(self.Pout, self.BK)]
+        q = [P.sum(axis=1) for P in self.Pout]
+        return M, q
+
+    def forward_collapsed(self, c_in, w, b) -> np.ndarray:
+        M, q = self.collapse_mats()
+        V, Co = c_in.shape[0], w.shape[0]
+        out = np.zeros((V, Co, self.s_out, self.n_out))
+        for s in range(self.s_out):
+            for p in range(self.s_in):
+                if not self.win[s, p]:
+                    continue
+                Weff = np.einsum("ack,kxy->axcy", w[:, s, :, p, :], M[s])  # [co, a, ci, b]
+                out[:, :, s, :] += np.einsum("axcy,vcy->vax", Weff, c_in[:, :, p, :])
+            out[:, :, s, :] += b[None, :, s, None] * q[s][None, None, :]
+        return out
+
+    # ---- analytic gradients of the literal form ----
+    def backward(self, c_in, w, d_out):
+        """(dc_in, dw, db) for upstream gradient d_out [V, Co, S_out, N_out]."""
+        dc_in = np.zeros_like(c_in)
+        dw = np.zeros_like(w)
+        db = np.zeros((w.shape[0], self.s_out))
+        for s in range(self.s_out):
+            dy = d_out[:, :, s, :] @ self.Pout[s]  # [v, co, i]
+            db[:, s] = dy.sum(axis=(0, 2))
+            U = self.resample(c_in, s)  # [v, ci, s', i, k]
+            mask = self.win[s].astype(np.float64)
+            dw[:, s] = np.einsum("vai,vcpik->acpk", dy, U) * mask[None, None, :, None]
+            dU = np.einsum("acpk,vai->vcpik", w[:, s] * mask[None, None, :, None], dy)
+            dc_in += np.einsum("ikj,vcpik->vcpj", self.BK[s], dU)
+        return dc_in, dw, db
