@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Benchmark: voxels/s of Signal2SH -> LSC -> SH2Signal forward + backward.
+
+Workload (one step = one pass of the whole path over one batch): 65,536 voxels,
+3 shells x 90 directions (b = 1000/2000/3000), SH order 8 (3 x 45 coefficients,
+lambda 0.006), LSC 16 -> 64 channels mixing adjacent shells, radius 25 deg,
+4 rings x 12 sectors (K = 49); BF16 activations on the tensor cores with FP32
+accumulation and FP32 master weights.  The FP32 path is measured beside it.
+Inputs are seeded synthetic fibre-model signals (stick + zeppelin, SNR 20) and
+Gaussian upstream gradients, larger than L2 (no flush needed).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 oracle
+(the reference arm: plain numpy on the host cores) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "voxels/s, Signal2SH->LSC->SH2Signal fwd+bwd, BF16 vs FP32 at stated error vs FP64 oracle"
+UNIT = "voxels/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-vox", type=int, default=65536)
+    ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip fp32 / e2e / cpu legs (profiling runs)")
+    return ap.parse_args()
+
+
+def workload_config(n_vox):
+    from paper_1808_01517_gb300.chain import ChainConfig
+    return ChainConfig(n_vox=n_vox)
+
+
+def table(cfg):
+    from paper_1808_01517_gb300 import synth
+    return synth.multishell_table(list(cfg.dirs_per_shell), list(cfg.bvals), seed=cfg.seed)
+
+
+# ---------------------------------------------------------------------------
+# FP64 oracle chain (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+class OracleChain:
+    def __init__(self, cfg, dirs, bvals):
+        from oracle import lsc as olsc
+        from oracle import sh as osh
+        self.cfg = cfg
+        self.ob = osh.SHBasisOracle(dirs, bvals, cfg.order, cfg.lam)
+        self.og = olsc.LSCOracle(self.ob, cfg.order, self.ob.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings,
+                                 cfg.sectors, cfg.window)
+
+    def step(self, sig, w, b, ds_out):
+        """sig [V, Ci, dirs], ds_out [V, Co, dirs] -> (s_out, ds_in, dw, db)."""
+        ob, og = self.ob, self.og
+        c_in = ob.signal2sh(sig)
+        s_out = ob.sh2signal(og.forward(c_in, w, b))
+        dc_in, dw, db = og.backward(c_in, w, ob.sh2signal_backward(ds_out))
+        return s_out, ob.signal2sh_backward(dc_in), dw, db
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_inputs(cfg, dirs, bvals, V, seed):
+    from paper_1808_01517_gb300 import synth
+    S = len(cfg.dirs_per_shell)
+    sig = synth.fibre_signal(dirs, bvals, V * cfg.c_in, seed=seed).astype(np.float64)
+    sig = sig.reshape(cfg.c_in, V, -1).transpose(1, 0, 2)
+    K = 1 + cfg.rings * cfg.sectors
+    w = synth.gaussian((cfg.c_out, S, cfg.c_in, S, K), 0.1, seed=seed)
+    b = synth.gaussian((cfg.c_out, S), 0.1, seed=seed + 1)
+    ds = synth.gaussian((V, cfg.c_out, dirs.shape[0]), 0.1, seed=seed, tag="grads")
+    return sig, w, b, ds
+
+
+def time_oracle(cfg, dirs, bvals, budget_s, chunk=64, max_vox=4096):
+    """Voxels/s of the oracle chain on a bounded sample (chunks of `chunk` voxels until
+    `budget_s` seconds of work or `max_vox` voxels)."""
+    oc = OracleChain(cfg, dirs, bvals)
+    done, t_work = 0, 0.0
+    while t_work < budget_s and done < max_vox:
+        sig, w, b, ds = oracle_inputs(cfg, dirs, bvals, chunk, seed=cfg.seed + done)
+        t0 = time.perf_counter()
+        oc.step(sig, w, b, ds)
+        t_work += time.perf_counter() - t0
+        done += chunk
+    return done / t_work, done, t_work
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cfg = workload_config(args.n_vox)
+    dirs, bvals = table(cfg)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps, warm = args.steps, args.warmup
+        oc = OracleChain(cfg, dirs, bvals)
+        chunk = 64
+        sig, w, b, ds = oracle_inputs(cfg, dirs, bvals, chunk, seed=cfg.seed)
+        for _ in range(warm):
+            oc.step(sig, w, b, ds)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            oc.step(sig, w, b, ds)
+        dt = time.perf_counter() - t0
+        v = chunk * steps / dt
+        cores = blas_threads()
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": steps,
+                "warmup": warm, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": cfg.name(), "sample_voxels_per_step": chunk},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"{chunk} voxels per step of the same workload, FP64 numpy oracle"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    from paper_1808_01517_gb300 import _lib as L
+    from paper_1808_01517_gb300 import synth
+    from paper_1808_01517_gb300.chain import Chain
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    V = cfg.n_vox
+    # ---- inputs (device-drawn fibre signals, per-rank seed) ----
+    def make_inputs(dtype):
+        S = len(cfg.dirs_per_shell)
+        sig = synth.fibre_signal_torch(dirs, bvals, cfg.c_in * V, seed=cfg.seed + rank)  # [270, Ci*V]
+        # library row order (s, c, i): per shell, channel-major blocks of that shell's directions
+        s_rows = []
+        off = 0
+        for m in cfg.dirs_per_shell:
+            blk = sig[off:off + m].reshape(m, cfg.c_in, V).permute(1, 0, 2).reshape(cfg.c_in * m, V)
+            s_rows.append(blk)
+            off += m
+        s_in = torch.cat(s_rows, 0).to(dtype)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(cfg.seed * 31 + rank)
+        ds_out = (0.1 * torch.randn((cfg.c_out * dirs.shape[0], V), generator=gen, device="cuda")).to(dtype)
+        K = 1 + cfg.rings * cfg.sectors
+        w = torch.from_numpy(synth.gaussian((cfg.c_out, S, cfg.c_in, S, K), 0.1, seed=cfg.seed)).float().cuda()
+        b = torch.from_numpy(synth.gaussian((cfg.c_out, S), 0.1, seed=cfg.seed + 1)).float().cuda()
+        return s_in, ds_out, w, b
+
+    ch = Chain(cfg, dirs, bvals, torch.bfloat16)
+    s_in, ds_out, w, b = make_inputs(torch.bfloat16)
+    ch.set_inputs(s_in, ds_out, w, b)
+    del s_in, ds_out
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        ch.step()
+    barrier()
+
+    # ---- timed region ----
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = L.get().delimit_kernel_launches()
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_stop = torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    for k in range(K):
+        ch.step(events=ev[k])
+    t_stop.record()
+    barrier()
+    launches = L.get().delimit_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = t_start.elapsed_time(t_stop) / K
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * V / (ms * 1e-3)
+    per_call = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]))
+                for i, name in enumerate(Chain.CALLS)}
+    st, code = L.device_error(torch.cuda.current_stream().cuda_stream)
+    if st != L.OK:
+        raise RuntimeError(f"device error word set: {code:#x}")
+
+    import json as _json
+    peaks = {}
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            peaks = _json.load(f)
+        peak_src = "measured"
+    except Exception:
+        peak_src = "fallback"
+    tf_sust = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    fl, by = ch.flops(), ch.bytes()
+    dom = max(per_call, key=per_call.get)
+    per_call_roof = {n: {"ms": per_call[n], "tflops": fl[n] / (per_call[n] * 1e-3) / 1e12,
+                         "gbs": by[n] / (per_call[n] * 1e-3) / 1e9} for n in per_call}
+    ach = per_call_roof[dom]["tflops"]
+    roofline = {"bound": "tensor", "achieved": ach, "peak": tf_sust, "unit": "TFLOP/s", "frac": ach / tf_sust,
+                "traffic": None, "kernel": f"delimit_{dom}", "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "step_tflops": sum(fl.values()) / (ms * 1e-3) / 1e12}
+    roofline["step_frac"] = roofline["step_tflops"] / tf_sust
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        # ---- accuracy on sampled voxels vs the FP64 oracle ----
+        idx = synth.voxel_subset(V, 32, seed=cfg.seed + 99)
+        extras["err_vs_oracle_bf16"] = sampled_errors(ch, cfg, dirs, bvals, idx)
+        # ---- FP32 path (CUDA cores, accurate) ----
+        ch32 = Chain(cfg, dirs, bvals, torch.float32)
+        ch32.s_in.copy_(ch.s_in.float())
+        ch32.ds_out.copy_(ch.ds_out.float())
+        ch32.w.copy_(ch.w)
+        ch32.b.copy_(ch.b)
+        ch32.step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.fp32_steps):
+            ch32.step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1) / args.fp32_steps
+        extras["fp32"] = {"value": V / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32, "steps": args.fp32_steps,
+                          "err_vs_oracle": sampled_errors(ch32, cfg, dirs, bvals, idx)}
+        del ch32
+        torch.cuda.empty_cache()
+        # ---- end to end through host buffers ----
+        extras["e2e"] = run_e2e(ch, args.e2e_steps)
+        # ---- oracle on the host cores ----
+        vps, nv, tw = time_oracle(cfg, dirs, bvals, args.cpu_seconds)
+        extras["cpu_baseline"] = {"value": vps, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                                  "sample": f"{nv} voxels of the same workload in 64-voxel chunks, "
+                                            f"{tw:.1f} s of FP64 numpy oracle work"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": cfg.name(), "n_vox": V, "shells": list(cfg.dirs_per_shell),
+                           "sh_order": cfg.order, "c_in": cfg.c_in, "c_out": cfg.c_out, "kernel_points": ch.geom.K,
+                           "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "per_call": per_call_roof, "clocks": clk, "gpu_launches": int(launches)}
+        line.update({k: v for k, v in extras.items() if k in ("e2e", "cpu_baseline")})
+        line["fp32"] = extras.get("fp32")
+        line["err_vs_oracle_bf16"] = extras.get("err_vs_oracle_bf16")
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def sampled_errors(ch, cfg, dirs, bvals, idx):
+    """Relative L2 of s_out, ds_in, db on sampled voxels against the FP64 oracle."""
+    import torch
+    ch.step()
+    torch.cuda.synchronize()
+    S, m = len(cfg.dirs_per_shell), cfg.dirs_per_shell[0]
+
+    def rows_to_vcd(rows, C):  # library signal rows -> [V, C, dirs]
+        x = rows.float().cpu().numpy().astype(np.float64)
+        out = np.empty((x.shape[1], C, S * m))
+        for s in range(S):
+            out[:, :, s * m:(s + 1) * m] = x[s * C * m:(s + 1) * C * m].reshape(C, m, -1).transpose(2, 0, 1)
+        return out
+
+    sig = rows_to_vcd(ch.s_in[:, idx], cfg.c_in)
+    dso = rows_to_vcd(ch.ds_out[:, idx], cfg.c_out)
+    oc = OracleChain(cfg, dirs, bvals)
+    s_out, ds_in, _, _ = oc.step(sig, ch.w.cpu().numpy().astype(np.float64), ch.b.cpu().numpy().astype(np.float64),
+                                 dso)
+    got_s = rows_to_vcd(ch.s_out[:, idx], cfg.c_out)
+    got_d = rows_to_vcd(ch.ds_in[:, idx], cfg.c_in)
+    rel = lambda a, r: float(np.linalg.norm(a - r) / np.linalg.norm(r))  # noqa: E731
+    return {"s_out": rel(got_s, s_out), "ds_in": rel(got_d, ds_in), "voxels": int(len(idx))}
+
+
+def run_e2e(ch, steps):
+    """Same step with inputs copied from pinned host memory and outputs copied back."""
+    import torch
+    s_in_h = torch.empty(ch.s_in.shape, dtype=ch.s_in.dtype, pin_memory=True)
+    ds_out_h = torch.empty(ch.ds_out.shape, dtype=ch.ds_out.dtype, pin_memory=True)
+    s_out_h = torch.empty(ch.s_out.shape, dtype=ch.s_out.dtype, pin_memory=True)
+    ds_in_h = torch.empty(ch.ds_in.shape, dtype=ch.ds_in.dtype, pin_memory=True)
+    dw_h = torch.empty(ch.dw.shape, dtype=torch.float32, pin_memory=True)
+    db_h = torch.empty(ch.db.shape, dtype=torch.float32, pin_memory=True)
+    s_in_h.copy_(ch.s_in)
+    ds_out_h.copy_(ch.ds_out)
+    h2d = s_in_h.numel() * s_in_h.element_size() + ds_out_h.numel() * ds_out_h.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in (s_out_h, ds_in_h, dw_h, db_h))
+
+    def one():
+        ch.s_in.copy_(s_in_h, non_blocking=True)
+        ch.ds_out.copy_(ds_out_h, non_blocking=True)
+        ch.step()
+        s_out_h.copy_(ch.s_out, non_blocking=True)
+        ds_in_h.copy_(ch.ds_in, non_blocking=True)
+        dw_h.copy_(ch.dw, non_blocking=True)
+        db_h.copy_(ch.db, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": ch.cfg.n_vox / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms, "steps": steps}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * delimit.h - C ABI of the GB300 (sm_103a) DELIMIT spherical-layer library.
+ *
+ * Koppers & Merhof, "DELIMIT PyTorch - An extension for Deep Learning in
+ * Diffusion Imaging" (arXiv:1808.01517).  The library implements the paper's
+ * three layers: Signal2SH and SH2Signal (Sec. 2.2) and the local spherical
+ * convolution, LSC (Sec. 2.3, including "Extension to multiple b-values").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Activations follow the paper's 5-D tensor convention (Sec. 2.1:
+ * subjects x (#shells * #directions) x H x W x D): a tensor is a row-major
+ * matrix whose ROWS are features and whose COLUMNS are voxels, voxels
+ * contiguous.  `n_vox` columns are used; consecutive rows are `ld` elements
+ * apart (ld >= n_vox).  Row order:
+ *   signal rows  (s, c, i): row = C * dir_off[s] + c * m_s + i
+ *                (shell s, channel c, direction i of shell s)
+ *   SH rows      (s, c, j): row = (s * C + c) * N + j
+ *                (N = (L+1)(L+2)/2 coefficients, j = l(l+1)/2 + m)
+ * With C = 1 this is exactly the paper's tensor for one subject.
+ * Alignment: every activation pointer must be 16-byte aligned and
+ * ld * sizeof(element) a multiple of 16 (DELIMIT_ERR_ALIGNMENT otherwise).
+ *
+ * Ownership: handles own their host FP64 tables and device copies and are
+ * immutable after creation.  Activation, weight and workspace pointers are
+ * caller-owned device memory; no compute call allocates.  Calls are
+ * asynchronous on `stream` (a cudaStream_t passed as void*; NULL is the legacy
+ * default stream).  Argument errors are returned synchronously; errors of a
+ * running kernel (a bounded device-side wait that ran out) are reported by
+ * delimit_device_error().  All entry points are thread-safe for distinct
+ * handles; delimit_last_error() is per thread.
+ *
+ * Shells: rows of a gradient table are grouped by b-value rounded to an
+ * integer, shells in ascending b, rows of a shell in input order
+ * (delimit_sh_basis_tables returns the original row of every grouped row).
+ * b <= 0 rows are rejected: the paper normalises by the b = 0 volume first
+ * (Sec. 2.2) and the caller does that.
+ */
+#ifndef DELIMIT_H
+#define DELIMIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DELIMIT_OK = 0,
+  DELIMIT_ERR_INVALID_ARG = 1,     /* bad size, order, direction, null pointer, ... */
+  DELIMIT_ERR_RANK_DEFICIENT = 2,  /* normal equations singular (e.g. lambda = 0, m < N) */
+  DELIMIT_ERR_UNSUPPORTED = 3,     /* valid request outside what this build implements */
+  DELIMIT_ERR_ALIGNMENT = 4,       /* pointer or row stride violates the 16-byte rule */
+  DELIMIT_ERR_CUDA = 5,            /* a CUDA runtime call failed (see delimit_last_error) */
+  DELIMIT_ERR_DEVICE_TIMEOUT = 6,  /* a bounded device-side wait ran out */
+  DELIMIT_ERR_OOM = 7,             /* device table allocation failed at create time */
+  DELIMIT_ERR_WORKSPACE = 8        /* workspace smaller than *_workspace_size() */
+} delimit_status;
+
+typedef enum {
+  DELIMIT_F32 = 0,  /* float32 activations, FP32 arithmetic (the accurate path) */
+  DELIMIT_BF16 = 1  /* bfloat16 activations, tensor cores, FP32 accumulation */
+} delimit_dtype;
+
+/* create flags */
+#define DELIMIT_HOST_ONLY 1u /* build host FP64 tables only (no device copies, no GPU needed) */
+
+/* LSC shell windows (which input shells s' feed output shell s) */
+#define DELIMIT_WINDOW_SAME 0      /* s' = s (needs as many input as output shells) */
+#define DELIMIT_WINDOW_ADJACENT 1  /* |s - s'| <= 1 (same) */
+#define DELIMIT_WINDOW_ALL (-1)    /* every input shell: the paper's shells-as-channels form */
+
+typedef struct delimit_sh_basis delimit_sh_basis;
+typedef struct delimit_lsc_geometry delimit_lsc_geometry;
+
+/* ------------------------------------------------------------------------ */
+/* Spherical-harmonic basis of one gradient table (Sec. 2.2, Signal2SH      */
+/* parameters sh_order, gradients, lb_lambda).                               */
+/* ------------------------------------------------------------------------ */
+
+/* Builds, per shell s, the real even-order SH basis B_s[i, j] = Y_j(g_i)
+ * (Descoteaux 2007, cited in Sec. 1) and the Laplace-Beltrami regularised
+ * pseudo-inverse P_s = (B_s^T B_s + lambda diag(l^2 (l+1)^2))^-1 B_s^T in FP64
+ * (Cholesky), then uploads FP32/BF16 copies unless DELIMIT_HOST_ONLY.
+ *   dirs   host, n_dirs x 3 doubles, each of norm 1 +- 1e-6
+ *   bvals  host, n_dirs doubles, every one > 0
+ *   order  even, 0..16;  lambda >= 0
+ * Errors: INVALID_ARG (odd/negative order, bad norm, b <= 0, lambda < 0,
+ * null pointer), RANK_DEFICIENT (a shell's normal matrix is not positive
+ * definite), OOM / CUDA on device upload.  *out is NULL on error. */
+delimit_status delimit_sh_basis_create(const double* dirs, const double* bvals, int n_dirs, int order,
+                                       double lambda, unsigned flags, delimit_sh_basis** out);
+delimit_status delimit_sh_basis_destroy(delimit_sh_basis* basis);
+
+/* Sizes: number of shells, coefficients N, total directions. Any out pointer may be NULL. */
+delimit_status delimit_sh_basis_info(const delimit_sh_basis* basis, int* n_shells, int* n_coef,
+                                     int* n_dirs);
+
+/* One shell: directions m_s, offset dir_off[s] of its first grouped row, its b-value. */
+delimit_status delimit_sh_basis_shell(const delimit_sh_basis* basis, int shell, int* n_dirs,
+                                      int* dir_offset, double* bval);
+
+/* Host FP64 copies of shell s: B (m_s x N, row-major), P (N x m_s, row-major) and
+ * dir_index (m_s ints: original row of each grouped row).  NULL skips an output. */
+delimit_status delimit_sh_basis_tables(const delimit_sh_basis* basis, int shell, double* B, double* P,
+                                       int* dir_index);
+
+/* Signal2SH (Sec. 2.2): sh[(s,c,:), v] = P_s sig[(s,c,:), v] for every shell s,
+ * channel c < channels and voxel v < n_vox.  in_t/out_t: F32 or BF16 each.
+ * sig: signal rows, sh: SH rows (layout above). */
+delimit_status delimit_signal2sh(const delimit_sh_basis* basis, const void* sig, void* sh, int64_t n_vox,
+                                 int channels, int64_t ld_sig, int64_t ld_sh, delimit_dtype in_t,
+                                 delimit_dtype out_t, void* stream);
+
+/* SH2Signal (Sec. 2.2): sig[(s,c,:), v] = B_s sh[(s,c,:), v] on the basis' own
+ * directions (create a basis on the "resampled" directions to evaluate there). */
+delimit_status delimit_sh2signal(const delimit_sh_basis* basis, const void* sh, void* sig, int64_t n_vox,
+                                 int channels, int64_t ld_sh, int64_t ld_sig, delimit_dtype in_t,
+                                 delimit_dtype out_t, void* stream);
+
+/* Adjoints used by back-propagation: d_sig = P_s^T d_sh and d_sh = B_s^T d_sig. */
+delimit_status delimit_signal2sh_backward(const delimit_sh_basis* basis, const void* d_sh, void* d_sig,
+                                          int64_t n_vox, int channels, int64_t ld_sh, int64_t ld_sig,
+                                          delimit_dtype in_t, delimit_dtype out_t, void* stream);
+delimit_status delimit_sh2signal_backward(const delimit_sh_basis* basis, const void* d_sig, void* d_sh,
+                                          int64_t n_vox, int channels, int64_t ld_sig, int64_t ld_sh,
+                                          delimit_dtype in_t, delimit_dtype out_t, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Local spherical convolution (Sec. 2.3; multi-shell form of Sec. 2.3.1).   */
+/* ------------------------------------------------------------------------ */
+
+/* Geometry of one LSC layer.  Output shell s is sampled on out_basis' shell-s
+ * directions ("sampled_gradients"); its output order and lambda ("sh_order_out",
+ * "lb_lambda") are out_basis'.  The input is SH of order `order_in` on
+ * `shells_in` shells.  Kernel: origin plus `rings` rings of `sectors` points,
+ * ring r = 1..rings at polar angle r * radius / rings ("angular_distance",
+ * "kernel_sizes"), K = 1 + rings * sectors points in the order
+ * [origin, ring 1 (azimuth 0, 2pi/sectors, ...), ring 2, ...], tangent frame
+ * e1 = normalise(a - (a.g) g) with a the axis of smallest |g_k| (lowest k on
+ * ties), e2 = g x e1.  Built in FP64: kernel points, the input basis at every
+ * kernel point, M_{s,k} = P_out,s B^K_{s,k} (N_out x N_in), q_s = P_out,s 1,
+ * the window table and the neighbour table {j : |g_i.g_j| >= cos(radius)}.
+ * Errors: INVALID_ARG (radius outside (0, pi/2], rings/sectors < 1, window not
+ * matching the shell counts, bad order), OOM/CUDA on upload. */
+delimit_status delimit_lsc_geometry_create(const delimit_sh_basis* out_basis, int order_in, int shells_in,
+                                           double radius, int rings, int sectors, int window,
+                                           unsigned flags, delimit_lsc_geometry** out);
+delimit_status delimit_lsc_geometry_destroy(delimit_lsc_geometry* geom);
+
+/* Sizes: kernel points K, coefficients in/out, shells in/out, neighbour-table
+ * entries summed over output shells.  Any out pointer may be NULL. */
+delimit_status delimit_lsc_geometry_info(const delimit_lsc_geometry* geom, int* K, int* n_coef_in,
+                                         int* n_coef_out, int* shells_in, int* shells_out,
+                                         int64_t* n_neighbours);
+
+/* Host copies of output shell s's tables; NULL skips an output.
+ *   kpts       m_s x K x 3 doubles (kernel points)
+ *   M          K x N_out x N_in doubles (M_{s,k})
+ *   q          N_out doubles
+ *   nb_indptr  m_s + 1 int64, nb_indices nb_indptr[m_s] int64 (ascending)
+ *   row_index  m_s x K int64: row (dir_off[s] + i) * K + k of kernel point (i, k)
+ *   window     shells_in bytes: 1 where input shell s' feeds output shell s */
+delimit_status delimit_lsc_geometry_tables(const delimit_lsc_geometry* geom, int shell, double* kpts,
+                                           double* M, double* q, int64_t* nb_indptr, int64_t* nb_indices,
+                                           int64_t* row_index, unsigned char* window);
+
+/* Device workspace bytes needed by delimit_lsc_forward (backward = 0) or
+ * delimit_lsc_backward (backward = 1) for these sizes; 0 on invalid input. */
+size_t delimit_lsc_workspace_size(const delimit_lsc_geometry* geom, int64_t n_vox, int c_in, int c_out,
+                                  delimit_dtype act_t, int backward);
+
+/* LSC forward (Sec. 2.3): for every voxel, resample each input shell's SH
+ * interpolant at the kernel points of every output-shell direction, take the
+ * point-wise product with the kernel weights summed over kernel points, input
+ * channels and windowed input shells, add the bias, and project onto SH of
+ * the output order.  Computed through the exact linear collapse
+ * sh_out[(s,co,:)] = sum_{ci, s' in win(s)} (sum_k w[co,s,ci,s',k] M_{s,k}) sh_in[(s',ci,:)]
+ *                    + b[co,s] q_s.
+ *   sh_in   device, SH rows (S_in x c_in x N_in) x n_vox, ld_in
+ *   w       device float32 [c_out, S_out, c_in, S_in, K] (entries outside the window unused)
+ *   b       device float32 [c_out, S_out], or NULL for no bias
+ *   sh_out  device, SH rows (S_out x c_out x N_out) x n_vox, ld_out
+ *   act_t   dtype of sh_in and sh_out
+ *   workspace >= delimit_lsc_workspace_size(..., 0) bytes, 256-byte aligned. */
+delimit_status delimit_lsc_forward(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
+                                   const float* b, void* sh_out, int64_t n_vox, int c_in, int c_out,
+                                   int64_t ld_in, int64_t ld_out, delimit_dtype act_t, void* workspace,
+                                   size_t ws_bytes, void* stream);
+
+/* LSC backward for upstream gradient d_out (SH rows of the output):
+ *   d_in  = adjoint of the forward in sh_in (same layout as sh_in), or NULL
+ *   dw    = float32 [c_out, S_out, c_in, S_in, K] (zero outside the window), or NULL
+ *   db    = float32 [c_out, S_out], or NULL
+ * All outputs are overwritten (not accumulated).  Reductions over voxels are
+ * deterministic (fixed split and order). */
+delimit_status delimit_lsc_backward(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
+                                    const void* d_out, void* d_in, float* dw, float* db, int64_t n_vox,
+                                    int c_in, int c_out, int64_t ld_in, int64_t ld_out, delimit_dtype act_t,
+                                    void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Errors and version                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Synchronises `stream`, then reads and clears the device error word that
+ * bounded device-side waits set when they run out.  *code receives the raw
+ * word (0 = none).  Returns DEVICE_TIMEOUT if it was set, CUDA if the
+ * synchronisation failed, OK otherwise. */
+delimit_status delimit_device_error(void* stream, int* code);
+
+/* Process-wide switch, default 1: BF16 steps run on the tcgen05 tensor-core
+ * kernels where their shape rules allow, else on the CUDA-core kernels.  0
+ * forces the CUDA-core kernels (same results within BF16 rounding; used to
+ * cross-check the two).  Has no counterpart in the paper. */
+delimit_status delimit_set_tensor_cores(int enable);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (host-side count, for instrumentation).  No counterpart in the paper. */
+uint64_t delimit_kernel_launches(void);
+
+const char* delimit_status_string(delimit_status status);
+const char* delimit_last_error(void); /* detail of the last failure on this thread */
+int delimit_version(void);            /* major * 10000 + minor * 100 + patch */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DELIMIT_H */

@@ -137,7 +137,7 @@ class LSCOracle:
     # ---- literal form: resample -> point-wise product -> projection (Sec. 2.3) ----
     def resample(self, c_in: np.ndarray, s: int) -> np.ndarray:
         """U[v, ci, s', i, k]: input shell s' interpolant at output-shell-s kernel points."""
-        return np.einsum("ikj,vcpj->vcpik", self.BK[s], c_in)
+        return np.einsum("ikj,vcpj->vcpik", self.BK[s], c_in, optimize=True)
 
     def direction_space(self, c_in, w, b) -> list:
         """y[s][v, co, i] = sum_{ci, s' in win(s), k} w[co,s,ci,s',k] U[v,ci,s',i,k] + b[co,s]."""
@@ -146,7 +146,7 @@ class LSCOracle:
             U = self.resample(c_in, s)
             mask = self.win[s].astype(np.float64)
             ws = w[:, s] * mask[None, None, :, None]  # [co, ci, s', k]
-            ys.append(np.einsum("acpk,vcpik->vai", ws, U) + b[None, :, s, None])
+            ys.append(np.einsum("acpk,vcpik->vai", ws, U, optimize=True) + b[None, :, s, None])
         return ys
 
     def forward(self, c_in, w, b) -> np.ndarray:
@@ -185,7 +185,7 @@ class LSCOracle:
             db[:, s] = dy.sum(axis=(0, 2))
             U = self.resample(c_in, s)  # [v, ci, s', i, k]
             mask = self.win[s].astype(np.float64)
-            dw[:, s] = np.einsum("vai,vcpik->acpk", dy, U) * mask[None, None, :, None]
-            dU = np.einsum("acpk,vai->vcpik", w[:, s] * mask[None, None, :, None], dy)
-            dc_in += np.einsum("ikj,vcpik->vcpj", self.BK[s], dU)
+            dw[:, s] = np.einsum("vai,vcpik->acpk", dy, U, optimize=True) * mask[None, None, :, None]
+            dU = np.einsum("acpk,vai->vcpik", w[:, s] * mask[None, None, :, None], dy, optimize=True)
+            dc_in += np.einsum("ikj,vcpik->vcpj", self.BK[s], dU, optimize=True)
         return dc_in, dw, db

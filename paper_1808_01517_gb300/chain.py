@@ -1,0 +1,131 @@
+"""Signal2SH -> LSC -> SH2Signal, forward and backward, as one reusable step.
+
+This is the metric path of the layers: a multi-shell signal with C_in channels
+is fitted per shell (Signal2SH, Sec. 2.2), convolved by one LSC layer mixing
+channels and shells (Sec. 2.3), and evaluated back on the table's directions
+(SH2Signal); back-propagation runs the adjoints in reverse order and yields
+the weight and bias gradients.  Each step issues six C-ABI calls on the
+current CUDA stream with preallocated buffers and workspaces.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import layers
+
+
+@dataclass
+class ChainConfig:
+    n_vox: int = 65536
+    dirs_per_shell: tuple = (90, 90, 90)
+    bvals: tuple = (1000, 2000, 3000)
+    order: int = 8
+    lam: float = 0.006
+    c_in: int = 16
+    c_out: int = 64
+    radius_deg: float = 25.0
+    rings: int = 4
+    sectors: int = 12
+    window: str = "adjacent"
+    seed: int = 1808
+
+    def name(self) -> str:
+        return (f"S2SH-LSC-SH2S fwd+bwd V={self.n_vox} {len(self.dirs_per_shell)}x{self.dirs_per_shell[0]} dirs "
+                f"L={self.order} {self.c_in}->{self.c_out} ch {self.window} {self.radius_deg:g}deg "
+                f"{self.rings}x{self.sectors}")
+
+
+class Chain:
+    """Preallocated buffers + handles for one configuration and activation dtype."""
+
+    CALLS = ("signal2sh", "lsc_forward", "sh2signal", "sh2signal_backward", "lsc_backward", "signal2sh_backward")
+
+    def __init__(self, cfg: ChainConfig, dirs: np.ndarray, bvals: np.ndarray, dtype=torch.bfloat16, device="cuda"):
+        self.cfg, self.dtype = cfg, dtype
+        self.code = L.BF16 if dtype == torch.bfloat16 else L.F32
+        self.basis = L.SHBasis(dirs, bvals, cfg.order, cfg.lam)
+        self.geom = L.LSCGeometry(self.basis, cfg.order, self.basis.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings,
+                                  cfg.sectors, cfg.window)
+        V, S, N, nd = cfg.n_vox, self.basis.n_shells, self.basis.n_coef, self.basis.n_dirs
+        ci, co = cfg.c_in, cfg.c_out
+        self.rows = dict(s_in=ci * nd, c_in=S * ci * N, c_out=S * co * N, s_out=co * nd)
+        mk = lambda r: layers.empty_act(r, V, dtype, device)  # noqa: E731
+        self.s_in, self.c_in_buf = mk(self.rows["s_in"]), mk(self.rows["c_in"])
+        self.c_out_buf, self.s_out = mk(self.rows["c_out"]), mk(self.rows["s_out"])
+        self.ds_out, self.dc_out = mk(self.rows["s_out"]), mk(self.rows["c_out"])
+        self.dc_in, self.ds_in = mk(self.rows["c_in"]), mk(self.rows["s_in"])
+        K = self.geom.K
+        self.w = torch.zeros((co, S, ci, S, K), dtype=torch.float32, device=device)
+        self.b = torch.zeros((co, S), dtype=torch.float32, device=device)
+        self.dw = torch.empty_like(self.w)
+        self.db = torch.empty_like(self.b)
+        self.ws_f = self.geom.workspace_size(V, ci, co, self.code, False)
+        self.ws_b = self.geom.workspace_size(V, ci, co, self.code, True)
+        self._ws = torch.empty(max(self.ws_f, self.ws_b) + 256, dtype=torch.uint8, device=device)
+        self.ws = (self._ws.data_ptr() + 255) // 256 * 256
+        self.lib = L.get()
+
+    def set_inputs(self, s_in: torch.Tensor, ds_out: torch.Tensor, w: torch.Tensor, b: torch.Tensor):
+        self.s_in.copy_(s_in)
+        self.ds_out.copy_(ds_out)
+        self.w.copy_(w)
+        self.b.copy_(b)
+
+    def step(self, stream: int | None = None, events=None):
+        """One forward + backward pass.  ``events``: optional list of 7 CUDA events
+        recorded between the six calls (per-call timing on the launch stream)."""
+        lib, cfg, V = self.lib, self.cfg, self.cfg.n_vox
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        bh, gh, t, ci, co, ws = self.basis.handle, self.geom.handle, self.code, cfg.c_in, cfg.c_out, self.ws
+        rec = (lambda i: events[i].record()) if events is not None else (lambda i: None)
+        rec(0)
+        L.check(lib.delimit_signal2sh(bh, self.s_in.data_ptr(), self.c_in_buf.data_ptr(), V, ci, self.s_in.stride(0),
+                                      self.c_in_buf.stride(0), t, t, st), "delimit_signal2sh")
+        rec(1)
+        L.check(lib.delimit_lsc_forward(gh, self.c_in_buf.data_ptr(), self.w.data_ptr(), self.b.data_ptr(),
+                                        self.c_out_buf.data_ptr(), V, ci, co, self.c_in_buf.stride(0),
+                                        self.c_out_buf.stride(0), t, ws, self.ws_f, st), "delimit_lsc_forward")
+        rec(2)
+        L.check(lib.delimit_sh2signal(bh, self.c_out_buf.data_ptr(), self.s_out.data_ptr(), V, co,
+                                      self.c_out_buf.stride(0), self.s_out.stride(0), t, t, st), "delimit_sh2signal")
+        rec(3)
+        L.check(lib.delimit_sh2signal_backward(bh, self.ds_out.data_ptr(), self.dc_out.data_ptr(), V, co,
+                                               self.ds_out.stride(0), self.dc_out.stride(0), t, t, st),
+                "delimit_sh2signal_backward")
+        rec(4)
+        L.check(lib.delimit_lsc_backward(gh, self.c_in_buf.data_ptr(), self.w.data_ptr(), self.dc_out.data_ptr(),
+                                         self.dc_in.data_ptr(), self.dw.data_ptr(), self.db.data_ptr(), V, ci, co,
+                                         self.c_in_buf.stride(0), self.dc_out.stride(0), t, ws, self.ws_b, st),
+                "delimit_lsc_backward")
+        rec(5)
+        L.check(lib.delimit_signal2sh_backward(bh, self.dc_in.data_ptr(), self.ds_in.data_ptr(), V, ci,
+                                               self.dc_in.stride(0), self.ds_in.stride(0), t, t, st),
+                "delimit_signal2sh_backward")
+        rec(6)
+
+    # algorithmic work per step (used for roofline figures)
+    def flops(self) -> dict:
+        cfg, b = self.cfg, self.basis
+        V, S, N, ci, co, K = cfg.n_vox, b.n_shells, b.n_coef, cfg.c_in, cfg.c_out, self.geom.K
+        win = np.array([[abs(s - p) <= 1 if cfg.window == "adjacent" else (s == p if cfg.window == "same" else True)
+                         for p in range(S)] for s in range(S)])
+        pairs = int(win.sum())
+        lsc_gemm = 2.0 * pairs * (co * N) * (ci * N) * V  # one of fwd / dgrad / wgrad
+        build_w = 2.0 * pairs * co * ci * N * N * K
+        s2sh = 2.0 * ci * b.n_dirs * N * V
+        sh2s = 2.0 * co * b.n_dirs * N * V
+        return dict(signal2sh=s2sh, lsc_forward=lsc_gemm + build_w, sh2signal=sh2s, sh2signal_backward=sh2s,
+                    lsc_backward=2 * lsc_gemm + build_w + 2.0 * pairs * co * ci * N * N * K, signal2sh_backward=s2sh)
+
+    def bytes(self) -> dict:
+        """Compulsory HBM bytes per call (activations read + written once)."""
+        e = 2 if self.dtype == torch.bfloat16 else 4
+        V, r = self.cfg.n_vox, self.rows
+        return dict(signal2sh=e * V * (r["s_in"] + r["c_in"]), lsc_forward=e * V * (r["c_in"] + r["c_out"]),
+                    sh2signal=e * V * (r["c_out"] + r["s_out"]), sh2signal_backward=e * V * (r["s_out"] + r["c_out"]),
+                    lsc_backward=e * V * (r["c_out"] + 2 * r["c_in"]),
+                    signal2sh_backward=e * V * (r["c_in"] + r["s_in"]))

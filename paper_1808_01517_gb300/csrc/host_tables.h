@@ -1,0 +1,51 @@
+// Host-side FP64 tables of the spherical layers: SH basis, regularised
+// pseudo-inverse, LSC kernel geometry, collapse matrices and integer tables.
+// Built once per gradient table (Sec. 2.2 and 2.3 constructors); no GPU needed.
+#pragma once
+
+#include <string>
+#include <vector>
+
+namespace delimit {
+
+int sh_ncoef(int order);                         // (L+1)(L+2)/2 for even L >= 0, else -1
+void sh_eval(int order, const double g[3], double* out);  // N real even-order values at unit g
+
+struct ShellHost {
+  double bval = 0;
+  int m = 0;                 // directions in the shell
+  int dir_off = 0;           // first grouped row
+  std::vector<int> dir_index;  // original row of each grouped row
+  std::vector<double> dirs;  // m x 3
+  std::vector<double> B;     // m x N   (B[i,j] = Y_j(g_i))
+  std::vector<double> P;     // N x m   ((B^T B + lambda L)^-1 B^T)
+};
+
+struct BasisHost {
+  int order = 0, N = 0, n_dirs = 0;
+  double lambda = 0;
+  std::vector<ShellHost> shells;
+};
+
+// Returns 0 on success, 1 invalid argument, 2 rank deficient; err gets a message.
+int build_basis(const double* dirs, const double* bvals, int n, int order, double lambda, BasisHost& out,
+                std::string& err);
+
+struct LscShellHost {
+  std::vector<double> kpts;       // m x K x 3
+  std::vector<double> M;          // K x Nout x Nin
+  std::vector<double> q;          // Nout
+  std::vector<long long> nb_indptr, nb_indices;  // neighbour CSR
+  std::vector<unsigned char> window;             // S_in
+};
+
+struct LscHost {
+  int order_in = 0, n_in = 0, n_out = 0, s_in = 0, s_out = 0, K = 0, rings = 0, sectors = 0, window = 0;
+  double radius = 0;
+  std::vector<LscShellHost> shells;
+};
+
+int build_lsc(const BasisHost& out_basis, int order_in, int shells_in, double radius, int rings, int sectors,
+              int window, LscHost& out, std::string& err);
+
+}  // namespace delimit

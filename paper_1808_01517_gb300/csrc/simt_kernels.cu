@@ -1,0 +1,417 @@
+// CUDA-core kernels of the spherical layers: the FP32 accurate path of every
+// step, and the small weight-side steps of the BF16 path.
+//
+//   transform_simt   grouped Signal2SH / SH2Signal and their adjoints (Sec. 2.2)
+//   build_w          collapsed LSC operator W = sum_k w_k M_{s,k} per shell pair (Sec. 2.3)
+//   row_gemm_simt    LSC forward / input-gradient GEMM over voxels
+//   wgrad_simt       LSC weight-gradient GEMM (reduction over voxels, split, deterministic)
+//   reduce_dw        dW -> kernel-point weights dw and bias gradient db
+#include <atomic>
+
+#include "kernels.h"
+
+namespace delimit {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+__device__ __forceinline__ float ldf(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void stf(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stf(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+// ---------------------------------------------------------------------------
+// Grouped transform: one thread owns VPT voxels and OPT output rows.
+// ---------------------------------------------------------------------------
+template <typename Tin, typename Tout, int OPT, int VPT>
+__global__ void __launch_bounds__(128) transform_simt_kernel(const __grid_constant__ TransformArgs a, int ochunks) {
+  constexpr int KC = 32;
+  __shared__ __align__(16) float Ts[KC][OPT];
+  const TransformGroup& gd = a.g[blockIdx.z];
+  const int c = blockIdx.y / ochunks, oc = blockIdx.y % ochunks;
+  const int o0 = oc * OPT;
+  if (o0 >= gd.n_out) return;
+  const int no = min(OPT, gd.n_out - o0);
+  int64_t v[VPT];
+  bool ok[VPT];
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    v[k] = (int64_t)blockIdx.x * (128 * VPT) + threadIdx.x + k * 128;
+    ok[k] = v[k] < a.n_vox;
+  }
+  float acc[OPT][VPT];
+#pragma unroll
+  for (int o = 0; o < OPT; ++o)
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) acc[o][k] = 0.f;
+  const Tin* X = reinterpret_cast<const Tin*>(a.X) + (gd.x_row0 + (int64_t)c * gd.x_cstride) * a.ldx;
+  for (int j0 = 0; j0 < gd.n_in; j0 += KC) {
+    const int nj = min(KC, gd.n_in - j0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < KC * OPT; idx += 128) {
+      const int jj = idx / OPT, oo = idx % OPT;
+      Ts[jj][oo] = (jj < nj && oo < no) ? gd.T[(int64_t)(o0 + oo) * gd.n_in + j0 + jj] : 0.f;
+    }
+    __syncthreads();
+    for (int jj = 0; jj < nj; ++jj) {
+      const Tin* xr = X + (int64_t)(j0 + jj) * a.ldx;
+      float x[VPT];
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) x[k] = ok[k] ? ldf(xr + v[k]) : 0.f;
+#pragma unroll
+      for (int o = 0; o < OPT; o += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(&Ts[jj][o]);
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          acc[o][k] = fmaf(t.x, x[k], acc[o][k]);
+          acc[o + 1][k] = fmaf(t.y, x[k], acc[o + 1][k]);
+          acc[o + 2][k] = fmaf(t.z, x[k], acc[o + 2][k]);
+          acc[o + 3][k] = fmaf(t.w, x[k], acc[o + 3][k]);
+        }
+      }
+    }
+  }
+  Tout* Y = reinterpret_cast<Tout*>(a.Y) + (gd.y_row0 + (int64_t)c * gd.y_cstride + o0) * a.ldy;
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    if (o < no) {
+#pragma unroll
+      for (int k = 0; k < VPT; ++k)
+        if (ok[k]) stf(Y + (int64_t)o * a.ldy + v[k], acc[o][k]);
+    }
+  }
+}
+
+template <typename Tin, typename Tout>
+static cudaError_t transform_dispatch(const TransformArgs& a, int n_groups, int max_out, cudaStream_t st) {
+  constexpr int VPT = 2;
+  const unsigned gx = (unsigned)((a.n_vox + 128 * VPT - 1) / (128 * VPT));
+  if (max_out <= 16) {
+    const int och = 1;
+    dim3 grid(gx, a.channels * och, n_groups);
+    { transform_simt_kernel<Tin, Tout, 16, VPT><<<grid, 128, 0, st>>>(a, och); count_launch(); }
+  } else {
+    const int och = (max_out + 47) / 48;
+    dim3 grid(gx, a.channels * och, n_groups);
+    { transform_simt_kernel<Tin, Tout, 48, VPT><<<grid, 128, 0, st>>>(a, och); count_launch(); }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_out, int in_t, int out_t,
+                                  cudaStream_t st) {
+  if (a.n_vox == 0) return cudaSuccess;
+  if (in_t == 0 && out_t == 0) return transform_dispatch<float, float>(a, n_groups, max_out, st);
+  if (in_t == 1 && out_t == 0) return transform_dispatch<__nv_bfloat16, float>(a, n_groups, max_out, st);
+  if (in_t == 0 && out_t == 1) return transform_dispatch<float, __nv_bfloat16>(a, n_groups, max_out, st);
+  return transform_dispatch<__nv_bfloat16, __nv_bfloat16>(a, n_groups, max_out, st);
+}
+
+// ---------------------------------------------------------------------------
+// Collapsed LSC operator.  Block 32 x 8 threads covers a 32 x 32 tile of W;
+// W is written row-major directly, Wt through a shared-memory transpose.
+// ---------------------------------------------------------------------------
+template <typename TW>
+__global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
+                                                      const float* __restrict__ M, TW* __restrict__ W,
+                                                      TW* __restrict__ Wt) {
+  // tile over (rows_out) x (padded input columns ldW); Wt written through a transpose
+  __shared__ float tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t cp = c0 + tx;  // padded input column
+  const int sp = (int)(cp / d.in_blk);
+  const int64_t cin = cp % d.in_blk;  // (ci, b) within the shell block, or padding
+  const bool col_valid = cp < d.ldW && cin < (int64_t)d.c_in * d.n_in;
+  const int ci = (int)(cin / d.n_in), bb = (int)(cin % d.n_in);
+  const int per_out = d.c_out * d.n_out;
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r0 + i;
+    float val = 0.f;
+    if (r < d.rows_out && col_valid) {
+      const int s = (int)(r / per_out), co = (int)((r / d.n_out) % d.c_out), aa = (int)(r % d.n_out);
+      if (sp >= d.win_lo[s] && sp < d.win_hi[s]) {
+        const float* wr = w + ((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K;
+        const float* mr = M + ((int64_t)s * d.K * d.n_out + aa) * d.n_in + bb;
+        const int64_t mstride = (int64_t)d.n_out * d.n_in;
+        for (int k = 0; k < d.K; ++k) val = fmaf(__ldg(wr + k), __ldg(mr + k * mstride), val);
+      }
+    }
+    if (r < d.rows_out && cp < d.ldW) stf(W + r * d.ldW + cp, val);
+    tile[i][tx] = val;
+  }
+  __syncthreads();
+  // transpose: thread (tx, i) writes Wt[input row of column c0 + i][padded output column of row r0 + tx]
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t cc = c0 + i;
+    if (cc >= d.ldW) continue;
+    const int spp = (int)(cc / d.in_blk);
+    const int64_t cinn = cc % d.in_blk;
+    if (cinn >= (int64_t)d.c_in * d.n_in) continue;
+    const int64_t in_row = (int64_t)spp * d.c_in * d.n_in + cinn;
+    const int64_t rr = r0 + tx;
+    if (rr >= d.rows_out) continue;
+    const int s = (int)(rr / per_out);
+    const int64_t oc = (int64_t)s * d.out_blk + rr % per_out;
+    stf(Wt + in_row * d.ldWt + oc, tile[tx][i]);
+  }
+}
+
+__global__ void build_bias_kernel(const __grid_constant__ LscDims d, const float* __restrict__ b,
+                                  const float* __restrict__ q, float* __restrict__ bias_vec) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.rows_out) return;
+  const int per_out = d.c_out * d.n_out;
+  const int s = (int)(r / per_out), co = (int)((r / d.n_out) % d.c_out), aa = (int)(r % d.n_out);
+  bias_vec[r] = b ? b[co * d.s_out + s] * q[s * d.n_out + aa] : 0.f;
+}
+
+cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, const float* M, const float* q,
+                           void* W, void* Wt, float* bias_vec, int w_t, cudaStream_t st) {
+  // zero the padding of Wt (columns between shell blocks are never produced by the transpose)
+  const size_t es = w_t == 0 ? 4 : 2;
+  if (d.out_blk != (int64_t)d.c_out * d.n_out) {
+    cudaError_t e0 = cudaMemsetAsync(Wt, 0, (size_t)d.rows_in * d.ldWt * es, st);
+    if (e0 != cudaSuccess) return e0;
+  }
+  dim3 grid((unsigned)((d.ldW + 31) / 32), (unsigned)((d.rows_out + 31) / 32));
+  dim3 block(32, 8);
+  if (w_t == 0)
+    { build_w_kernel<float><<<grid, block, 0, st>>>(d, w, M, (float*)W, (float*)Wt); count_launch(); }
+  else
+    { build_w_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(d, w, M, (__nv_bfloat16*)W, (__nv_bfloat16*)Wt); count_launch(); }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !bias_vec) return e;
+  { build_bias_kernel<<<(unsigned)((d.rows_out + 255) / 256), 256, 0, st>>>(d, b, q, bias_vec); count_launch(); }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Row GEMM over voxels (LSC forward and input gradient), 128 x 128 x 8 tiles,
+// 256 threads, 8 x 8 outputs per thread.
+// ---------------------------------------------------------------------------
+template <typename TA, typename TX>
+__global__ void __launch_bounds__(256) row_gemm_simt_kernel(const __grid_constant__ RowGemmArgs p) {
+  constexpr int BM = 128, BN = 128, BK = 8;
+  __shared__ __align__(16) float As[BK][BM];
+  __shared__ __align__(16) float Xs[BK][BN];
+  const RowGemmGroup& g = p.g[blockIdx.z];
+  const int m0 = blockIdx.y * BM;
+  if (m0 >= g.R) return;
+  const int64_t v0 = (int64_t)blockIdx.x * BN;
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  const TA* At = reinterpret_cast<const TA*>(p.At);
+  const TX* X = reinterpret_cast<const TX*>(p.X);
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  const int lk = t / 32, lc = (t % 32) * 4;
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    float ra[4], rx[4];
+    const int k = k0 + lk;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + lc + i;
+      ra[i] = (k < g.K && r < g.R) ? ldf(At + (g.at_row0 + k) * p.ldat + g.at_col0 + r) : 0.f;
+      const int64_t vv = v0 + lc + i;
+      rx[i] = (k < g.K && vv < p.n_vox) ? ldf(X + (g.x_row0 + k) * p.ldx + vv) : 0.f;
+    }
+    __syncthreads();
+    *reinterpret_cast<float4*>(&As[lk][lc]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+    *reinterpret_cast<float4*>(&Xs[lk][lc]) = make_float4(rx[0], rx[1], rx[2], rx[3]);
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+      const float4 x0 = *reinterpret_cast<const float4*>(&Xs[kk][tx * 4]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&Xs[kk][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float xv8[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], xv8[j], acc[i][j]);
+    }
+  }
+  TX* Y = reinterpret_cast<TX*>(p.Y);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (r >= g.R) continue;
+    const float bias = p.bias ? p.bias[g.y_row0 + r] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t vv = v0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+      if (vv < p.n_vox) stf(Y + (g.y_row0 + r) * p.ldy + vv, acc[i][j] + bias);
+    }
+  }
+}
+
+cudaError_t launch_row_gemm_simt(const RowGemmArgs& a, int n_groups, int max_R, int act_t, cudaStream_t st) {
+  if (a.n_vox == 0) return cudaSuccess;
+  dim3 grid((unsigned)((a.n_vox + 127) / 128), (unsigned)((max_R + 127) / 128), n_groups);
+  if (act_t == 0)
+    { row_gemm_simt_kernel<float, float><<<grid, 256, 0, st>>>(a); count_launch(); }
+  else
+    { row_gemm_simt_kernel<__nv_bfloat16, __nv_bfloat16><<<grid, 256, 0, st>>>(a); count_launch(); }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Weight-gradient GEMM: reduction over a voxel split, 128 x 128 tiles, BK = 16
+// voxels.  Column N of every group is the virtual all-ones input row, so the
+// same pass yields the row sums of dY needed for the bias gradient.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) wgrad_simt_kernel(const __grid_constant__ WgradArgs p, int mtiles) {
+  constexpr int BM = 128, BN = 128, BK = 16;
+  __shared__ __align__(16) float As[BK][BM];
+  __shared__ __align__(16) float Bs[BK][BN];
+  const int gi = blockIdx.y / mtiles, mt = blockIdx.y % mtiles;
+  const WgradGroup& g = p.g[gi];
+  const int m0 = mt * BM, n0 = blockIdx.x * BN;
+  const int Ne = g.N + 1;  // + ones column
+  if (m0 >= g.M || n0 >= Ne) return;
+  const int64_t vs = (int64_t)blockIdx.z * p.vox_per_split;
+  const int64_t ve = min(p.n_vox, vs + p.vox_per_split);
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  const T* dY = reinterpret_cast<const T*>(p.dY);
+  const T* X = reinterpret_cast<const T*>(p.X);
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  const int lr = t / 2, lv = (t % 2) * 8;
+  for (int64_t k0 = vs; k0 < ve; k0 += BK) {
+    float ra[8], rb[8];
+    const int m = m0 + lr, n = n0 + lr;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t vv = k0 + lv + i;
+      const bool in = vv < ve;
+      ra[i] = (in && m < g.M) ? ldf(dY + (g.m_row0 + m) * p.lddy + vv) : 0.f;
+      rb[i] = (in && n < g.N) ? ldf(X + (g.x_row0 + n) * p.ldx + vv) : ((in && n == g.N) ? 1.f : 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      As[lv + i][lr] = ra[i];
+      Bs[lv + i][lr] = rb[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+  }
+  float* P = p.P + (int64_t)blockIdx.z * p.split_stride;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+      if (n > g.N) continue;
+      const int64_t col = (n == g.N) ? p.ones_col : g.n_col0 + n;
+      P[(g.m_row0 + m) * p.ldp + col] = acc[i][j];
+    }
+  }
+}
+
+cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int max_N, int splits, int act_t,
+                              cudaStream_t st) {
+  const int mtiles = (max_M + 127) / 128;
+  dim3 grid((unsigned)((max_N + 1 + 127) / 128), (unsigned)(mtiles * n_groups), (unsigned)splits);
+  if (act_t == 0)
+    { wgrad_simt_kernel<float><<<grid, 256, 0, st>>>(a, mtiles); count_launch(); }
+  else
+    { wgrad_simt_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(a, mtiles); count_launch(); }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// dW -> dw (kernel-point weights) and db.  One block per (ci, co, s, s').
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ LscDims d, const float* __restrict__ P,
+                                                        int64_t ldp, int64_t split_stride, int splits,
+                                                        const float* __restrict__ M, float* __restrict__ dw) {
+  extern __shared__ float blk[];
+  const int ci = blockIdx.x, co = blockIdx.y;
+  const int s = blockIdx.z / d.s_in, sp = blockIdx.z % d.s_in;
+  const int nn = d.n_out * d.n_in;
+  float* out = dw + ((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K;
+  if (sp < d.win_lo[s] || sp >= d.win_hi[s]) {
+    for (int k = threadIdx.x; k < d.K; k += blockDim.x) out[k] = 0.f;
+    return;
+  }
+  const int64_t row0 = ((int64_t)s * d.c_out + co) * d.n_out, col0 = ((int64_t)sp * d.c_in + ci) * d.n_in;
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int aa = idx / d.n_in, bb = idx % d.n_in;
+    float acc = 0.f;
+    for (int z = 0; z < splits; ++z) acc += P[z * split_stride + (row0 + aa) * ldp + col0 + bb];
+    blk[idx] = acc;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int k = warp; k < d.K; k += blockDim.x / 32) {
+    const float* mk = M + ((int64_t)s * d.K + k) * nn;
+    float acc = 0.f;
+    for (int idx = lane; idx < nn; idx += 32) acc = fmaf(blk[idx], __ldg(mk + idx), acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[k] = acc;
+  }
+}
+
+__global__ void reduce_db_kernel(const __grid_constant__ LscDims d, const float* __restrict__ P, int64_t ldp,
+                                 int64_t split_stride, int splits, int64_t ones_col, const float* __restrict__ q,
+                                 float* __restrict__ db) {
+  const int co = blockIdx.x, s = blockIdx.y;
+  const int64_t row0 = ((int64_t)s * d.c_out + co) * d.n_out;
+  float acc = 0.f;
+  for (int aa = threadIdx.x; aa < d.n_out; aa += 32) {
+    float r = 0.f;
+    for (int z = 0; z < splits; ++z) r += P[z * split_stride + (row0 + aa) * ldp + ones_col];
+    acc = fmaf(q[s * d.n_out + aa], r, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x == 0) db[co * d.s_out + s] = acc;
+}
+
+cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int64_t split_stride, int splits,
+                             const float* M, const float* q, float* dw, float* db, cudaStream_t st) {
+  if (dw) {
+    dim3 grid(d.c_in, d.c_out, d.s_out * d.s_in);
+    const size_t smem = sizeof(float) * d.n_out * d.n_in;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(reduce_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    { reduce_dw_kernel<<<grid, 256, smem, st>>>(d, P, ldp, split_stride, splits, M, dw); count_launch(); }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (db) {
+    { reduce_db_kernel<<<dim3(d.c_out, d.s_out), 32, 0, st>>>(d, P, ldp, split_stride, splits, d.rows_in, q, db); count_launch(); }
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+}  // namespace delimit

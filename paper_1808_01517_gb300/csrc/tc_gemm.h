@@ -1,0 +1,49 @@
+// Tensor-core (tcgen05 + TMA, sm_103a) paths of the BF16 layers.
+#pragma once
+
+#include <string>
+
+#include "host_tables.h"
+#include "kernels.h"
+
+namespace delimit {
+
+// BF16 operand images of one basis' per-shell transform matrices, laid out as
+// the tensor-core B operand (K-major, no swizzle), plus launch metadata.
+struct TcBasisTables {
+  void* d_mem = nullptr;
+  int n_shells = 0, N = 0;
+  // per shell and per transform kind: byte offset of the image in d_mem, padded sizes
+  size_t off[kMaxGroups][4] = {};
+  int n_in[kMaxGroups][4] = {}, n_out[kMaxGroups][4] = {}, kpad[kMaxGroups][4] = {}, npad[kMaxGroups][4] = {};
+  int m[kMaxGroups] = {}, dir_off[kMaxGroups] = {};
+  bool ok = false;
+};
+
+cudaError_t tc_basis_tables_create(const BasisHost& h, TcBasisTables& t, std::string& err);
+void tc_basis_tables_destroy(TcBasisTables& t);
+
+// kind: 0 Signal2SH, 1 SH2Signal, 2 Signal2SH adjoint, 3 SH2Signal adjoint (BF16 input)
+bool tc_transform_supported(const TcBasisTables& t, int kind, int64_t ldx, int64_t ldy, int out_t);
+cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X, void* Y, int64_t n_vox, int C,
+                                int64_t ldx, int64_t ldy, int out_t, int* err_word, cudaStream_t st);
+
+// LSC GEMMs (BF16 activations, FP32 accumulation in TMEM)
+bool tc_gemm_supported(const LscDims& d, int64_t n_vox, int64_t ld_in, int64_t ld_out);
+// Y[(s,co,a), v] = sum_{k in win(s)} Wt[k][s*out_blk + (co,a)] X[k, v] + bias[(s,co,a)]
+cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* Wt, const float* bias, void* Y,
+                           int64_t n_vox, int64_t ldx, int64_t ldy, int* err_word, cudaStream_t st);
+// dX[(s',ci,b), v] = sum_{k in rwin(s')} W[k][s'*in_blk + (ci,b)] dY[k, v]
+cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* dX, int64_t n_vox, int64_t lddy,
+                         int64_t lddx, int* err_word, cudaStream_t st);
+// P[split][(s,co,a)][(s',ci,b)] = sum_{v in split} dY[(s,co,a), v] X[(s',ci,b), v] for s' in win(s),
+// P[split][(s,co,a)][rows_in] = sum_{v in split} dY[(s,co,a), v]
+cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float* P, int64_t ldp, int64_t split_stride,
+                         int splits, int64_t vox_per_split, int64_t n_vox, int64_t lddy, int64_t ldx, int* err_word,
+                         cudaStream_t st);
+
+// process-wide switch (default on): when off every BF16 step runs on the CUDA-core kernels
+void tc_set_enabled(bool on);
+bool tc_enabled();
+
+}  // namespace delimit

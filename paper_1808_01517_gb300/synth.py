@@ -162,3 +162,33 @@ def ellipsoid_mask(shape=(145, 174, 145), target_voxels: int = 900_000, seed: in
     # choose the level set that holds target_voxels voxels
     thr = np.partition(q.ravel(), target_voxels - 1)[target_voxels - 1]
     return q <= thr
+
+
+def fibre_signal_torch(dirs, bvals, n_vox: int, *, seed: int = BASE_SEED, sub: int = 0, max_fibres: int = 2,
+                       snr=20.0, device="cuda", dtype=None):
+    """The same stick + zeppelin + Rician model as :func:`fibre_signal`, drawn on the
+    device with a seeded torch generator (for workloads too large to draw on the host).
+    Returns [n_dirs, n_vox] (feature rows x voxel columns), float32 unless ``dtype``."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1000003 + int(sub) * 7919 + _TAGS["fibres"])
+    g = torch.as_tensor(np.asarray(dirs, np.float64), dtype=torch.float32, device=device)
+    b = torch.as_tensor(np.asarray(bvals, np.float64), dtype=torch.float32, device=device)
+    nf = torch.randint(1, max_fibres + 1, (n_vox,), generator=gen, device=device)
+    u = torch.randn((max_fibres, n_vox, 3), generator=gen, device=device)
+    u = u / u.norm(dim=2, keepdim=True)
+    e = -torch.log(torch.rand((max_fibres, n_vox), generator=gen, device=device).clamp_min(1e-12))
+    e = torch.where(torch.arange(max_fibres, device=device)[:, None] < nf[None, :], e, torch.zeros_like(e))
+    w = e / e.sum(0, keepdim=True)
+    nu = 0.5 + 0.3 * torch.rand((max_fibres, n_vox), generator=gen, device=device)
+    s = torch.zeros((g.shape[0], n_vox), device=device)
+    for f in range(max_fibres):
+        cos2 = (g @ u[f].T) ** 2  # [dirs, vox]
+        stick = torch.exp(-b[:, None] * D_PAR * cos2)
+        zep = torch.exp(-b[:, None] * (D_PERP + (D_PAR - D_PERP) * cos2))
+        s += w[f][None, :] * (nu[f][None, :] * stick + (1 - nu[f][None, :]) * zep)
+    sigma = 1.0 / float(snr)
+    n1 = torch.randn(s.shape, generator=gen, device=device)
+    n2 = torch.randn(s.shape, generator=gen, device=device)
+    out = torch.sqrt((s + sigma * n1) ** 2 + (sigma * n2) ** 2)
+    return out if dtype is None else out.to(dtype)

@@ -1,0 +1,141 @@
+"""The C-ABI library without a GPU: exports, host FP64 tables vs the oracle, argument errors.
+
+The library builds its tables with its own code (normalised Legendre
+recurrence, Chebyshev azimuth recurrence, its own Cholesky); here they are
+compared with the oracle's independent numpy computation.  Integer tables are
+compared bit-exactly.
+"""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lsc as olsc
+from oracle import sh as osh
+from paper_1808_01517_gb300 import _lib as L
+from paper_1808_01517_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(delimit_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = L.get()
+    names = header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding declares argtypes for every one of them
+    assert names <= set(L.SIGNATURES), names - set(L.SIGNATURES)
+    assert lib.delimit_version() >= 100
+    assert lib.delimit_status_string(L.ERR_RANK_DEFICIENT) == b"rank deficient"
+
+
+@pytest.fixture(scope="module")
+def table3():
+    dirs, bvals = synth.multishell_table([90, 90, 90], [1000, 2000, 3000], seed=1808)
+    return dirs, bvals
+
+
+def test_basis_tables_match_oracle(table3):
+    dirs, bvals = table3
+    for order, lam in ((8, 0.006), (4, 0.06), (8, 0.0), (12, 0.006)):
+        lb = L.SHBasis(dirs, bvals, order, lam, host_only=True)
+        ob = osh.SHBasisOracle(dirs, bvals, order, lam)
+        assert lb.n_shells == 3 and lb.m == [90, 90, 90] and lb.dir_off == [0, 90, 180]
+        for s in range(3):
+            B, P, idx = lb.tables(s)
+            np.testing.assert_array_equal(idx, ob.rows[s])
+            np.testing.assert_allclose(B, ob.B[s], rtol=0, atol=1e-12)
+            scale = np.abs(ob.P[s]).max()
+            np.testing.assert_allclose(P, ob.P[s], rtol=0, atol=1e-12 * max(1.0, scale))
+
+
+def test_shell_grouping_order_and_dir_index():
+    dirs, bvals = synth.multishell_table([20, 30], [3000, 1000], seed=3)
+    lb = L.SHBasis(dirs, bvals, 4, 0.006, host_only=True)
+    assert lb.bval == [1000.0, 3000.0] and lb.m == [30, 20] and lb.dir_off == [0, 30]
+    _, _, idx0 = lb.tables(0)
+    np.testing.assert_array_equal(idx0, np.arange(20, 50))
+
+
+def test_basis_argument_errors():
+    g = synth.hemisphere_directions(30, seed=4)
+    b = np.full(30, 1000.0)
+    for args, status in (((g, b, 3, 0.0), L.ERR_INVALID_ARG),                      # odd order
+                         ((g * 1.01, b, 4, 0.0), L.ERR_INVALID_ARG),               # not unit
+                         ((g, np.where(np.arange(30) == 3, 0.0, b), 4, 0.0), L.ERR_INVALID_ARG),  # b = 0
+                         ((g, b, 4, -1.0), L.ERR_INVALID_ARG),                     # negative lambda
+                         ((g[:10], b[:10], 4, 0.0), L.ERR_RANK_DEFICIENT),         # 10 dirs < 15 coefs
+                         ((g, b, 18, 0.0), L.ERR_INVALID_ARG)):                    # order too high
+        with pytest.raises(L.DelimitError) as ei:
+            L.SHBasis(*args, host_only=True)
+        assert ei.value.status == status, args[2:]
+    # lambda > 0 regularises the under-determined case
+    L.SHBasis(g[:10], b[:10], 4, 0.006, host_only=True)
+
+
+def test_lsc_tables_match_oracle(table3):
+    dirs, bvals = table3
+    lb = L.SHBasis(dirs, bvals, 8, 0.006, host_only=True)
+    ob = osh.SHBasisOracle(dirs, bvals, 8, 0.006)
+    for order_in, window, R, Sec, rad in ((8, "adjacent", 4, 12, np.deg2rad(25)), (4, "same", 1, 5, np.pi / 5),
+                                          (6, "all", 3, 8, np.deg2rad(30))):
+        s_in = 3 if window != "all" else 2
+        lg = L.LSCGeometry(lb, order_in, s_in, rad, R, Sec, window, host_only=True)
+        og = olsc.LSCOracle(ob, order_in, s_in, rad, R, Sec, window)
+        M, q = og.collapse_mats()
+        assert lg.K == og.K == 1 + R * Sec
+        for s in range(3):
+            t = lg.tables(s)
+            np.testing.assert_allclose(t["kpts"], og.kpts[s], rtol=0, atol=1e-14)
+            np.testing.assert_allclose(t["M"], M[s], rtol=0, atol=1e-12)
+            np.testing.assert_allclose(t["q"], q[s], rtol=0, atol=1e-12)
+            ip, ix = olsc.neighbour_csr(og.dirs[s], rad)
+            np.testing.assert_array_equal(t["nb_indptr"], ip)
+            np.testing.assert_array_equal(t["nb_indices"], ix)
+            np.testing.assert_array_equal(t["window"], og.win[s])
+            T4 = olsc.kernel_row_index(lb.m, lg.K)
+            np.testing.assert_array_equal(t["row_index"], T4[lb.dir_off[s]:lb.dir_off[s] + lb.m[s]])
+
+
+def test_lsc_argument_errors(table3):
+    dirs, bvals = table3
+    lb = L.SHBasis(dirs, bvals, 4, 0.006, host_only=True)
+    for args in ((4, 2, 0.4, 2, 6, "adjacent"),   # adjacent needs shells_in == shells_out
+                 (4, 3, 0.0, 2, 6, "same"),       # radius 0
+                 (4, 3, 2.0, 2, 6, "same"),       # radius > pi/2
+                 (4, 3, 0.4, 0, 6, "same"),       # no rings
+                 (5, 3, 0.4, 2, 6, "same")):      # odd order
+        with pytest.raises(L.DelimitError) as ei:
+            L.LSCGeometry(lb, *args, host_only=True)
+        assert ei.value.status == L.ERR_INVALID_ARG
+
+
+def test_host_only_handles_refuse_compute(table3):
+    dirs, bvals = table3
+    lb = L.SHBasis(dirs, bvals, 4, 0.006, host_only=True)
+    st = L.get().delimit_signal2sh(lb.handle, 16, 16, 10, 1, 16, 16, L.F32, L.F32, None)
+    assert st == L.ERR_INVALID_ARG
+    assert b"HOST_ONLY" in L.get().delimit_last_error()
+
+
+def test_workspace_size_is_monotone(table3):
+    dirs, bvals = table3
+    lb = L.SHBasis(dirs, bvals, 8, 0.006, host_only=True)
+    lg = L.LSCGeometry(lb, 8, 3, np.deg2rad(25), 4, 12, "adjacent", host_only=True)
+    a = lg.workspace_size(65536, 16, 64, L.BF16, False)
+    b = lg.workspace_size(65536, 16, 64, L.BF16, True)
+    assert 0 < a < b
+    assert lg.workspace_size(65536, 0, 64, L.BF16, False) == 0
