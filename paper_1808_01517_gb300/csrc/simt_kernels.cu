@@ -109,52 +109,96 @@ cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_
 }
 
 // ---------------------------------------------------------------------------
-// Collapsed LSC operator.  Block 32 x 8 threads covers a 32 x 32 tile of W;
-// W is written row-major directly, Wt through a shared-memory transpose.
+// Collapsed LSC operator.  For every windowed shell pair (s, s') the block
+//   W[(s,co,a)][(s',ci,b)] = sum_k w[co,s,ci,s',k] M_s[k][a][b]
+// is a product of a [c_out*c_in x K] and a [K x n_out*n_in] matrix; blocks
+// of 32 channel pairs x 128 (a,b) entries keep both factors in shared memory.
+// W is cleared first (outside-window blocks and padding stay zero), then Wt is
+// written by a tiled transpose that also zeroes its padding columns.
 // ---------------------------------------------------------------------------
 template <typename TW>
-__global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
-                                                      const float* __restrict__ M, TW* __restrict__ W,
-                                                      TW* __restrict__ Wt) {
-  // tile over (rows_out) x (padded input columns ldW); Wt written through a transpose
+__global__ void __launch_bounds__(256) build_w_tiled_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
+                                                            const float* __restrict__ M, TW* __restrict__ W) {
+  constexpr int PT = 32, AB = 128, KMAX = 64;
+  __shared__ float ws_[PT][KMAX + 1];
+  __shared__ float ms_[KMAX][AB];
+  const int pair = blockIdx.z;  // s * s_in + s'
+  const int s = pair / d.s_in, sp = pair % d.s_in;
+  if (sp < d.win_lo[s] || sp >= d.win_hi[s]) return;
+  const int nab = d.n_out * d.n_in, npairs = d.c_out * d.c_in;
+  const int p0 = blockIdx.y * PT, ab0 = blockIdx.x * AB;
+  if (p0 >= npairs || ab0 >= nab) return;
+  const float* Ms = M + (int64_t)s * d.K * nab;
+  float acc[PT * AB / 256];
+#pragma unroll
+  for (int i = 0; i < PT * AB / 256; ++i) acc[i] = 0.f;
+  for (int k0 = 0; k0 < d.K; k0 += KMAX) {
+    const int nk = min(KMAX, d.K - k0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < PT * KMAX; idx += 256) {
+      const int pp = idx / KMAX, kk = idx % KMAX, pr = p0 + pp;
+      float v = 0.f;
+      if (pr < npairs && kk < nk) {
+        const int co = pr / d.c_in, ci = pr % d.c_in;
+        v = w[((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K + k0 + kk];
+      }
+      ws_[pp][kk] = v;
+    }
+    for (int idx = threadIdx.x; idx < KMAX * AB; idx += 256) {
+      const int kk = idx / AB, aa = idx % AB;
+      ms_[kk][aa] = (kk < nk && ab0 + aa < nab) ? Ms[(int64_t)(k0 + kk) * nab + ab0 + aa] : 0.f;
+    }
+    __syncthreads();
+    // thread: column ab0 + (tid % 128), pairs (tid / 128) + 2 j
+    const int col = threadIdx.x % AB, pr0 = threadIdx.x / AB;
+    for (int kk = 0; kk < nk; ++kk) {
+      const float mv = ms_[kk][col];
+#pragma unroll
+      for (int j = 0; j < PT * AB / 256; ++j) acc[j] = fmaf(ws_[pr0 + 2 * j][kk], mv, acc[j]);
+    }
+  }
+  const int col = threadIdx.x % AB, pr0 = threadIdx.x / AB;
+  const int ab = ab0 + col;
+  if (ab >= nab) return;
+  const int aa = ab / d.n_in, bb = ab % d.n_in;
+#pragma unroll
+  for (int j = 0; j < PT * AB / 256; ++j) {
+    const int pr = p0 + pr0 + 2 * j;
+    if (pr >= npairs) continue;
+    const int co = pr / d.c_in, ci = pr % d.c_in;
+    const int64_t r = ((int64_t)s * d.c_out + co) * d.n_out + aa;
+    const int64_t c = (int64_t)sp * d.in_blk + (int64_t)ci * d.n_in + bb;
+    stf(W + r * d.ldW + c, acc[j]);
+  }
+}
+
+// Wt[c][oc] = W[row(oc)][col(c)] over the padded index space of Wt (32 x 32 tiles).
+template <typename TW>
+__global__ void __launch_bounds__(256) transpose_w_kernel(const __grid_constant__ LscDims d, const TW* __restrict__ W,
+                                                          TW* __restrict__ Wt) {
   __shared__ float tile[32][33];
-  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  const int per_in = d.c_in * d.n_in, per_out = d.c_out * d.n_out;
+  const int64_t oc0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int64_t cp = c0 + tx;  // padded input column
-  const int sp = (int)(cp / d.in_blk);
-  const int64_t cin = cp % d.in_blk;  // (ci, b) within the shell block, or padding
-  const bool col_valid = cp < d.ldW && cin < (int64_t)d.c_in * d.n_in;
-  const int ci = (int)(cin / d.n_in), bb = (int)(cin % d.n_in);
-  const int per_out = d.c_out * d.n_out;
+  // read: W rows = output rows of the Wt columns oc0.., W columns = padded input columns of Wt rows c0..
   for (int i = ty; i < 32; i += 8) {
-    const int64_t r = r0 + i;
-    float val = 0.f;
-    if (r < d.rows_out && col_valid) {
-      const int s = (int)(r / per_out), co = (int)((r / d.n_out) % d.c_out), aa = (int)(r % d.n_out);
-      if (sp >= d.win_lo[s] && sp < d.win_hi[s]) {
-        const float* wr = w + ((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K;
-        const float* mr = M + ((int64_t)s * d.K * d.n_out + aa) * d.n_in + bb;
-        const int64_t mstride = (int64_t)d.n_out * d.n_in;
-        for (int k = 0; k < d.K; ++k) val = fmaf(__ldg(wr + k), __ldg(mr + k * mstride), val);
+    const int64_t oc = oc0 + i;  // Wt column -> W row
+    const int64_t c = c0 + tx;   // Wt row (input row) -> W column
+    float v = 0.f;
+    if (oc < d.ldWt && c < d.rows_in) {
+      const int64_t s = oc / d.out_blk, rl = oc % d.out_blk;
+      if (rl < per_out) {
+        const int64_t wrow = s * per_out + rl;
+        const int64_t wcol = (c / per_in) * d.in_blk + c % per_in;
+        v = ldf(W + wrow * d.ldW + wcol);
       }
     }
-    if (r < d.rows_out && cp < d.ldW) stf(W + r * d.ldW + cp, val);
-    tile[i][tx] = val;
+    tile[i][tx] = v;
   }
   __syncthreads();
-  // transpose: thread (tx, i) writes Wt[input row of column c0 + i][padded output column of row r0 + tx]
   for (int i = ty; i < 32; i += 8) {
-    const int64_t cc = c0 + i;
-    if (cc >= d.ldW) continue;
-    const int spp = (int)(cc / d.in_blk);
-    const int64_t cinn = cc % d.in_blk;
-    if (cinn >= (int64_t)d.c_in * d.n_in) continue;
-    const int64_t in_row = (int64_t)spp * d.c_in * d.n_in + cinn;
-    const int64_t rr = r0 + tx;
-    if (rr >= d.rows_out) continue;
-    const int s = (int)(rr / per_out);
-    const int64_t oc = (int64_t)s * d.out_blk + rr % per_out;
-    stf(Wt + in_row * d.ldWt + oc, tile[tx][i]);
+    const int64_t c = c0 + i, oc = oc0 + tx;
+    if (c < d.rows_in && oc < d.ldWt) stf(Wt + c * d.ldWt + oc, tile[tx][i]);
   }
 }
 
@@ -169,19 +213,20 @@ __global__ void build_bias_kernel(const __grid_constant__ LscDims d, const float
 
 cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, const float* M, const float* q,
                            void* W, void* Wt, float* bias_vec, int w_t, cudaStream_t st) {
-  // zero the padding of Wt (columns between shell blocks are never produced by the transpose)
   const size_t es = w_t == 0 ? 4 : 2;
-  if (d.out_blk != (int64_t)d.c_out * d.n_out) {
-    cudaError_t e0 = cudaMemsetAsync(Wt, 0, (size_t)d.rows_in * d.ldWt * es, st);
-    if (e0 != cudaSuccess) return e0;
+  cudaError_t e = cudaMemsetAsync(W, 0, (size_t)d.rows_out * d.ldW * es, st);
+  if (e != cudaSuccess) return e;
+  const int nab = d.n_out * d.n_in, npairs = d.c_out * d.c_in;
+  dim3 grid((unsigned)((nab + 127) / 128), (unsigned)((npairs + 31) / 32), (unsigned)(d.s_out * d.s_in));
+  dim3 tgrid((unsigned)((d.ldWt + 31) / 32), (unsigned)((d.rows_in + 31) / 32));
+  if (w_t == 0) {
+    { build_w_tiled_kernel<float><<<grid, 256, 0, st>>>(d, w, M, (float*)W); count_launch(); }
+    { transpose_w_kernel<float><<<tgrid, dim3(32, 8), 0, st>>>(d, (const float*)W, (float*)Wt); count_launch(); }
+  } else {
+    { build_w_tiled_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(d, w, M, (__nv_bfloat16*)W); count_launch(); }
+    { transpose_w_kernel<__nv_bfloat16><<<tgrid, dim3(32, 8), 0, st>>>(d, (const __nv_bfloat16*)W, (__nv_bfloat16*)Wt); count_launch(); }
   }
-  dim3 grid((unsigned)((d.ldW + 31) / 32), (unsigned)((d.rows_out + 31) / 32));
-  dim3 block(32, 8);
-  if (w_t == 0)
-    { build_w_kernel<float><<<grid, block, 0, st>>>(d, w, M, (float*)W, (float*)Wt); count_launch(); }
-  else
-    { build_w_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(d, w, M, (__nv_bfloat16*)W, (__nv_bfloat16*)Wt); count_launch(); }
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess || !bias_vec) return e;
   { build_bias_kernel<<<(unsigned)((d.rows_out + 255) / 256), 256, 0, st>>>(d, b, q, bias_vec); count_launch(); }
   return cudaGetLastError();
@@ -345,36 +390,70 @@ cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int m
 }
 
 // ---------------------------------------------------------------------------
-// dW -> dw (kernel-point weights) and db.  One block per (ci, co, s, s').
+// dW -> dw (kernel-point weights) and db.  For a windowed shell pair,
+//   dw[co,s,ci,s',k] = sum_{a,b} M_s[k][a][b] G[(s,co,a)][(s',ci,b)],  G = sum_split P;
+// a block owns 32 channel pairs x all K and walks (a,b) in chunks of 128.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ LscDims d, const float* __restrict__ P,
                                                         int64_t ldp, int64_t split_stride, int splits,
                                                         const float* __restrict__ M, float* __restrict__ dw) {
-  extern __shared__ float blk[];
-  const int ci = blockIdx.x, co = blockIdx.y;
-  const int s = blockIdx.z / d.s_in, sp = blockIdx.z % d.s_in;
-  const int nn = d.n_out * d.n_in;
-  float* out = dw + ((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K;
-  if (sp < d.win_lo[s] || sp >= d.win_hi[s]) {
-    for (int k = threadIdx.x; k < d.K; k += blockDim.x) out[k] = 0.f;
-    return;
-  }
-  const int64_t row0 = ((int64_t)s * d.c_out + co) * d.n_out, col0 = ((int64_t)sp * d.c_in + ci) * d.n_in;
-  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
-    const int aa = idx / d.n_in, bb = idx % d.n_in;
-    float acc = 0.f;
-    for (int z = 0; z < splits; ++z) acc += P[z * split_stride + (row0 + aa) * ldp + col0 + bb];
-    blk[idx] = acc;
-  }
-  __syncthreads();
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int k = warp; k < d.K; k += blockDim.x / 32) {
-    const float* mk = M + ((int64_t)s * d.K + k) * nn;
-    float acc = 0.f;
-    for (int idx = lane; idx < nn; idx += 32) acc = fmaf(blk[idx], __ldg(mk + idx), acc);
+  constexpr int PT = 32, AB = 128, KMAX = 64;
+  __shared__ float gs[PT][AB + 1];
+  __shared__ float ms_[AB][KMAX + 1];
+  const int pair = blockIdx.z;
+  const int s = pair / d.s_in, sp = pair % d.s_in;
+  const int npairs = d.c_out * d.c_in, nab = d.n_out * d.n_in;
+  const int p0 = blockIdx.y * PT;
+  if (p0 >= npairs) return;
+  const bool in_win = sp >= d.win_lo[s] && sp < d.win_hi[s];
+  // outputs of this thread: (pair p0 + pp, k) for idx = tid + 256 j
+  constexpr int OPT = (PT * KMAX + 255) / 256;
+  float acc[OPT];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[k] = acc;
+  for (int j = 0; j < OPT; ++j) acc[j] = 0.f;
+  for (int k0 = 0; k0 < d.K; k0 += KMAX) {
+    const int nk = min(KMAX, d.K - k0);
+    if (in_win) {
+      for (int ab0 = 0; ab0 < nab; ab0 += AB) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < PT * AB; idx += 256) {
+          const int pp = idx / AB, t = idx % AB, pr = p0 + pp, ab = ab0 + t;
+          float v = 0.f;
+          if (pr < npairs && ab < nab) {
+            const int co = pr / d.c_in, ci = pr % d.c_in, aa = ab / d.n_in, bb = ab % d.n_in;
+            const int64_t off = (((int64_t)s * d.c_out + co) * d.n_out + aa) * ldp + ((int64_t)sp * d.c_in + ci) * d.n_in + bb;
+            for (int z = 0; z < splits; ++z) v += P[z * split_stride + off];
+          }
+          gs[pp][t] = v;
+        }
+        for (int idx = threadIdx.x; idx < AB * KMAX; idx += 256) {
+          const int t = idx / KMAX, kk = idx % KMAX, ab = ab0 + t;
+          ms_[t][kk] = (ab < nab && kk < nk) ? M[((int64_t)s * d.K + k0 + kk) * nab + ab] : 0.f;
+        }
+        __syncthreads();
+        const int nt = min(AB, nab - ab0);
+#pragma unroll
+        for (int j = 0; j < OPT; ++j) {
+          const int idx = threadIdx.x + 256 * j;
+          const int pp = idx / KMAX, kk = idx % KMAX;
+          if (pp < PT) {
+            float a = acc[j];
+            for (int t = 0; t < nt; ++t) a = fmaf(gs[pp][t], ms_[t][kk], a);
+            acc[j] = a;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < OPT; ++j) {
+      const int idx = threadIdx.x + 256 * j;
+      const int pp = idx / KMAX, kk = idx % KMAX, pr = p0 + pp;
+      if (pp < PT && kk < nk && pr < npairs) {
+        const int co = pr / d.c_in, ci = pr % d.c_in;
+        dw[((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K + k0 + kk] = in_win ? acc[j] : 0.f;
+      }
+      acc[j] = 0.f;
+    }
   }
 }
 
@@ -397,13 +476,8 @@ __global__ void reduce_db_kernel(const __grid_constant__ LscDims d, const float*
 cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int64_t split_stride, int splits,
                              const float* M, const float* q, float* dw, float* db, cudaStream_t st) {
   if (dw) {
-    dim3 grid(d.c_in, d.c_out, d.s_out * d.s_in);
-    const size_t smem = sizeof(float) * d.n_out * d.n_in;
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(reduce_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    { reduce_dw_kernel<<<grid, 256, smem, st>>>(d, P, ldp, split_stride, splits, M, dw); count_launch(); }
+    dim3 grid(1, (unsigned)((d.c_out * d.c_in + 31) / 32), (unsigned)(d.s_out * d.s_in));
+    { reduce_dw_kernel<<<grid, 256, 0, st>>>(d, P, ldp, split_stride, splits, M, dw); count_launch(); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

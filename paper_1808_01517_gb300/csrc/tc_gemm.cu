@@ -692,21 +692,4 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// transforms: CUDA-core kernels for now
-// ---------------------------------------------------------------------------
-cudaError_t tc_basis_tables_create(const BasisHost&, TcBasisTables& t, std::string&) {
-  t = TcBasisTables();
-  return cudaSuccess;
-}
-void tc_basis_tables_destroy(TcBasisTables& t) {
-  if (t.d_mem) cudaFree(t.d_mem);
-  t.d_mem = nullptr;
-}
-bool tc_transform_supported(const TcBasisTables& t, int, int64_t, int64_t, int) { return t.ok && tc_enabled(); }
-cudaError_t tc_transform_launch(const TcBasisTables&, int, const void*, void*, int64_t, int, int64_t, int64_t, int, int*,
-                                cudaStream_t) {
-  return cudaErrorNotSupported;
-}
-
 }  // namespace delimit

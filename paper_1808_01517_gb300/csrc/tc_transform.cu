@@ -1,0 +1,395 @@
+// tcgen05 + TMA grouped transforms of the BF16 path: Signal2SH, SH2Signal and
+// their adjoints (Sec. 2.2).  Per shell g and channel c:
+//   Y[(g,c,i), v] = sum_j T_g[i][j] X[(g,c,j), v]
+// D[voxel, i] lives in TMEM (M = 128 voxels, N = n_out rounded to 16); A is a
+// 128-voxel x n_in tile of X loaded by TMA through a 3-D map {voxels, rows,
+// channels} so rows past n_in are zero-filled per channel; B = T_g^T (BF16,
+// [n_in padded to 16] x [n_out padded to 64]) stays resident in shared memory.
+// The kernel is HBM-bound (about 15 FLOP per byte at order 8): each CTA keeps
+// STAGES A tiles in flight and double-buffers the accumulator.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "tc_gemm.h"
+#include "tc_ptx.cuh"
+
+namespace delimit {
+
+namespace {
+
+constexpr int kThreads = 192;
+constexpr int kMaxTcGroups = 8;
+constexpr int kAccCols = 256;  // TMEM columns per accumulator buffer
+
+enum : int { kErrFull = 0x1100, kErrEmpty = 0x1200, kErrTFull = 0x1300, kErrTEmpty = 0x1400, kErrDrain = 0x1500 };
+
+}  // namespace
+
+struct TfGroup {
+  int64_t y_row0, y_cstride;
+  int n_out, n_mma, kpad, npad;
+  uint32_t b_off;  // byte offset of this group's B image in shared memory
+};
+
+struct TfParams {
+  CUtensorMap mapA[kMaxTcGroups];
+  CUtensorMap mapB[kMaxTcGroups];
+  TfGroup g[kMaxTcGroups];
+  int n_groups, channels, m_tiles, stages, stage_bytes;
+  uint32_t b_total;
+  int64_t total_tiles, n_vox, ldy;
+  void* Y;
+  int* err;
+};
+
+template <bool OUT_F32>
+__global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_constant__ TfParams p) {
+  using namespace ptx;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int STAGES = p.stages;
+  // layout: [B images][A stages][barriers]
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t a_base = sbase + p.b_total;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.b_total + (size_t)STAGES * p.stage_bytes);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], bload, drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
+  auto tfull_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
+  auto tempty_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
+  const uint32_t bload_bar = smem_u32(bars + 2 * STAGES + 4);
+  const uint32_t drain_bar = smem_u32(bars + 2 * STAGES + 5);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 4);
+    }
+    mbar_init(bload_bar, 1);
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), 2 * kAccCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int64_t per_group = (int64_t)p.channels * p.m_tiles;
+
+  if (warp == 0 && lane == 0) {
+    // resident B images (all groups), then the A ring
+    uint32_t bbytes = 0;
+    for (int g = 0; g < p.n_groups; ++g) bbytes += (uint32_t)(p.g[g].kpad * p.g[g].npad * 2);
+    mbar_arrive_expect_tx(bload_bar, bbytes);
+    for (int g = 0; g < p.n_groups; ++g)
+      for (int j = 0; j < p.g[g].npad / 64; ++j)
+        tma_load_2d(&p.mapB[g], bload_bar, sbase + p.g[g].b_off + j * p.g[g].kpad * 128, j * 64, 0);
+    int stage = 0;
+    uint32_t phase = 0;
+    int pend[8];
+    for (int s = 0; s < 8; ++s) pend[s] = -1;
+    for (int64_t t = blockIdx.x; t < p.total_tiles && !*abort_flag; t += gridDim.x) {
+      const int g = (int)(t / per_group);
+      const int64_t r = t % per_group;
+      const int c = (int)(r / p.m_tiles), mt = (int)(r % p.m_tiles);
+      if (!wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, p.err, kErrEmpty)) break;
+      const uint32_t dst = a_base + stage * p.stage_bytes;
+      const int kp = p.g[g].kpad;
+      mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(2 * kp * 128));
+      tma_load_3d(&p.mapA[g], full_bar(stage), dst, mt * 128, 0, c);
+      tma_load_3d(&p.mapA[g], full_bar(stage), dst + kp * 128, mt * 128 + 64, 0, c);
+      pend[stage] = (int)phase;
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+    }
+    wait_drain(bload_bar, 0, p.err, kErrDrain);
+    for (int s = 0; s < STAGES; ++s)
+      if (pend[s] >= 0) wait_drain(full_bar(s), (uint32_t)pend[s], p.err, kErrDrain);
+  } else if (warp == 1 && lane == 0) {
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    bool bready = wait_bounded(bload_bar, 0, abort_flag, p.err, kErrFull);
+    for (int64_t t = blockIdx.x; bready && t < p.total_tiles && !*abort_flag; t += gridDim.x) {
+      const int g = (int)(t / per_group);
+      const TfGroup& G = p.g[g];
+      if (!wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.err, kErrTEmpty)) break;
+      tc_fence_after();
+      if (!wait_bounded(full_bar(stage), phase, abort_flag, p.err, kErrFull)) break;
+      tc_fence_after();
+      const uint32_t a_src = a_base + stage * p.stage_bytes, b_src = sbase + G.b_off;
+      const uint32_t idesc = idesc_bf16(128, G.n_mma, true, true);
+      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
+      for (int k = 0; k < G.kpad / 16; ++k) {
+        const uint64_t ad = umma_desc(a_src + k * 2048, G.kpad * 128, 1024, kSwizzle128B);
+        const uint64_t bd = umma_desc(b_src + k * 2048, G.kpad * 128, 1024, kSwizzle128B);
+        mma_bf16(d_tmem, ad, bd, idesc, k != 0);
+      }
+      mma_commit(empty_bar(stage));
+      mma_commit(tfull_bar(acc));
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1u;
+    }
+    mma_commit(drain_bar);
+    wait_drain(drain_bar, 0, p.err, kErrDrain);
+  } else if (warp >= 2) {
+    const int q = warp & 3;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+      const int g = (int)(t / per_group);
+      const int64_t r = t % per_group;
+      const int c = (int)(r / p.m_tiles), mt = (int)(r % p.m_tiles);
+      const TfGroup& G = p.g[g];
+      bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTFull);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      const int64_t vox = (int64_t)mt * 128 + q * 32 + lane;
+      const bool vok = vox < p.n_vox;
+      const int64_t row0 = G.y_row0 + (int64_t)c * G.y_cstride;
+      for (int c0 = 0; c0 < G.n_out; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols + c0), v);
+        if (vok) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (c0 + j < G.n_out) {
+              const int64_t off = (row0 + c0 + j) * p.ldy + vox;
+              if (OUT_F32)
+                reinterpret_cast<float*>(p.Y)[off] = v[j];
+              else
+                reinterpret_cast<__nv_bfloat16*>(p.Y)[off] = __float2bfloat16_rn(v[j]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(acc));
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1u;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 2 * kAccCols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 tf_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  return fn;
+}
+
+int tf_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, sms);
+}
+
+int tf_major() {
+  int dev = 0, major = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  return major;
+}
+
+int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+constexpr size_t kSmemLimit = 220 * 1024;
+
+}  // namespace
+
+cudaError_t tc_basis_tables_create(const BasisHost& h, TcBasisTables& t, std::string& err) {
+  t = TcBasisTables();
+  t.n_shells = int(h.shells.size());
+  t.N = h.N;
+  if (t.n_shells > kMaxTcGroups) return cudaSuccess;  // CUDA-core kernels only
+  std::vector<__nv_bfloat16> img;
+  for (int s = 0; s < t.n_shells; ++s) {
+    const ShellHost& sh = h.shells[s];
+    t.m[s] = sh.m;
+    t.dir_off[s] = sh.dir_off;
+    for (int kind = 0; kind < 4; ++kind) {
+      // T[i][j] of this kind and its (n_out, n_in)
+      const bool out_is_coef = (kind == 0 || kind == 3);
+      const int n_out = out_is_coef ? h.N : sh.m, n_in = out_is_coef ? sh.m : h.N;
+      auto T = [&](int i, int j) -> double {
+        switch (kind) {
+          case 0: return sh.P[size_t(i) * sh.m + j];   // P [N][m]
+          case 1: return sh.B[size_t(i) * h.N + j];    // B [m][N]
+          case 2: return sh.P[size_t(j) * sh.m + i];   // P^T [m][N]
+          default: return sh.B[size_t(j) * h.N + i];   // B^T [N][m]
+        }
+      };
+      const int kpad = round_up(n_in, 16), npad = round_up(n_out, 64);
+      t.n_in[s][kind] = n_in;
+      t.n_out[s][kind] = n_out;
+      t.kpad[s][kind] = kpad;
+      t.npad[s][kind] = npad;
+      size_t off = (img.size() + 511) / 512 * 512;  // 1 KiB aligned (in elements of 2 bytes)
+      img.resize(off + size_t(kpad) * npad, __float2bfloat16_rn(0.f));
+      for (int k = 0; k < n_in; ++k)
+        for (int n = 0; n < n_out; ++n) img[off + size_t(k) * npad + n] = __float2bfloat16_rn(float(T(n, k)));
+      t.off[s][kind] = off * 2;
+    }
+  }
+  cudaError_t e = cudaMalloc(&t.d_mem, img.size() * 2);
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    return e;
+  }
+  e = cudaMemcpy(t.d_mem, img.data(), img.size() * 2, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    cudaFree(t.d_mem);
+    t.d_mem = nullptr;
+    return e;
+  }
+  t.ok = true;
+  return cudaSuccess;
+}
+
+void tc_basis_tables_destroy(TcBasisTables& t) {
+  if (t.d_mem) cudaFree(t.d_mem);
+  t.d_mem = nullptr;
+  t.ok = false;
+}
+
+bool tc_transform_supported(const TcBasisTables& t, int kind, int64_t ldx, int64_t ldy, int out_t) {
+  (void)ldx;
+  (void)ldy;
+  (void)out_t;
+  if (!t.ok || !tc_enabled() || !tf_encode() || tf_major() != 10) return false;
+  size_t btot = 0;
+  int kmax = 0;
+  for (int s = 0; s < t.n_shells; ++s) {
+    if (t.n_in[s][kind] > 256 || t.n_out[s][kind] > 256) return false;
+    btot += size_t(t.kpad[s][kind]) * t.npad[s][kind] * 2;
+    kmax = std::max(kmax, t.kpad[s][kind]);
+  }
+  const size_t stage = size_t(kmax) * 256;
+  return btot + 2 * stage + 2048 <= kSmemLimit;
+}
+
+cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X, void* Y, int64_t n_vox, int C,
+                                int64_t ldx, int64_t ldy, int out_t, int* err_word, cudaStream_t st) {
+  auto fn = tf_encode();
+  if (!fn) return cudaErrorNotSupported;
+  TfParams p;
+  memset(&p, 0, sizeof p);
+  const bool x_is_sig = (kind == 0 || kind == 3);  // input rows in the signal layout
+  uint32_t boff = 0;
+  int kmax = 0;
+  for (int s = 0; s < t.n_shells; ++s) {
+    const int n_in = t.n_in[s][kind], n_out = t.n_out[s][kind];
+    const int kpad = t.kpad[s][kind], npad = t.npad[s][kind];
+    const int64_t sig_row0 = int64_t(C) * t.dir_off[s], sig_cs = t.m[s];
+    const int64_t sh_row0 = int64_t(s) * C * t.N, sh_cs = t.N;
+    const int64_t x_row0 = x_is_sig ? sig_row0 : sh_row0, x_cs = x_is_sig ? sig_cs : sh_cs;
+    TfGroup& G = p.g[s];
+    G.y_row0 = x_is_sig ? sh_row0 : sig_row0;
+    G.y_cstride = x_is_sig ? sh_cs : sig_cs;
+    G.n_out = n_out;
+    G.n_mma = round_up(n_out, 16);
+    G.kpad = kpad;
+    G.npad = npad;
+    G.b_off = boff;
+    boff += uint32_t(kpad) * npad * 2;
+    kmax = std::max(kmax, kpad);
+    // A: 3-D {voxels, rows of one channel, channels}
+    {
+      const char* base = static_cast<const char*>(X) + x_row0 * ldx * 2;
+      cuuint64_t dims[3] = {(cuuint64_t)n_vox, (cuuint64_t)n_in, (cuuint64_t)C};
+      cuuint64_t strides[2] = {(cuuint64_t)ldx * 2, (cuuint64_t)(x_cs * ldx * 2)};
+      cuuint32_t box[3] = {64, (cuuint32_t)kpad, 1};
+      cuuint32_t es[3] = {1, 1, 1};
+      if (fn(&p.mapA[s], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<char*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    }
+    // B: 2-D {npad columns, kpad rows} of this group's image
+    {
+      const char* base = static_cast<const char*>(t.d_mem) + t.off[s][kind];
+      cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)kpad};
+      cuuint64_t strides[1] = {(cuuint64_t)npad * 2};
+      cuuint32_t box[2] = {64, (cuuint32_t)kpad};
+      cuuint32_t es[2] = {1, 1};
+      if (fn(&p.mapB[s], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<char*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    }
+  }
+  p.n_groups = t.n_shells;
+  p.channels = C;
+  p.m_tiles = (int)((n_vox + 127) / 128);
+  p.stage_bytes = kmax * 256;
+  p.b_total = (boff + 1023) / 1024 * 1024;
+  const size_t fixed = 1024 + p.b_total + 16 * 8 + 64;
+  int stages = (int)((kSmemLimit - fixed) / p.stage_bytes);
+  stages = std::max(2, std::min(8, stages));
+  p.stages = stages;
+  p.total_tiles = (int64_t)t.n_shells * C * p.m_tiles;
+  p.n_vox = n_vox;
+  p.ldy = ldy;
+  p.Y = Y;
+  p.err = err_word;
+  // at least 120 KiB so that two CTAs never share an SM (each holds 512 TMEM columns)
+  const size_t smem = std::max<size_t>(120 * 1024, fixed + (size_t)stages * p.stage_bytes + (2 * stages + 6) * 8);
+  if (p.total_tiles == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(p.total_tiles, tf_sms());
+  cudaError_t e;
+  if (out_t == 0) {
+    e = cudaFuncSetAttribute(transform_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    transform_tc_kernel<true><<<grid, kThreads, smem, st>>>(p);
+  } else {
+    e = cudaFuncSetAttribute(transform_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    transform_tc_kernel<false><<<grid, kThreads, smem, st>>>(p);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace delimit
