@@ -37,8 +37,9 @@ struct TfGroup {
 struct TfParams {
   CUtensorMap mapA[kMaxTcGroups];
   CUtensorMap mapB[kMaxTcGroups];
+  CUtensorMap mapY[kMaxTcGroups];  // output, 3-D {voxels, rows of one channel, channels}
   TfGroup g[kMaxTcGroups];
-  int n_groups, channels, m_tiles, stages, stage_bytes;
+  int n_groups, channels, m_tiles, stages, stage_bytes, stg_bytes;
   uint32_t b_total;
   int64_t total_tiles, n_vox, ldy;
   void* Y;
@@ -51,12 +52,14 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int STAGES = p.stages;
-  // layout: [B images][A stages][barriers]
+  // layout: [B images][A stages][2 output staging tiles][barriers]
   const uint32_t sbase = smem_u32(smem);
   const uint32_t a_base = sbase + p.b_total;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.b_total + (size_t)STAGES * p.stage_bytes);
-  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], bload, drain
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  const uint32_t stg_base = a_base + STAGES * p.stage_bytes;
+  uint8_t* stg_ptr = smem + p.b_total + (size_t)STAGES * p.stage_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_ptr + 2 * (size_t)p.stg_bytes);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], bload, drain, stg_ready[2], stg_free[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 10);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
@@ -65,6 +68,8 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
   auto tempty_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
   const uint32_t bload_bar = smem_u32(bars + 2 * STAGES + 4);
   const uint32_t drain_bar = smem_u32(bars + 2 * STAGES + 5);
+  auto stg_ready_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + 6 + b); };
+  auto stg_free_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + 8 + b); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -77,6 +82,10 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
     }
     mbar_init(bload_bar, 1);
     mbar_init(drain_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(stg_ready_bar(b), 4);
+      mbar_init(stg_free_bar(b), 1);
+    }
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -154,43 +163,69 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
     mma_commit(drain_bar);
     wait_drain(drain_bar, 0, p.err, kErrDrain);
   } else if (warp >= 2) {
+    // TMEM -> registers -> shared staging tile [rows][64 voxels] x 2 halves -> TMA store.
+    // Two staging buffers; stg_ready (4 warp arrivals) hands a filled buffer to the
+    // storing lane, stg_free (1 arrival) returns it once its store has read it.
+    constexpr int ES = OUT_F32 ? 4 : 2;
     const int q = warp & 3;
+    const bool leader = (warp == 2 && lane == 0);
+    const int h = q >> 1, xl = (q & 1) * 32 + lane;  // voxel half and voxel within the half
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x, ++it) {
       const int g = (int)(t / per_group);
       const int64_t r = t % per_group;
       const int c = (int)(r / p.m_tiles), mt = (int)(r % p.m_tiles);
       const TfGroup& G = p.g[g];
+      const int buf = it & 1;
+      const uint32_t use_par = (uint32_t)((it >> 1) & 1);
       bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTFull);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
+      ok = ok && wait_bounded(stg_free_bar(buf), use_par ^ 1u, abort_flag, p.err, kErrTEmpty);
+      if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const int64_t vox = (int64_t)mt * 128 + q * 32 + lane;
-      const bool vok = vox < p.n_vox;
-      const int64_t row0 = G.y_row0 + (int64_t)c * G.y_cstride;
+      uint8_t* stg = stg_ptr + (size_t)buf * p.stg_bytes + (size_t)h * G.n_out * 64 * ES;
       for (int c0 = 0; c0 < G.n_out; c0 += 16) {
         float v[16];
         tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols + c0), v);
-        if (vok) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if (c0 + j < G.n_out) {
-              const int64_t off = (row0 + c0 + j) * p.ldy + vox;
-              if (OUT_F32)
-                reinterpret_cast<float*>(p.Y)[off] = v[j];
-              else
-                reinterpret_cast<__nv_bfloat16*>(p.Y)[off] = __float2bfloat16_rn(v[j]);
-            }
+        for (int j = 0; j < 16; ++j) {
+          if (c0 + j < G.n_out) {
+            if (OUT_F32)
+              reinterpret_cast<float*>(stg)[(c0 + j) * 64 + xl] = v[j];
+            else
+              reinterpret_cast<__nv_bfloat16*>(stg)[(c0 + j) * 64 + xl] = __float2bfloat16_rn(v[j]);
           }
         }
       }
+      // accumulator drained: hand it back to the MMA warp; staging filled: hand it to the store
       tc_fence_before();
+      fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty_bar(acc));
+      if (lane == 0) {
+        mbar_arrive(tempty_bar(acc));
+        mbar_arrive(stg_ready_bar(buf));
+      }
+      if (warp == 2) {
+        bool lead_ok = true;
+        if (lane == 0) {
+          lead_ok = wait_bounded(stg_ready_bar(buf), use_par, abort_flag, p.err, kErrTFull);
+          if (lead_ok) {
+            const uint32_t src = stg_base + (uint32_t)(buf * p.stg_bytes);
+            tma_store_3d(&p.mapY[g], src, mt * 128, 0, c);
+            tma_store_3d(&p.mapY[g], src + (uint32_t)(G.n_out * 64 * ES), mt * 128 + 64, 0, c);
+            bulk_commit();
+            // the previous tile's store has finished reading its buffer: release it
+            bulk_wait_read<1>();
+            if (it >= 1) mbar_arrive(stg_free_bar(buf ^ 1));
+          }
+        }
+        if (!__shfl_sync(0xffffffffu, lead_ok ? 1 : 0, 0)) break;
+      }
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
+    if (leader) bulk_wait<0>();
   }
   tc_fence_before();
   __syncthreads();
@@ -306,8 +341,11 @@ bool tc_transform_supported(const TcBasisTables& t, int kind, int64_t ldx, int64
     btot += size_t(t.kpad[s][kind]) * t.npad[s][kind] * 2;
     kmax = std::max(kmax, t.kpad[s][kind]);
   }
+  int nmax = 0;
+  for (int s = 0; s < t.n_shells; ++s) nmax = std::max(nmax, t.n_out[s][kind]);
   const size_t stage = size_t(kmax) * 256;
-  return btot + 2 * stage + 2048 <= kSmemLimit;
+  const size_t stg = 2 * (size_t(2 * nmax * 64 * (out_t == 0 ? 4 : 2)) + 1024);
+  return btot + 2 * stage + stg + 4096 <= kSmemLimit;
 }
 
 cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X, void* Y, int64_t n_vox, int C,
@@ -360,12 +398,29 @@ cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X,
         return cudaErrorInvalidValue;
     }
   }
+  // output maps
+  const int es = out_t == 0 ? 4 : 2;
+  int nmax = 0;
+  for (int s = 0; s < t.n_shells; ++s) {
+    const TfGroup& G = p.g[s];
+    nmax = std::max(nmax, G.n_out);
+    const char* base = static_cast<const char*>(Y) + G.y_row0 * ldy * es;
+    cuuint64_t dims[3] = {(cuuint64_t)n_vox, (cuuint64_t)G.n_out, (cuuint64_t)C};
+    cuuint64_t strides[2] = {(cuuint64_t)ldy * es, (cuuint64_t)(G.y_cstride * ldy * es)};
+    cuuint32_t box[3] = {64, (cuuint32_t)G.n_out, 1};
+    cuuint32_t esz[3] = {1, 1, 1};
+    if (fn(&p.mapY[s], out_t == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+           const_cast<char*>(base), dims, strides, box, esz, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
   p.n_groups = t.n_shells;
   p.channels = C;
   p.m_tiles = (int)((n_vox + 127) / 128);
   p.stage_bytes = kmax * 256;
+  p.stg_bytes = (2 * nmax * 64 * es + 1023) / 1024 * 1024;
   p.b_total = (boff + 1023) / 1024 * 1024;
-  const size_t fixed = 1024 + p.b_total + 16 * 8 + 64;
+  const size_t fixed = 1024 + p.b_total + 2 * (size_t)p.stg_bytes + 16 * 8 + 128;
   int stages = (int)((kSmemLimit - fixed) / p.stage_bytes);
   stages = std::max(2, std::min(8, stages));
   p.stages = stages;
@@ -375,7 +430,7 @@ cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X,
   p.Y = Y;
   p.err = err_word;
   // at least 120 KiB so that two CTAs never share an SM (each holds 512 TMEM columns)
-  const size_t smem = std::max<size_t>(120 * 1024, fixed + (size_t)stages * p.stage_bytes + (2 * stages + 6) * 8);
+  const size_t smem = std::max<size_t>(120 * 1024, fixed + (size_t)stages * p.stage_bytes + (2 * stages + 10) * 8);
   if (p.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)std::min<int64_t>(p.total_tiles, tf_sms());
   cudaError_t e;
