@@ -19,6 +19,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <atomic>
 #include <mutex>
 
@@ -78,22 +79,27 @@ __device__ __forceinline__ void vox_decode(const VoxParams& p, int64_t t, int& g
   nt = r;
 }
 
-template <int BN, int STAGES>
+// STAGED: the epilogue writes the tile to shared memory and stores it with TMA
+// through mapY (3-D {voxels, N rows of a group, groups}: rows past a group's N
+// are clipped); otherwise each lane stores its voxel's columns directly.
+template <int BN, int STAGES, bool STAGED>
 __global__ void __launch_bounds__(kThreads, 1)
     vox_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                    const __grid_constant__ VoxParams p) {
+                    const __grid_constant__ CUtensorMap mapY, const __grid_constant__ VoxParams p) {
   using namespace ptx;
   constexpr int A_BYTES = 2 * kBoxBytes;        // 128 voxels x 64 K rows
   constexpr int B_BYTES = (BN / 64) * kBoxBytes;  // BN columns x 64 K rows
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr int STG_BYTES = STAGED ? BN * 128 * 2 : 0;  // [BN rows][64 voxels] x 2 halves, BF16
   constexpr uint32_t TMEM_COLS = (2 * BN <= 256) ? 256 : 512;
   constexpr uint32_t IDESC = idesc_bf16(128, BN, true, true);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  uint8_t* stg_ptr = smem + STAGES * STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_ptr + STG_BYTES);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain, stg_ready, stg_free
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 7);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -103,6 +109,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto tfull_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
   auto tempty_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
   const uint32_t drain_bar = smem_u32(bars + 2 * STAGES + 4);
+  const uint32_t stg_ready_bar = smem_u32(bars + 2 * STAGES + 5);
+  const uint32_t stg_free_bar = smem_u32(bars + 2 * STAGES + 6);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -114,10 +122,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(tempty_bar(b), 4);
     }
     mbar_init(drain_bar, 1);
+    mbar_init(stg_ready_bar, 4);
+    mbar_init(stg_free_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
     prefetch_tmap(&mapA);
     prefetch_tmap(&mapB);
+    if (STAGED) prefetch_tmap(&mapY);
   }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
@@ -211,37 +222,65 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+    int it = 0;
+    const int h = q >> 1, xl = (q & 1) * 32 + lane;
+    for (int64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x, ++it) {
       int g, mt, nt;
       vox_decode(p, t, g, mt, nt);
       const VoxGroup& G = p.g[g];
       bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTmemFull);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
+      if (STAGED) ok = ok && wait_bounded(stg_free_bar, (uint32_t)(it & 1) ^ 1u, abort_flag, p.err, kErrTmemEmpty);
+      if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const int64_t vox = (int64_t)mt * 128 + q * 32 + lane;
       const bool vok = vox < p.n_vox;
       for (int c0 = 0; c0 < BN; c0 += 16) {
         const int nbase = nt * BN + c0;
         if (nbase >= G.N) break;
+        float bv[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          bv[j] = (p.bias && nbase + j < G.N) ? __ldg(p.bias + G.y_row0 + nbase + j) : 0.f;
         float v[16];
         tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c0), v);
+        if (STAGED) {
+          __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(stg_ptr) + (size_t)h * BN * 64;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = nbase + j;
-          if (n < G.N && vok) {
-            const int64_t row = G.y_row0 + n;
-            const float b = p.bias ? __ldg(p.bias + row) : 0.f;
-            p.Y[row * p.ldy + vox] = __float2bfloat16_rn(v[j] + b);
+          for (int j = 0; j < 16; ++j) stg[(c0 + j) * 64 + xl] = __float2bfloat16_rn(v[j] + bv[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = nbase + j;
+            if (n < G.N && vok) p.Y[(G.y_row0 + n) * p.ldy + vox] = __float2bfloat16_rn(v[j] + bv[j]);
           }
         }
       }
       tc_fence_before();
+      if (STAGED) fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty_bar(acc));
+      if (lane == 0) {
+        mbar_arrive(tempty_bar(acc));
+        if (STAGED) mbar_arrive(stg_ready_bar);
+      }
+      if (STAGED && warp == 2) {
+        bool lead_ok = true;
+        if (lane == 0) {
+          lead_ok = wait_bounded(stg_ready_bar, (uint32_t)(it & 1), abort_flag, p.err, kErrTmemFull);
+          if (lead_ok) {
+            const uint32_t src = smem_u32(stg_ptr);
+            tma_store_3d(&mapY, src, mt * 128, nt * BN, g);
+            tma_store_3d(&mapY, src + BN * 128, mt * 128 + 64, nt * BN, g);
+            bulk_commit();
+            bulk_wait_read<0>();
+            mbar_arrive(stg_free_bar);
+          }
+        }
+        if (!__shfl_sync(0xffffffffu, lead_ok ? 1 : 0, 0)) break;
+      }
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
+    if (STAGED && warp == 2 && lane == 0) bulk_wait<0>();
   }
   tc_fence_before();
   __syncthreads();
@@ -522,9 +561,10 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, bool STAGED>
 constexpr int vox_stages() {
-  return (BN == 256) ? 4 : (BN == 192 ? 5 : 6);
+  // operand ring + (staged) one BN x 128 BF16 output tile within ~210 KiB
+  return STAGED ? (BN == 256 ? 3 : (BN == 192 ? 4 : 5)) : ((BN == 256) ? 4 : (BN == 192 ? 5 : 6));
 }
 
 template <int BN, int STAGES>
@@ -532,16 +572,17 @@ constexpr size_t smem_bytes(int a_bytes, int b_bytes) {
   return 1024 + (size_t)STAGES * (a_bytes + b_bytes) + (2 * STAGES + 5) * 8 + 16;
 }
 
-template <int BN>
-cudaError_t launch_vox(const CUtensorMap& ma, const CUtensorMap& mb, const VoxParams& p, cudaStream_t st) {
-  constexpr int S = vox_stages<BN>();
-  const size_t smem = smem_bytes<BN, S>(2 * kBoxBytes, (BN / 64) * kBoxBytes);
-  auto kern = vox_gemm_kernel<BN, S>;
+template <int BN, bool STAGED>
+cudaError_t launch_vox(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& my, const VoxParams& p,
+                       cudaStream_t st) {
+  constexpr int S = vox_stages<BN, STAGED>();
+  const size_t smem = smem_bytes<BN, S>(2 * kBoxBytes, (BN / 64) * kBoxBytes) + (STAGED ? BN * 256 : 0) + 16;
+  auto kern = vox_gemm_kernel<BN, S, STAGED>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int sms = std::max(1, dev_info().sms);
   const unsigned grid = (unsigned)std::min<int64_t>(p.total_tiles, sms);
-  { kern<<<grid, kThreads, smem, st>>>(ma, mb, p); count_launch(); }
+  { kern<<<grid, kThreads, smem, st>>>(ma, mb, my, p); count_launch(); }
   return cudaGetLastError();
 }
 
@@ -561,19 +602,48 @@ int pick_bn(const int* Ns, int n) {
   return best;
 }
 
-cudaError_t run_vox(const CUtensorMap& ma, const CUtensorMap& mb, VoxParams& p, int bn, cudaStream_t st) {
+// The staged epilogue is used when every group has the same N (one 3-D output
+// map covers them) and the tile is at most 192 wide (ring + tile fit in smem).
+cudaError_t run_vox(const CUtensorMap& ma, const CUtensorMap& mb, VoxParams& p, int bn, bool staged_ok,
+                    void* Y, int64_t ldy, cudaStream_t st) {
   p.tiles_per_m = 0;
+  bool same_n = true;
   for (int i = 0; i < p.n_groups; ++i) {
     p.g[i].n_tiles = (p.g[i].N + bn - 1) / bn;
     p.tiles_per_m += p.g[i].n_tiles;
+    same_n = same_n && p.g[i].N == p.g[0].N && p.g[i].y_row0 == (int64_t)i * p.g[0].N;
   }
   p.total_tiles = (int64_t)p.m_tiles * p.tiles_per_m;
   if (p.total_tiles == 0) return cudaSuccess;
-  switch (bn) {
-    case 256: return launch_vox<256>(ma, mb, p, st);
-    case 192: return launch_vox<192>(ma, mb, p, st);
-    default: return launch_vox<128>(ma, mb, p, st);
+  CUtensorMap my;
+  memset(&my, 0, sizeof my);
+  bool staged = staged_ok && same_n && bn <= 192;
+  if (staged) {
+    auto fn = encode_fn();
+    cuuint64_t dims[3] = {(cuuint64_t)p.n_vox, (cuuint64_t)p.g[0].N, (cuuint64_t)p.n_groups};
+    cuuint64_t strides[2] = {(cuuint64_t)ldy * 2, (cuuint64_t)(p.g[0].N * ldy * 2)};
+    cuuint32_t box[3] = {64, (cuuint32_t)bn, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    staged = fn(&my, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Y, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   }
+  if (staged) {
+    switch (bn) {
+      case 192: return launch_vox<192, true>(ma, mb, my, p, st);
+      default: return launch_vox<128, true>(ma, mb, my, p, st);
+    }
+  }
+  switch (bn) {
+    case 256: return launch_vox<256, false>(ma, mb, my, p, st);
+    case 192: return launch_vox<192, false>(ma, mb, my, p, st);
+    default: return launch_vox<128, false>(ma, mb, my, p, st);
+  }
+}
+
+int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return (v && *v) ? atoi(v) : dflt;
 }
 
 }  // namespace
@@ -614,7 +684,11 @@ cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* Wt, cons
   p.Y = reinterpret_cast<__nv_bfloat16*>(Y);
   p.bias = bias;
   p.err = err;
-  return run_vox(ma, mb, p, pick_bn(Ns, d.s_out), st);
+  // forward tiles are short in K and wide in output: stage the epilogue through TMA stores
+  int bn = pick_bn(Ns, d.s_out);
+  if (bn == 256) bn = ((Ns[0] % 192) == 0) ? 192 : 128;
+  bn = env_int("DELIMIT_FWD_BN", bn);
+  return run_vox(ma, mb, p, bn, env_int("DELIMIT_FWD_STAGED", 1) != 0, Y, ldy, st);
 }
 
 cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* dX, int64_t n_vox, int64_t lddy,
@@ -642,7 +716,8 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* 
   p.Y = reinterpret_cast<__nv_bfloat16*>(dX);
   p.bias = nullptr;
   p.err = err;
-  return run_vox(ma, mb, p, pick_bn(Ns, d.s_in), st);
+  return run_vox(ma, mb, p, env_int("DELIMIT_DGRAD_BN", pick_bn(Ns, d.s_in)), env_int("DELIMIT_DGRAD_STAGED", 0) != 0,
+                 dX, lddx, st);
 }
 
 cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float* P, int64_t ldp, int64_t split_stride,
