@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ 
           gs[pp][t] = v;
         }
         for (int idx = threadIdx.x; idx < AB * KMAX; idx += 256) {
-          const int t = idx / KMAX, kk = idx % KMAX, ab = ab0 + t;
+          const int kk = idx / AB, t = idx % AB, ab = ab0 + t;  // consecutive threads read consecutive (a,b)
           ms_[t][kk] = (ab < nab && kk < nk) ? M[((int64_t)s * d.K + k0 + kk) * nab + ab] : 0.f;
         }
         __syncthreads();

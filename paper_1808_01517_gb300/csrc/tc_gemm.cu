@@ -40,7 +40,8 @@ enum : int {
   kErrDrain = 0x500,
 };
 
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // + TMA warp + MMA warp
 constexpr int kBK = 64;            // K rows (or voxels) per stage
 constexpr int kBoxBytes = 64 * 128;  // one 64 x 64 BF16 box, 128-byte rows
 
@@ -119,10 +120,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 4);
+      mbar_init(tempty_bar(b), kEpiWarps);
     }
     mbar_init(drain_bar, 1);
-    mbar_init(stg_ready_bar, 4);
+    mbar_init(stg_ready_bar, kEpiWarps);
     mbar_init(stg_free_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
     const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;  // 16-column chunks 2k + half
     int acc = 0;
     uint32_t acc_phase = 0;
     int it = 0;
@@ -234,24 +236,36 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int64_t vox = (int64_t)mt * 128 + q * 32 + lane;
       const bool vok = vox < p.n_vox;
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        const int nbase = nt * BN + c0;
-        if (nbase >= G.N) break;
-        float bv[16];
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+      for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
+        uint32_t rv[4][16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          bv[j] = (p.bias && nbase + j < G.N) ? __ldg(p.bias + G.y_row0 + nbase + j) : 0.f;
-        float v[16];
-        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c0), v);
-        if (STAGED) {
-          __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(stg_ptr) + (size_t)h * BN * 64;
+        for (int u = 0; u < 4; ++u) {
+          const int c0 = 32 * (k0 + u) + 16 * half;
+          if (c0 < BN && nt * BN + c0 < G.N) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+        }
+        tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) stg[(c0 + j) * 64 + xl] = __float2bfloat16_rn(v[j] + bv[j]);
-        } else {
+        for (int u = 0; u < 4; ++u) {
+          const int c0 = 32 * (k0 + u) + 16 * half;
+          const int nbase = nt * BN + c0;
+          if (c0 < BN && nbase < G.N) {
+            float bv[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = nbase + j;
-            if (n < G.N && vok) p.Y[(G.y_row0 + n) * p.ldy + vox] = __float2bfloat16_rn(v[j] + bv[j]);
+            for (int j = 0; j < 16; ++j)
+              bv[j] = (p.bias && nbase + j < G.N) ? __ldg(p.bias + G.y_row0 + nbase + j) : 0.f;
+            if (STAGED) {
+              __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(stg_ptr) + (size_t)h * BN * 64;
+#pragma unroll
+              for (int j = 0; j < 16; ++j) stg[(c0 + j) * 64 + xl] = __float2bfloat16_rn(__uint_as_float(rv[u][j]) + bv[j]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int n = nbase + j;
+                if (n < G.N && vok)
+                  p.Y[(G.y_row0 + n) * p.ldy + vox] = __float2bfloat16_rn(__uint_as_float(rv[u][j]) + bv[j]);
+              }
+            }
           }
         }
       }
@@ -350,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 4);
+      mbar_init(tempty_bar(b), kEpiWarps);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -443,6 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     wait_drain(drain_bar, 0, p.err, kErrDrain);
   } else if (warp >= 2) {
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;  // 16-column chunks 2k + half
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
@@ -455,15 +470,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int m = mt * 128 + q * 32 + lane;
       float* prow = p.P + (int64_t)split * p.split_stride + (G.m_row0 + m) * p.ldp + G.n_col0;
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        const int nbase = nt * BN + c0;
-        if (nbase >= G.N) break;
-        float v[16];
-        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c0), v);
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+      for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
+        uint32_t rv[4][16];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c0 = 32 * (k0 + u) + 16 * half;
+          if (c0 < BN && nt * BN + c0 < G.N) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+        }
+        tmem_wait_ld();
         if (m < G.M) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (nbase + j < G.N) prow[nbase + j] = v[j];
+          for (int u = 0; u < 4; ++u) {
+            const int nbase = nt * BN + 32 * (k0 + u) + 16 * half;
+            if (32 * (k0 + u) + 16 * half < BN && nbase < G.N) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (nbase + j < G.N) prow[nbase + j] = __uint_as_float(rv[u][j]);
+            }
+          }
         }
       }
       tc_fence_before();

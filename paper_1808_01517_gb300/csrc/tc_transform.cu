@@ -20,7 +20,8 @@ namespace delimit {
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // + TMA warp + MMA warp
 constexpr int kMaxTcGroups = 8;
 constexpr int kAccCols = 256;  // TMEM columns per accumulator buffer
 
@@ -78,12 +79,12 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 4);
+      mbar_init(tempty_bar(b), kEpiWarps);
     }
     mbar_init(bload_bar, 1);
     mbar_init(drain_bar, 1);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(stg_ready_bar(b), 4);
+      mbar_init(stg_ready_bar(b), kEpiWarps);
       mbar_init(stg_free_bar(b), 1);
     }
     *abort_flag = 0;
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
     // storing lane, stg_free (1 arrival) returns it once its store has read it.
     constexpr int ES = OUT_F32 ? 4 : 2;
     const int q = warp & 3;
-    const bool leader = (warp == 2 && lane == 0);
+    const int half = (warp - 2) >> 2;  // which 16-column chunks: 2k + half
     const int h = q >> 1, xl = (q & 1) * 32 + lane;  // voxel half and voxel within the half
     int acc = 0;
     uint32_t acc_phase = 0;
@@ -185,16 +186,34 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       uint8_t* stg = stg_ptr + (size_t)buf * p.stg_bytes + (size_t)h * G.n_out * 64 * ES;
-      for (int c0 = 0; c0 < G.n_out; c0 += 16) {
-        float v[16];
-        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols + c0), v);
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
+      // this warp's chunks: c0 = 16 * (2k + half); up to four loads in flight per wait
+      for (int k0 = 0; 32 * k0 + 16 * half < G.n_out; k0 += 4) {
+        uint32_t rv[4][16];
+        int nld = 0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          if (c0 + j < G.n_out) {
-            if (OUT_F32)
-              reinterpret_cast<float*>(stg)[(c0 + j) * 64 + xl] = v[j];
-            else
-              reinterpret_cast<__nv_bfloat16*>(stg)[(c0 + j) * 64 + xl] = __float2bfloat16_rn(v[j]);
+        for (int u = 0; u < 4; ++u) {
+          const int c0 = 32 * (k0 + u) + 16 * half;
+          if (c0 < G.n_out) {
+            tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+            nld = u + 1;
+          }
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c0 = 32 * (k0 + u) + 16 * half;
+          if (u < nld) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (c0 + j < G.n_out) {
+                const float v = __uint_as_float(rv[u][j]);
+                if (OUT_F32)
+                  reinterpret_cast<float*>(stg)[(c0 + j) * 64 + xl] = v;
+                else
+                  reinterpret_cast<__nv_bfloat16*>(stg)[(c0 + j) * 64 + xl] = __float2bfloat16_rn(v);
+              }
+            }
           }
         }
       }
@@ -225,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
-    if (leader) bulk_wait<0>();
+    if (warp == 2 && lane == 0) bulk_wait<0>();
   }
   tc_fence_before();
   __syncthreads();
