@@ -200,6 +200,26 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* geom, const void
                                     int c_in, int c_out, int64_t ld_in, int64_t ld_out, delimit_dtype act_t,
                                     void* workspace, size_t ws_bytes, void* stream);
 
+/* Same computation as delimit_lsc_forward, for callers that cannot allocate
+ * device memory where they run the layer (inside a region where the CUDA
+ * allocator must not be called, such as a host callback or a stream another
+ * component is capturing; hosts whose allocator owns all device memory; or
+ * deployments with a fixed memory budget), so they cannot supply a workspace.
+ * The paper has no counterpart to this call.
+ * Scratch: a fixed 16 MiB (16777216-byte) device array inside this library,
+ * present on every GPU that loads the library until the process exits.  Sizes
+ * whose forward workspace (delimit_lsc_workspace_size(..., 0)) exceeds it are
+ * rejected with DELIMIT_ERR_WORKSPACE and a message; nothing is allocated,
+ * neither here nor in the kernels it launches.  The first call on a device
+ * (with that device current) resolves the array's device address; make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents (every call rewrites what it reads): calls
+ * that overlap on the GPU (different streams, or host threads without
+ * ordering) race on it and must be serialised by the caller. */
+delimit_status delimit_lsc_forward_noalloc(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
+                                           const float* b, void* sh_out, int64_t n_vox, int c_in, int c_out,
+                                           int64_t ld_in, int64_t ld_out, delimit_dtype act_t, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Errors and version                                                        */
 /* ------------------------------------------------------------------------ */

@@ -62,6 +62,8 @@ SIGNATURES = {
                                       C.c_size_t, _vp]),
     "delimit_lsc_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64,
                                        C.c_int, _vp, C.c_size_t, _vp]),
+    "delimit_lsc_forward_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64, C.c_int,
+                                              _vp]),
     "delimit_device_error": (C.c_int, [_vp, _ip]),
     "delimit_set_tensor_cores": (C.c_int, [C.c_int]),
     "delimit_kernel_launches": (C.c_uint64, []),

@@ -71,6 +71,8 @@ struct Uploader {
 
 }  // namespace
 
+void delimit::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 struct delimit_sh_basis {
   BasisHost h;
   bool on_device = false;

@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace delimit {
 
 constexpr int kMaxGroups = 64;
@@ -83,6 +85,9 @@ cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int m
 // dw[co,s,ci,s',k] = sum_{a,b} M[s][k][a][b] sum_split P[split][(s,co,a)][(s',ci,b)];  db[co,s] = sum_a q[s][a] rowsum
 cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int64_t split_stride, int splits,
                              const float* M, const float* q, float* dw, float* db, cudaStream_t st);
+
+// sets the thread-local message returned by delimit_last_error()
+void set_last_error(const std::string& msg);
 
 // host-side count of kernels launched by the library (instrumentation)
 void count_launch();
