@@ -200,6 +200,36 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* geom, const void
                                     int c_in, int c_out, int64_t ld_in, int64_t ld_out, delimit_dtype act_t,
                                     void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Helpers of the learned network and whole-volume inference (no counterpart */
+/* in the paper beyond its use of the layers inside networks, Sec. 2 and 3)  */
+/* ------------------------------------------------------------------------ */
+
+/* y = x > 0 ? x : slope * x on `rows` feature rows of `n_vox` voxels (activation
+ * between LSC layers, applied to SH coefficients).  x and y may alias. */
+delimit_status delimit_leaky_relu(const void* x, void* y, int64_t rows, int64_t n_vox, int64_t ld_x, int64_t ld_y,
+                                  float slope, delimit_dtype dtype, void* stream);
+/* dx = dy * (y > 0 ? 1 : slope), with y the forward output (it keeps the input's sign). */
+delimit_status delimit_leaky_relu_backward(const void* y, const void* dy, void* dx, int64_t rows, int64_t n_vox,
+                                           int64_t ld_y, int64_t ld_dy, int64_t ld_dx, float slope,
+                                           delimit_dtype dtype, void* stream);
+
+/* Table T5: index[0..*count) = ascending positions i < n with mask[i] != 0 (the
+ * brain-mask voxel list of a volume stored with its last axis fastest).  Device
+ * pointers; *count is written on the device.  index must hold n entries in the
+ * worst case.  Deterministic.  workspace >= delimit_mask_compact_workspace_size(n). */
+size_t delimit_mask_compact_workspace_size(int64_t n);
+delimit_status delimit_mask_compact(const uint8_t* mask, int64_t n, int64_t* index, int64_t* count, void* workspace,
+                                    size_t ws_bytes, void* stream);
+
+/* dst[r, j] = src[r, index[j]] for r < rows, j < n (volume -> masked voxel list);
+ * indices outside [0, n_src) give 0.  scatter is the inverse placement
+ * dst[r, index[j]] = src[r, j] (indices outside [0, n_dst) are skipped). */
+delimit_status delimit_gather_voxels(const void* src, int64_t ld_src, int64_t n_src, int64_t rows, const int64_t* index,
+                                     int64_t n, void* dst, int64_t ld_dst, delimit_dtype dtype, void* stream);
+delimit_status delimit_scatter_voxels(const void* src, int64_t ld_src, int64_t rows, const int64_t* index, int64_t n,
+                                      void* dst, int64_t ld_dst, int64_t n_dst, delimit_dtype dtype, void* stream);
+
 /* Same computation as delimit_lsc_forward, for callers that cannot allocate
  * device memory where they run the layer (inside a region where the CUDA
  * allocator must not be called, such as a host callback or a stream another

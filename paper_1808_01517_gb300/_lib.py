@@ -62,6 +62,12 @@ SIGNATURES = {
                                       C.c_size_t, _vp]),
     "delimit_lsc_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64,
                                        C.c_int, _vp, C.c_size_t, _vp]),
+    "delimit_leaky_relu": (C.c_int, [_vp, _vp, _i64, _i64, _i64, _i64, C.c_float, C.c_int, _vp]),
+    "delimit_leaky_relu_backward": (C.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, C.c_float, C.c_int, _vp]),
+    "delimit_mask_compact_workspace_size": (C.c_size_t, [_i64]),
+    "delimit_mask_compact": (C.c_int, [_vp, _i64, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "delimit_gather_voxels": (C.c_int, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _i64, C.c_int, _vp]),
+    "delimit_scatter_voxels": (C.c_int, [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _i64, C.c_int, _vp]),
     "delimit_lsc_forward_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64, C.c_int,
                                               _vp]),
     "delimit_device_error": (C.c_int, [_vp, _ip]),

@@ -151,6 +151,44 @@ class _LSCFn(torch.autograd.Function):
         return d_in, dw, db, None, None, None
 
 
+def leaky_relu(x: torch.Tensor, slope: float) -> torch.Tensor:
+    x = as_act(x)
+    y = empty_act(x.shape[0], x.shape[1], x.dtype, x.device)
+    L.check(L.get().delimit_leaky_relu(x.data_ptr(), y.data_ptr(), x.shape[0], x.shape[1], x.stride(0), y.stride(0),
+                                       float(slope), _code(x), _stream()), "delimit_leaky_relu")
+    return y
+
+
+class _LeakyFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, slope):
+        y = leaky_relu(x, slope)
+        ctx.slope = slope
+        ctx.save_for_backward(y)
+        return y
+
+    @staticmethod
+    def backward(ctx, g):
+        (y,) = ctx.saved_tensors
+        g = as_act(g.to(y.dtype))
+        dx = empty_act(y.shape[0], y.shape[1], y.dtype, y.device)
+        L.check(L.get().delimit_leaky_relu_backward(y.data_ptr(), g.data_ptr(), dx.data_ptr(), y.shape[0], y.shape[1],
+                                                    y.stride(0), g.stride(0), dx.stride(0), float(ctx.slope), _code(y),
+                                                    _stream()), "delimit_leaky_relu_backward")
+        return dx, None
+
+
+class LeakyReLU(torch.nn.Module):
+    """Leaky ReLU on SH activations, in the library's kernels."""
+
+    def __init__(self, slope: float = 0.1):
+        super().__init__()
+        self.slope = float(slope)
+
+    def forward(self, x):
+        return _LeakyFn.apply(x, self.slope)
+
+
 def _to_rows(x: torch.Tensor):
     """5-D [B, F, H, W, D] -> ([F, B*H*W*D], restore) ; 2-D passes through."""
     if x.dim() == 2:

@@ -165,16 +165,18 @@ def ellipsoid_mask(shape=(145, 174, 145), target_voxels: int = 900_000, seed: in
 
 
 def fibre_signal_torch(dirs, bvals, n_vox: int, *, seed: int = BASE_SEED, sub: int = 0, max_fibres: int = 2,
-                       snr=20.0, device="cuda", dtype=None):
+                       min_fibres: int = 1, snr=20.0, device="cuda", dtype=None, return_clean: bool = False):
     """The same stick + zeppelin + Rician model as :func:`fibre_signal`, drawn on the
     device with a seeded torch generator (for workloads too large to draw on the host).
-    Returns [n_dirs, n_vox] (feature rows x voxel columns), float32 unless ``dtype``."""
+    ``snr`` is a number or a (lo, hi) range drawn uniformly per voxel.  Returns
+    [n_dirs, n_vox] (feature rows x voxel columns), float32 unless ``dtype``; with
+    ``return_clean`` also the noise-free signal."""
     import torch
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed) * 1000003 + int(sub) * 7919 + _TAGS["fibres"])
     g = torch.as_tensor(np.asarray(dirs, np.float64), dtype=torch.float32, device=device)
     b = torch.as_tensor(np.asarray(bvals, np.float64), dtype=torch.float32, device=device)
-    nf = torch.randint(1, max_fibres + 1, (n_vox,), generator=gen, device=device)
+    nf = torch.randint(min_fibres, max_fibres + 1, (n_vox,), generator=gen, device=device)
     u = torch.randn((max_fibres, n_vox, 3), generator=gen, device=device)
     u = u / u.norm(dim=2, keepdim=True)
     e = -torch.log(torch.rand((max_fibres, n_vox), generator=gen, device=device).clamp_min(1e-12))
@@ -187,8 +189,15 @@ def fibre_signal_torch(dirs, bvals, n_vox: int, *, seed: int = BASE_SEED, sub: i
         stick = torch.exp(-b[:, None] * D_PAR * cos2)
         zep = torch.exp(-b[:, None] * (D_PERP + (D_PAR - D_PERP) * cos2))
         s += w[f][None, :] * (nu[f][None, :] * stick + (1 - nu[f][None, :]) * zep)
-    sigma = 1.0 / float(snr)
+    if isinstance(snr, (tuple, list)):
+        sigma = 1.0 / (snr[0] + (snr[1] - snr[0]) * torch.rand((1, n_vox), generator=gen, device=device))
+    else:
+        sigma = 1.0 / float(snr)
     n1 = torch.randn(s.shape, generator=gen, device=device)
     n2 = torch.randn(s.shape, generator=gen, device=device)
     out = torch.sqrt((s + sigma * n1) ** 2 + (sigma * n2) ** 2)
-    return out if dtype is None else out.to(dtype)
+    if dtype is not None:
+        out = out.to(dtype)
+    if return_clean:
+        return out, (s if dtype is None else s.to(dtype))
+    return out
