@@ -65,6 +65,10 @@ typedef enum {
 
 /* create flags */
 #define DELIMIT_HOST_ONLY 1u /* build host FP64 tables only (no device copies, no GPU needed) */
+#define DELIMIT_EVAL_ONLY 2u /* basis for SH2Signal only: no pseudo-inverse (P reads as zero); any
+                                direction count and lambda = 0 allowed.  Signal2SH, its adjoint and
+                                LSC geometries reject such a basis with INVALID_ARG.  SH2Signal in
+                                Sec. 2.2 takes only sh_order and gradients. */
 
 /* LSC shell windows (which input shells s' feed output shell s) */
 #define DELIMIT_WINDOW_SAME 0      /* s' = s (needs as many input as output shells) */

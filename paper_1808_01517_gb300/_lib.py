@@ -32,6 +32,7 @@ ERR_WORKSPACE = 8
 F32 = 0
 BF16 = 1
 HOST_ONLY = 1
+EVAL_ONLY = 2
 WINDOW_SAME, WINDOW_ADJACENT, WINDOW_ALL = 0, 1, -1
 WINDOWS = {"same": WINDOW_SAME, "adjacent": WINDOW_ADJACENT, "all": WINDOW_ALL}
 
@@ -118,13 +119,14 @@ def _dptr(a: np.ndarray):
 class SHBasis:
     """Handle of ``delimit_sh_basis`` (per-shell B_s and P_s of one gradient table)."""
 
-    def __init__(self, dirs, bvals, order: int, lam: float = 0.0, host_only: bool = False):
+    def __init__(self, dirs, bvals, order: int, lam: float = 0.0, host_only: bool = False, eval_only: bool = False):
         lib = get()
         self._dirs = np.ascontiguousarray(np.asarray(dirs, np.float64).reshape(-1, 3))
         self._bvals = np.ascontiguousarray(np.asarray(bvals, np.float64).reshape(-1))
         h = _vp()
         check(lib.delimit_sh_basis_create(_dptr(self._dirs), _dptr(self._bvals), self._dirs.shape[0], int(order),
-                                          float(lam), HOST_ONLY if host_only else 0, C.byref(h)),
+                                          float(lam), (HOST_ONLY if host_only else 0) | (EVAL_ONLY if eval_only else 0),
+                                          C.byref(h)),
               "delimit_sh_basis_create")
         self.handle = h
         self.order = int(order)

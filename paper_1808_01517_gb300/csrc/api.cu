@@ -140,7 +140,7 @@ delimit_status delimit_sh_basis_create(const double* dirs, const double* bvals, 
   delimit_sh_basis* b = new (std::nothrow) delimit_sh_basis();
   if (!b) return fail(DELIMIT_ERR_OOM, "host allocation failed");
   std::string err;
-  const int rc = build_basis(dirs, bvals, n_dirs, order, lambda, b->h, err);
+  const int rc = build_basis(dirs, bvals, n_dirs, order, lambda, b->h, err, !(flags & DELIMIT_EVAL_ONLY));
   if (rc) {
     delete b;
     return fail(rc == 2 ? DELIMIT_ERR_RANK_DEFICIENT : DELIMIT_ERR_INVALID_ARG, err);
@@ -259,6 +259,8 @@ static delimit_status run_transform(const delimit_sh_basis* b, const void* X, vo
                                     TransformKind kind) {
   if (!b) return fail(DELIMIT_ERR_INVALID_ARG, "basis is NULL");
   if (!b->on_device) return fail(DELIMIT_ERR_INVALID_ARG, "basis was created with DELIMIT_HOST_ONLY");
+  if (!b->h.has_pinv && (kind == kS2SH || kind == kS2SH_BWD))
+    return fail(DELIMIT_ERR_INVALID_ARG, "basis was created with DELIMIT_EVAL_ONLY (no pseudo-inverse)");
   if (n_vox < 0 || C < 1 || C > 65535) return fail(DELIMIT_ERR_INVALID_ARG, "need n_vox >= 0 and 1 <= channels <= 65535");
   if (!valid_dtype(in_t) || !valid_dtype(out_t)) return fail(DELIMIT_ERR_INVALID_ARG, "bad dtype");
   if (n_vox == 0) return DELIMIT_OK;
@@ -338,6 +340,7 @@ delimit_status delimit_lsc_geometry_create(const delimit_sh_basis* ob, int order
   if (!out) return fail(DELIMIT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!ob) return fail(DELIMIT_ERR_INVALID_ARG, "out_basis is NULL");
+  if (!ob->h.has_pinv) return fail(DELIMIT_ERR_INVALID_ARG, "out_basis was created with DELIMIT_EVAL_ONLY");
   delimit_lsc_geometry* g = new (std::nothrow) delimit_lsc_geometry();
   if (!g) return fail(DELIMIT_ERR_OOM, "host allocation failed");
   std::string err;

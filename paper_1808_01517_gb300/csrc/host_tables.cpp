@@ -115,7 +115,7 @@ static bool regularised_pinv(const std::vector<double>& B, int m, int N, int ord
 }
 
 int build_basis(const double* dirs, const double* bvals, int n, int order, double lambda, BasisHost& out,
-                std::string& err) {
+                std::string& err, bool need_pinv) {
   char buf[256];
   const int N = sh_ncoef(order);
   if (N < 0 || order > 16) {
@@ -153,6 +153,7 @@ int build_basis(const double* dirs, const double* bvals, int n, int order, doubl
   out.N = N;
   out.n_dirs = n;
   out.lambda = lambda;
+  out.has_pinv = need_pinv;
   int off = 0;
   for (auto& kv : groups) {
     ShellHost sh;
@@ -167,7 +168,9 @@ int build_basis(const double* dirs, const double* bvals, int n, int order, doubl
       for (int k = 0; k < 3; ++k) sh.dirs[3 * i + k] = g[k];
       sh_eval(order, g, &sh.B[size_t(i) * N]);
     }
-    if (!regularised_pinv(sh.B, sh.m, N, order, lambda, sh.P)) {
+    if (!need_pinv) {
+      sh.P.assign(size_t(N) * sh.m, 0.0);
+    } else if (!regularised_pinv(sh.B, sh.m, N, order, lambda, sh.P)) {
       std::snprintf(buf, sizeof buf,
                     "shell b=%lld: normal matrix not positive definite (%d directions, %d coefficients, "
                     "lambda=%g)",

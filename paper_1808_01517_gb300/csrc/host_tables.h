@@ -24,12 +24,14 @@ struct ShellHost {
 struct BasisHost {
   int order = 0, N = 0, n_dirs = 0;
   double lambda = 0;
+  bool has_pinv = true;
   std::vector<ShellHost> shells;
 };
 
 // Returns 0 on success, 1 invalid argument, 2 rank deficient; err gets a message.
+// need_pinv = false skips the pseudo-inverse (P is left zero): an evaluation-only basis.
 int build_basis(const double* dirs, const double* bvals, int n, int order, double lambda, BasisHost& out,
-                std::string& err);
+                std::string& err, bool need_pinv = true);
 
 struct LscShellHost {
   std::vector<double> kpts;       // m x K x 3

@@ -226,7 +226,7 @@ class SH2Signal(torch.nn.Module):
         super().__init__()
         g = np.asarray(gradients, np.float64).reshape(-1, 3)
         b = np.full(g.shape[0], 1000.0) if bvals is None else np.asarray(bvals, np.float64)
-        self.basis = L.SHBasis(g, b, sh_order, 0.0)
+        self.basis = L.SHBasis(g, b, sh_order, 0.0, eval_only=True)
         self.channels, self.out_dtype = channels, out_dtype
 
     def forward(self, sh):

@@ -139,3 +139,14 @@ def test_workspace_size_is_monotone(table3):
     b = lg.workspace_size(65536, 16, 64, L.BF16, True)
     assert 0 < a < b
     assert lg.workspace_size(65536, 0, 64, L.BF16, False) == 0
+
+
+def test_eval_only_basis():
+    g = synth.hemisphere_directions(30, seed=8)
+    b = np.full(30, 1000.0)
+    lb = L.SHBasis(g, b, 8, 0.0, host_only=True, eval_only=True)  # 30 directions < 45 coefficients
+    B, P, _ = lb.tables(0)
+    np.testing.assert_allclose(B, osh.real_sh(8, g), atol=1e-12)
+    assert np.all(P == 0)
+    with pytest.raises(L.DelimitError):
+        L.LSCGeometry(lb, 8, 1, 0.4, 2, 6, "same", host_only=True)
