@@ -119,56 +119,59 @@ cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_
 template <typename TW>
 __global__ void __launch_bounds__(256) build_w_tiled_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
                                                             const float* __restrict__ M, TW* __restrict__ W) {
-  constexpr int PT = 32, AB = 128, KMAX = 64;
-  __shared__ float ws_[PT][KMAX + 1];
-  __shared__ float ms_[KMAX][AB];
+  // block: 64 channel pairs x 64 (a,b) entries; thread: 4 pairs x 4 entries
+  constexpr int PT = 64, AB = 64, KC = 64;
+  __shared__ __align__(16) float ws_[KC][PT + 4];  // padded: 4-way instead of 32-way conflicts on fill
+  __shared__ __align__(16) float ms_[KC][AB];
   const int pair = blockIdx.z;  // s * s_in + s'
   const int s = pair / d.s_in, sp = pair % d.s_in;
   if (sp < d.win_lo[s] || sp >= d.win_hi[s]) return;
   const int nab = d.n_out * d.n_in, npairs = d.c_out * d.c_in;
   const int p0 = blockIdx.y * PT, ab0 = blockIdx.x * AB;
-  if (p0 >= npairs || ab0 >= nab) return;
   const float* Ms = M + (int64_t)s * d.K * nab;
-  float acc[PT * AB / 256];
-#pragma unroll
-  for (int i = 0; i < PT * AB / 256; ++i) acc[i] = 0.f;
-  for (int k0 = 0; k0 < d.K; k0 += KMAX) {
-    const int nk = min(KMAX, d.K - k0);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < d.K; k0 += KC) {
+    const int nk = min(KC, d.K - k0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < PT * KMAX; idx += 256) {
-      const int pp = idx / KMAX, kk = idx % KMAX, pr = p0 + pp;
+    for (int idx = threadIdx.x; idx < PT * KC; idx += 256) {
+      const int kk = idx % KC, pp = idx / KC, pr = p0 + pp;  // consecutive threads: consecutive k of one pair
       float v = 0.f;
       if (pr < npairs && kk < nk) {
         const int co = pr / d.c_in, ci = pr % d.c_in;
         v = w[((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K + k0 + kk];
       }
-      ws_[pp][kk] = v;
+      ws_[kk][pp] = v;
     }
-    for (int idx = threadIdx.x; idx < KMAX * AB; idx += 256) {
+    for (int idx = threadIdx.x; idx < KC * AB; idx += 256) {
       const int kk = idx / AB, aa = idx % AB;
       ms_[kk][aa] = (kk < nk && ab0 + aa < nab) ? Ms[(int64_t)(k0 + kk) * nab + ab0 + aa] : 0.f;
     }
     __syncthreads();
-    // thread: column ab0 + (tid % 128), pairs (tid / 128) + 2 j
-    const int col = threadIdx.x % AB, pr0 = threadIdx.x / AB;
     for (int kk = 0; kk < nk; ++kk) {
-      const float mv = ms_[kk][col];
+      const float4 a4 = *reinterpret_cast<const float4*>(&ws_[kk][ty * 4]);
+      const float4 m4 = *reinterpret_cast<const float4*>(&ms_[kk][tx * 4]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, mv[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
-      for (int j = 0; j < PT * AB / 256; ++j) acc[j] = fmaf(ws_[pr0 + 2 * j][kk], mv, acc[j]);
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], mv[j], acc[i][j]);
     }
   }
-  const int col = threadIdx.x % AB, pr0 = threadIdx.x / AB;
-  const int ab = ab0 + col;
-  if (ab >= nab) return;
-  const int aa = ab / d.n_in, bb = ab % d.n_in;
 #pragma unroll
-  for (int j = 0; j < PT * AB / 256; ++j) {
-    const int pr = p0 + pr0 + 2 * j;
+  for (int i = 0; i < 4; ++i) {
+    const int pr = p0 + ty * 4 + i;
     if (pr >= npairs) continue;
     const int co = pr / d.c_in, ci = pr % d.c_in;
-    const int64_t r = ((int64_t)s * d.c_out + co) * d.n_out + aa;
-    const int64_t c = (int64_t)sp * d.in_blk + (int64_t)ci * d.n_in + bb;
-    stf(W + r * d.ldW + c, acc[j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ab = ab0 + tx * 4 + j;
+      if (ab >= nab) continue;
+      const int aa = ab / d.n_in, bb = ab % d.n_in;
+      const int64_t r = ((int64_t)s * d.c_out + co) * d.n_out + aa;
+      const int64_t c = (int64_t)sp * d.in_blk + (int64_t)ci * d.n_in + bb;
+      stf(W + r * d.ldW + c, acc[i][j]);
+    }
   }
 }
 
@@ -217,7 +220,7 @@ cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, con
   cudaError_t e = cudaMemsetAsync(W, 0, (size_t)d.rows_out * d.ldW * es, st);
   if (e != cudaSuccess) return e;
   const int nab = d.n_out * d.n_in, npairs = d.c_out * d.c_in;
-  dim3 grid((unsigned)((nab + 127) / 128), (unsigned)((npairs + 31) / 32), (unsigned)(d.s_out * d.s_in));
+  dim3 grid((unsigned)((nab + 63) / 64), (unsigned)((npairs + 63) / 64), (unsigned)(d.s_out * d.s_in));
   dim3 tgrid((unsigned)((d.ldWt + 31) / 32), (unsigned)((d.rows_in + 31) / 32));
   if (w_t == 0) {
     { build_w_tiled_kernel<float><<<grid, 256, 0, st>>>(d, w, M, (float*)W); count_launch(); }
@@ -397,62 +400,58 @@ cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int m
 __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ LscDims d, const float* __restrict__ P,
                                                         int64_t ldp, int64_t split_stride, int splits,
                                                         const float* __restrict__ M, float* __restrict__ dw) {
-  constexpr int PT = 32, AB = 128, KMAX = 64;
-  __shared__ float gs[PT][AB + 1];
-  __shared__ float ms_[AB][KMAX + 1];
+  // block: 64 channel pairs x 64 kernel points; thread: 4 pairs x 4 points; (a,b) walked in chunks of 32
+  constexpr int PT = 64, KT = 64, AB = 32;
+  __shared__ __align__(16) float gs[AB][PT + 4];
+  __shared__ __align__(16) float ms_[AB][KT + 4];
   const int pair = blockIdx.z;
   const int s = pair / d.s_in, sp = pair % d.s_in;
   const int npairs = d.c_out * d.c_in, nab = d.n_out * d.n_in;
-  const int p0 = blockIdx.y * PT;
-  if (p0 >= npairs) return;
+  const int p0 = blockIdx.y * PT, k0 = blockIdx.x * KT;
   const bool in_win = sp >= d.win_lo[s] && sp < d.win_hi[s];
-  // outputs of this thread: (pair p0 + pp, k) for idx = tid + 256 j
-  constexpr int OPT = (PT * KMAX + 255) / 256;
-  float acc[OPT];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4] = {};
+  if (in_win) {
+    for (int ab0 = 0; ab0 < nab; ab0 += AB) {
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < PT * AB; idx += 256) {
+        const int t = idx % AB, pp = idx / AB, pr = p0 + pp, ab = ab0 + t;
+        float v = 0.f;
+        if (pr < npairs && ab < nab) {
+          const int co = pr / d.c_in, ci = pr % d.c_in, aa = ab / d.n_in, bb = ab % d.n_in;
+          const int64_t off =
+              (((int64_t)s * d.c_out + co) * d.n_out + aa) * ldp + ((int64_t)sp * d.c_in + ci) * d.n_in + bb;
+          for (int z = 0; z < splits; ++z) v += P[z * split_stride + off];
+        }
+        gs[t][pp] = v;
+      }
+      for (int idx = threadIdx.x; idx < KT * AB; idx += 256) {
+        const int t = idx % AB, kk = idx / AB, ab = ab0 + t, k = k0 + kk;
+        ms_[t][kk] = (ab < nab && k < d.K) ? M[((int64_t)s * d.K + k) * nab + ab] : 0.f;
+      }
+      __syncthreads();
+      const int nt = min(AB, nab - ab0);
+      for (int t = 0; t < nt; ++t) {
+        const float4 g4 = *reinterpret_cast<const float4*>(&gs[t][ty * 4]);
+        const float4 m4 = *reinterpret_cast<const float4*>(&ms_[t][tx * 4]);
+        const float gv[4] = {g4.x, g4.y, g4.z, g4.w}, mv[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
-  for (int j = 0; j < OPT; ++j) acc[j] = 0.f;
-  for (int k0 = 0; k0 < d.K; k0 += KMAX) {
-    const int nk = min(KMAX, d.K - k0);
-    if (in_win) {
-      for (int ab0 = 0; ab0 < nab; ab0 += AB) {
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < PT * AB; idx += 256) {
-          const int pp = idx / AB, t = idx % AB, pr = p0 + pp, ab = ab0 + t;
-          float v = 0.f;
-          if (pr < npairs && ab < nab) {
-            const int co = pr / d.c_in, ci = pr % d.c_in, aa = ab / d.n_in, bb = ab % d.n_in;
-            const int64_t off = (((int64_t)s * d.c_out + co) * d.n_out + aa) * ldp + ((int64_t)sp * d.c_in + ci) * d.n_in + bb;
-            for (int z = 0; z < splits; ++z) v += P[z * split_stride + off];
-          }
-          gs[pp][t] = v;
-        }
-        for (int idx = threadIdx.x; idx < AB * KMAX; idx += 256) {
-          const int kk = idx / AB, t = idx % AB, ab = ab0 + t;  // consecutive threads read consecutive (a,b)
-          ms_[t][kk] = (ab < nab && kk < nk) ? M[((int64_t)s * d.K + k0 + kk) * nab + ab] : 0.f;
-        }
-        __syncthreads();
-        const int nt = min(AB, nab - ab0);
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < OPT; ++j) {
-          const int idx = threadIdx.x + 256 * j;
-          const int pp = idx / KMAX, kk = idx % KMAX;
-          if (pp < PT) {
-            float a = acc[j];
-            for (int t = 0; t < nt; ++t) a = fmaf(gs[pp][t], ms_[t][kk], a);
-            acc[j] = a;
-          }
-        }
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(gv[i], mv[j], acc[i][j]);
       }
     }
+  }
 #pragma unroll
-    for (int j = 0; j < OPT; ++j) {
-      const int idx = threadIdx.x + 256 * j;
-      const int pp = idx / KMAX, kk = idx % KMAX, pr = p0 + pp;
-      if (pp < PT && kk < nk && pr < npairs) {
-        const int co = pr / d.c_in, ci = pr % d.c_in;
-        dw[((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K + k0 + kk] = in_win ? acc[j] : 0.f;
-      }
-      acc[j] = 0.f;
+  for (int i = 0; i < 4; ++i) {
+    const int pr = p0 + ty * 4 + i;
+    if (pr >= npairs) continue;
+    const int co = pr / d.c_in, ci = pr % d.c_in;
+    float* out = dw + ((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + tx * 4 + j;
+      if (k < d.K) out[k] = in_win ? acc[i][j] : 0.f;
     }
   }
 }
@@ -476,7 +475,7 @@ __global__ void reduce_db_kernel(const __grid_constant__ LscDims d, const float*
 cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int64_t split_stride, int splits,
                              const float* M, const float* q, float* dw, float* db, cudaStream_t st) {
   if (dw) {
-    dim3 grid(1, (unsigned)((d.c_out * d.c_in + 31) / 32), (unsigned)(d.s_out * d.s_in));
+    dim3 grid((unsigned)((d.K + 63) / 64), (unsigned)((d.c_out * d.c_in + 63) / 64), (unsigned)(d.s_out * d.s_in));
     { reduce_dw_kernel<<<grid, 256, 0, st>>>(d, P, ldp, split_stride, splits, M, dw); count_launch(); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
