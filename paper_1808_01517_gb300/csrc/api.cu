@@ -471,7 +471,7 @@ namespace {
 struct LscPlan {
   LscDims d;
   size_t w_bytes;       // one of W / Wt
-  size_t off_W, off_Wt, off_bias, off_P, total_fwd, total_bwd;
+  size_t off_W, off_Wt, off_bias, off_P, off_dwp, total_fwd, total_bwd;
   int splits;
   int64_t vox_per_split;
   bool tc;              // tensor-core GEMMs
@@ -517,7 +517,8 @@ bool make_plan(const delimit_lsc_geometry* g, int64_t n_vox, int c_in, int c_out
   p.total_fwd = p.off_bias + align_up(size_t(p.d.rows_out) * 4, 256);
   p.splits = wgrad_splits(p.d, std::max<int64_t>(n_vox, 1), &p.vox_per_split);
   p.off_P = p.total_fwd;
-  p.total_bwd = p.off_P + align_up(size_t(p.splits) * size_t(p.d.rows_out) * size_t(p.d.rows_in + 1) * 4, 256);
+  p.off_dwp = p.off_P + align_up(size_t(p.splits) * size_t(p.d.rows_out) * size_t(p.d.rows_in + 1) * 4, 256);
+  p.total_bwd = p.off_dwp + align_up(reduce_dw_scratch_floats(p.d) * 4, 256);
   p.tc = false;
   return true;
 }
@@ -696,7 +697,8 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
       e = launch_wgrad_simt(a, d.s_out, per_out, maxN, p.splits, int(act_t), cs);
       if (e != cudaSuccess) return cuda_fail(e, "LSC weight-gradient launch");
     }
-    e = launch_reduce_dw(d, P, ldp, split_stride, p.splits, g->d_M, g->d_q, dw, db, cs);
+    e = launch_reduce_dw(d, P, ldp, split_stride, p.splits, g->d_M, g->d_q, dw, db,
+                         reinterpret_cast<float*>(base + p.off_dwp), cs);
     if (e != cudaSuccess) return cuda_fail(e, "dw/db reduction launch");
   }
   return DELIMIT_OK;

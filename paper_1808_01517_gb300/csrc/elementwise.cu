@@ -24,6 +24,64 @@ __global__ void leaky_kernel(const T* x, T* y, int64_t rows, int64_t n, int64_t 
   }
 }
 
+// 16-byte vectors of BF16 (rows 16-byte aligned); one grid row per feature row
+__global__ void leaky_bf16x8_kernel(const __nv_bfloat16* x, __nv_bfloat16* y, int64_t n, int64_t ldx, int64_t ldy,
+                                    float slope) {
+  const int64_t r = blockIdx.y;
+  const int64_t n8 = n / 8;
+  const uint4* xr = reinterpret_cast<const uint4*>(x + r * ldx);
+  uint4* yr = reinterpret_cast<uint4*>(y + r * ldy);
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n8; v += (int64_t)gridDim.x * blockDim.x) {
+    uint4 u = xr[v];
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 f = __bfloat1622float2(h[i]);
+      f.x = f.x > 0.f ? f.x : slope * f.x;
+      f.y = f.y > 0.f ? f.y : slope * f.y;
+      h[i] = __float22bfloat162_rn(f);
+    }
+    yr[v] = u;
+  }
+  for (int64_t v = n8 * 8 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const float a = __bfloat162float(x[r * ldx + v]);
+    y[r * ldy + v] = __float2bfloat16_rn(a > 0.f ? a : slope * a);
+  }
+}
+
+__global__ void leaky_bwd_bf16x8_kernel(const __nv_bfloat16* __restrict__ y, const __nv_bfloat16* __restrict__ dy,
+                                        __nv_bfloat16* __restrict__ dx, int64_t n, int64_t ldy, int64_t lddy,
+                                        int64_t lddx, float slope) {
+  const int64_t r = blockIdx.y;
+  const int64_t n8 = n / 8;
+  const uint4* yr = reinterpret_cast<const uint4*>(y + r * ldy);
+  const uint4* gr = reinterpret_cast<const uint4*>(dy + r * lddy);
+  uint4* dr = reinterpret_cast<uint4*>(dx + r * lddx);
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n8; v += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 uy = yr[v];
+    uint4 ug = gr[v];
+    const __nv_bfloat162* hy = reinterpret_cast<const __nv_bfloat162*>(&uy);
+    __nv_bfloat162* hg = reinterpret_cast<__nv_bfloat162*>(&ug);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 a = __bfloat1622float2(hy[i]);
+      float2 g = __bfloat1622float2(hg[i]);
+      g.x = a.x > 0.f ? g.x : slope * g.x;
+      g.y = a.y > 0.f ? g.y : slope * g.y;
+      hg[i] = __float22bfloat162_rn(g);
+    }
+    dr[v] = ug;
+  }
+  for (int64_t v = n8 * 8 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const float a = __bfloat162float(y[r * ldy + v]), g = __bfloat162float(dy[r * lddy + v]);
+    dx[r * lddx + v] = __float2bfloat16_rn(a > 0.f ? g : slope * g);
+  }
+}
+
+static bool al16(const void* p, int64_t ld) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && (ld * 2) % 16 == 0;
+}
+
 // dx = dy * (y > 0 ? 1 : slope): the forward output y carries the sign of its input
 template <typename T>
 __global__ void leaky_bwd_kernel(const T* __restrict__ y, const T* __restrict__ dy, T* __restrict__ dx, int64_t rows,
@@ -153,6 +211,9 @@ delimit_status delimit_leaky_relu(const void* x, void* y, int64_t rows, int64_t 
   dim3 grid(grid_x(n_vox), (unsigned)rows);
   if (t == DELIMIT_F32) {
     leaky_kernel<float><<<grid, 256, 0, st>>>((const float*)x, (float*)y, rows, n_vox, ld_x, ld_y, slope);
+  } else if (al16(x, ld_x) && al16(y, ld_y)) {
+    dim3 g8(grid_x((n_vox + 7) / 8), (unsigned)rows);
+    leaky_bf16x8_kernel<<<g8, 256, 0, st>>>((const __nv_bfloat16*)x, (__nv_bfloat16*)y, n_vox, ld_x, ld_y, slope);
   } else {
     leaky_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16*)x, (__nv_bfloat16*)y, rows, n_vox, ld_x,
                                                       ld_y, slope);
@@ -173,6 +234,10 @@ delimit_status delimit_leaky_relu_backward(const void* y, const void* dy, void* 
   if (t == DELIMIT_F32) {
     leaky_bwd_kernel<float><<<grid, 256, 0, st>>>((const float*)y, (const float*)dy, (float*)dx, rows, n_vox, ld_y,
                                                   ld_dy, ld_dx, slope);
+  } else if (al16(y, ld_y) && al16(dy, ld_dy) && al16(dx, ld_dx)) {
+    dim3 g8(grid_x((n_vox + 7) / 8), (unsigned)rows);
+    leaky_bwd_bf16x8_kernel<<<g8, 256, 0, st>>>((const __nv_bfloat16*)y, (const __nv_bfloat16*)dy, (__nv_bfloat16*)dx,
+                                                n_vox, ld_y, ld_dy, ld_dx, slope);
   } else {
     leaky_bwd_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16*)y, (const __nv_bfloat16*)dy,
                                                           (__nv_bfloat16*)dx, rows, n_vox, ld_y, ld_dy, ld_dx, slope);

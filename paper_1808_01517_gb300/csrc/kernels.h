@@ -83,8 +83,10 @@ cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int m
                               cudaStream_t st);
 
 // dw[co,s,ci,s',k] = sum_{a,b} M[s][k][a][b] sum_split P[split][(s,co,a)][(s',ci,b)];  db[co,s] = sum_a q[s][a] rowsum
+// scratch: reduce_dw_scratch_floats(d) floats of partial sums
+size_t reduce_dw_scratch_floats(const LscDims& d);
 cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int64_t split_stride, int splits,
-                             const float* M, const float* q, float* dw, float* db, cudaStream_t st);
+                             const float* M, const float* q, float* dw, float* db, float* scratch, cudaStream_t st);
 
 // sets the thread-local message returned by delimit_last_error()
 void set_last_error(const std::string& msg);

@@ -6,6 +6,7 @@
 //   row_gemm_simt    LSC forward / input-gradient GEMM over voxels
 //   wgrad_simt       LSC weight-gradient GEMM (reduction over voxels, split, deterministic)
 //   reduce_dw        dW -> kernel-point weights dw and bias gradient db
+#include <algorithm>
 #include <atomic>
 
 #include "kernels.h"
@@ -109,99 +110,99 @@ cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_
 }
 
 // ---------------------------------------------------------------------------
-// Collapsed LSC operator.  For every windowed shell pair (s, s') the block
+// Collapsed LSC operator.  For every shell pair (s, s') in the window
 //   W[(s,co,a)][(s',ci,b)] = sum_k w[co,s,ci,s',k] M_s[k][a][b]
-// is a product of a [c_out*c_in x K] and a [K x n_out*n_in] matrix; blocks
-// of 32 channel pairs x 128 (a,b) entries keep both factors in shared memory.
-// W is cleared first (outside-window blocks and padding stay zero), then Wt is
-// written by a tiled transpose that also zeroes its padding columns.
+// One block: 8 channel pairs (co, ci) of one shell pair and all n_out x n_in
+// entries (a, b).  M_s[k] rows stream from L2 (k outer); each thread keeps
+// 8 pairs x ceil(n_out*n_in / 256) accumulators.  The finished blocks go to
+// shared memory and are written to W (runs along b) and Wt (runs along a).
+// Shell pairs outside the window write zeros.
 // ---------------------------------------------------------------------------
-template <typename TW>
-__global__ void __launch_bounds__(256) build_w_tiled_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
-                                                            const float* __restrict__ M, TW* __restrict__ W) {
-  // block: 64 channel pairs x 64 (a,b) entries; thread: 4 pairs x 4 entries
-  constexpr int PT = 64, AB = 64, KC = 64;
-  __shared__ __align__(16) float ws_[KC][PT + 4];  // padded: 4-way instead of 32-way conflicts on fill
-  __shared__ __align__(16) float ms_[KC][AB];
-  const int pair = blockIdx.z;  // s * s_in + s'
-  const int s = pair / d.s_in, sp = pair % d.s_in;
-  if (sp < d.win_lo[s] || sp >= d.win_hi[s]) return;
-  const int nab = d.n_out * d.n_in, npairs = d.c_out * d.c_in;
-  const int p0 = blockIdx.y * PT, ab0 = blockIdx.x * AB;
-  const float* Ms = M + (int64_t)s * d.K * nab;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < d.K; k0 += KC) {
-    const int nk = min(KC, d.K - k0);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < PT * KC; idx += 256) {
-      const int kk = idx % KC, pp = idx / KC, pr = p0 + pp;  // consecutive threads: consecutive k of one pair
-      float v = 0.f;
-      if (pr < npairs && kk < nk) {
-        const int co = pr / d.c_in, ci = pr % d.c_in;
-        v = w[((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K + k0 + kk];
-      }
-      ws_[kk][pp] = v;
-    }
-    for (int idx = threadIdx.x; idx < KC * AB; idx += 256) {
-      const int kk = idx / AB, aa = idx % AB;
-      ms_[kk][aa] = (kk < nk && ab0 + aa < nab) ? Ms[(int64_t)(k0 + kk) * nab + ab0 + aa] : 0.f;
-    }
-    __syncthreads();
-    for (int kk = 0; kk < nk; ++kk) {
-      const float4 a4 = *reinterpret_cast<const float4*>(&ws_[kk][ty * 4]);
-      const float4 m4 = *reinterpret_cast<const float4*>(&ms_[kk][tx * 4]);
-      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, mv[4] = {m4.x, m4.y, m4.z, m4.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], mv[j], acc[i][j]);
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int pr = p0 + ty * 4 + i;
-    if (pr >= npairs) continue;
-    const int co = pr / d.c_in, ci = pr % d.c_in;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int ab = ab0 + tx * 4 + j;
-      if (ab >= nab) continue;
-      const int aa = ab / d.n_in, bb = ab % d.n_in;
-      const int64_t r = ((int64_t)s * d.c_out + co) * d.n_out + aa;
-      const int64_t c = (int64_t)sp * d.in_blk + (int64_t)ci * d.n_in + bb;
-      stf(W + r * d.ldW + c, acc[i][j]);
-    }
-  }
-}
+constexpr int kBwPairs = 8, kBwMaxPer = 8, kBwChunk = 256 * kBwMaxPer;  // (a,b) entries per block
 
-// Wt[c][oc] = W[row(oc)][col(c)] over the padded index space of Wt (32 x 32 tiles).
 template <typename TW>
-__global__ void __launch_bounds__(256) transpose_w_kernel(const __grid_constant__ LscDims d, const TW* __restrict__ W,
-                                                          TW* __restrict__ Wt) {
-  __shared__ float tile[32][33];
-  const int per_in = d.c_in * d.n_in, per_out = d.c_out * d.n_out;
-  const int64_t oc0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  // read: W rows = output rows of the Wt columns oc0.., W columns = padded input columns of Wt rows c0..
-  for (int i = ty; i < 32; i += 8) {
-    const int64_t oc = oc0 + i;  // Wt column -> W row
-    const int64_t c = c0 + tx;   // Wt row (input row) -> W column
-    float v = 0.f;
-    if (oc < d.ldWt && c < d.rows_in) {
-      const int64_t s = oc / d.out_blk, rl = oc % d.out_blk;
-      if (rl < per_out) {
-        const int64_t wrow = s * per_out + rl;
-        const int64_t wcol = (c / per_in) * d.in_blk + c % per_in;
-        v = ldf(W + wrow * d.ldW + wcol);
+__global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
+                                                      const float* __restrict__ M, TW* __restrict__ W,
+                                                      TW* __restrict__ Wt) {
+  extern __shared__ float blk[];  // [kBwPairs][kBwChunk]
+  __shared__ float wk[kBwPairs][64];
+  const int pair = blockIdx.y;  // s * s_in + s'
+  const int s = pair / d.s_in, sp = pair % d.s_in;
+  const bool in_win = sp >= d.win_lo[s] && sp < d.win_hi[s];
+  const int nab = d.n_out * d.n_in, npairs = d.c_out * d.c_in;
+  const int p0 = blockIdx.x * kBwPairs;
+  const int np = min(kBwPairs, npairs - p0);
+  const int ab0 = blockIdx.z * kBwChunk, nabc = min(kBwChunk, nab - ab0);  // this block's (a,b) range
+  const float* Ms = M + (int64_t)s * d.K * nab;
+  float acc[kBwPairs][kBwMaxPer];
+#pragma unroll
+  for (int p = 0; p < kBwPairs; ++p)
+#pragma unroll
+    for (int e = 0; e < kBwMaxPer; ++e) acc[p][e] = 0.f;
+  if (in_win) {
+    for (int k0 = 0; k0 < d.K; k0 += 64) {
+      const int nk = min(64, d.K - k0);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < kBwPairs * 64; idx += 256) {
+        const int pp = idx / 64, kk = idx % 64, pr = p0 + pp;
+        float v = 0.f;
+        if (pp < np && kk < nk) {
+          const int co = pr / d.c_in, ci = pr % d.c_in;
+          v = w[((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K + k0 + kk];
+        }
+        wk[pp][kk] = v;
+      }
+      __syncthreads();
+      for (int kk = 0; kk < nk; ++kk) {
+        const float* mk = Ms + (int64_t)(k0 + kk) * nab;
+        float mv[kBwMaxPer];
+#pragma unroll
+        for (int e = 0; e < kBwMaxPer; ++e) {
+          const int t = threadIdx.x + 256 * e;
+          mv[e] = t < nabc ? __ldg(mk + ab0 + t) : 0.f;
+        }
+#pragma unroll
+        for (int p = 0; p < kBwPairs; ++p) {
+          const float wv = wk[p][kk];
+#pragma unroll
+          for (int e = 0; e < kBwMaxPer; ++e) acc[p][e] = fmaf(wv, mv[e], acc[p][e]);
+        }
       }
     }
-    tile[i][tx] = v;
   }
   __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int64_t c = c0 + i, oc = oc0 + tx;
-    if (c < d.rows_in && oc < d.ldWt) stf(Wt + c * d.ldWt + oc, tile[tx][i]);
+#pragma unroll
+  for (int p = 0; p < kBwPairs; ++p)
+#pragma unroll
+    for (int e = 0; e < kBwMaxPer; ++e) {
+      const int t = threadIdx.x + 256 * e;
+      if (t < nabc) blk[p * kBwChunk + t] = acc[p][e];
+    }
+  __syncthreads();
+  // W: row (s, co, a), columns s'*in_blk + ci*n_in + b: consecutive threads along b
+  for (int idx = threadIdx.x; idx < np * nabc; idx += 256) {
+    const int p = idx / nabc, t = idx % nabc, pr = p0 + p, ab = ab0 + t;
+    const int co = pr / d.c_in, ci = pr % d.c_in, aa = ab / d.n_in, bb = ab % d.n_in;
+    const int64_t r = ((int64_t)s * d.c_out + co) * d.n_out + aa;
+    stf(W + r * d.ldW + (int64_t)sp * d.in_blk + (int64_t)ci * d.n_in + bb, blk[p * kBwChunk + t]);
+  }
+  // Wt: row (s', ci, b), columns s*out_blk + co*n_out + a: consecutive threads along a when the
+  // block holds all (a,b) entries, in (a,b) order otherwise
+  const bool whole = nabc == nab;
+  for (int idx = threadIdx.x; idx < np * nabc; idx += 256) {
+    const int p = idx / nabc, t = idx % nabc, pr = p0 + p;
+    int aa, bb;
+    if (whole) {
+      bb = t / d.n_out;
+      aa = t % d.n_out;
+    } else {
+      aa = (ab0 + t) / d.n_in;
+      bb = (ab0 + t) % d.n_in;
+    }
+    const int co = pr / d.c_in, ci = pr % d.c_in;
+    const int64_t r = ((int64_t)sp * d.c_in + ci) * d.n_in + bb;
+    stf(Wt + r * d.ldWt + (int64_t)s * d.out_blk + (int64_t)co * d.n_out + aa,
+        blk[p * kBwChunk + (aa * d.n_in + bb) - ab0]);
   }
 }
 
@@ -217,17 +218,28 @@ __global__ void build_bias_kernel(const __grid_constant__ LscDims d, const float
 cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, const float* M, const float* q,
                            void* W, void* Wt, float* bias_vec, int w_t, cudaStream_t st) {
   const size_t es = w_t == 0 ? 4 : 2;
-  cudaError_t e = cudaMemsetAsync(W, 0, (size_t)d.rows_out * d.ldW * es, st);
-  if (e != cudaSuccess) return e;
   const int nab = d.n_out * d.n_in, npairs = d.c_out * d.c_in;
-  dim3 grid((unsigned)((nab + 63) / 64), (unsigned)((npairs + 63) / 64), (unsigned)(d.s_out * d.s_in));
-  dim3 tgrid((unsigned)((d.ldWt + 31) / 32), (unsigned)((d.rows_in + 31) / 32));
+  cudaError_t e;
+  // padding columns between shell blocks stay zero
+  if (d.in_blk != (int64_t)d.c_in * d.n_in) {
+    e = cudaMemsetAsync(W, 0, (size_t)d.rows_out * d.ldW * es, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (d.out_blk != (int64_t)d.c_out * d.n_out) {
+    e = cudaMemsetAsync(Wt, 0, (size_t)d.rows_in * d.ldWt * es, st);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)((npairs + kBwPairs - 1) / kBwPairs), (unsigned)(d.s_out * d.s_in),
+            (unsigned)((nab + kBwChunk - 1) / kBwChunk));
+  const size_t smem = sizeof(float) * kBwPairs * kBwChunk;
   if (w_t == 0) {
-    { build_w_tiled_kernel<float><<<grid, 256, 0, st>>>(d, w, M, (float*)W); count_launch(); }
-    { transpose_w_kernel<float><<<tgrid, dim3(32, 8), 0, st>>>(d, (const float*)W, (float*)Wt); count_launch(); }
+    e = cudaFuncSetAttribute(build_w_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    { build_w_kernel<float><<<grid, 256, smem, st>>>(d, w, M, (float*)W, (float*)Wt); count_launch(); }
   } else {
-    { build_w_tiled_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(d, w, M, (__nv_bfloat16*)W); count_launch(); }
-    { transpose_w_kernel<__nv_bfloat16><<<tgrid, dim3(32, 8), 0, st>>>(d, (const __nv_bfloat16*)W, (__nv_bfloat16*)Wt); count_launch(); }
+    e = cudaFuncSetAttribute(build_w_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    { build_w_kernel<__nv_bfloat16><<<grid, 256, smem, st>>>(d, w, M, (__nv_bfloat16*)W, (__nv_bfloat16*)Wt); count_launch(); }
   }
   e = cudaGetLastError();
   if (e != cudaSuccess || !bias_vec) return e;
@@ -397,27 +409,33 @@ cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int m
 //   dw[co,s,ci,s',k] = sum_{a,b} M_s[k][a][b] G[(s,co,a)][(s',ci,b)],  G = sum_split P;
 // a block owns 32 channel pairs x all K and walks (a,b) in chunks of 128.
 // ---------------------------------------------------------------------------
+constexpr int kDwAbPart = 256;  // (a,b) entries per partial sum
+
 __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ LscDims d, const float* __restrict__ P,
                                                         int64_t ldp, int64_t split_stride, int splits,
-                                                        const float* __restrict__ M, float* __restrict__ dw) {
-  // block: 64 channel pairs x 64 kernel points; thread: 4 pairs x 4 points; (a,b) walked in chunks of 32
+                                                        const float* __restrict__ M, float* __restrict__ dwp,
+                                                        int64_t part_stride) {
+  // block: 64 channel pairs x 64 kernel points x one (a,b) part; thread: 4 pairs x 4 points;
+  // the part is walked in chunks of 32.  Writes partial sums dwp[part][dw index].
   constexpr int PT = 64, KT = 64, AB = 32;
   __shared__ __align__(16) float gs[AB][PT + 4];
   __shared__ __align__(16) float ms_[AB][KT + 4];
-  const int pair = blockIdx.z;
-  const int s = pair / d.s_in, sp = pair % d.s_in;
   const int npairs = d.c_out * d.c_in, nab = d.n_out * d.n_in;
+  const int nparts = (nab + kDwAbPart - 1) / kDwAbPart;
+  const int pair = blockIdx.z / nparts, part = blockIdx.z % nparts;
+  const int s = pair / d.s_in, sp = pair % d.s_in;
   const int p0 = blockIdx.y * PT, k0 = blockIdx.x * KT;
   const bool in_win = sp >= d.win_lo[s] && sp < d.win_hi[s];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int ab_end = min(nab, (part + 1) * kDwAbPart);
   float acc[4][4] = {};
   if (in_win) {
-    for (int ab0 = 0; ab0 < nab; ab0 += AB) {
+    for (int ab0 = part * kDwAbPart; ab0 < ab_end; ab0 += AB) {
       __syncthreads();
       for (int idx = threadIdx.x; idx < PT * AB; idx += 256) {
         const int t = idx % AB, pp = idx / AB, pr = p0 + pp, ab = ab0 + t;
         float v = 0.f;
-        if (pr < npairs && ab < nab) {
+        if (pr < npairs && ab < ab_end) {
           const int co = pr / d.c_in, ci = pr % d.c_in, aa = ab / d.n_in, bb = ab % d.n_in;
           const int64_t off =
               (((int64_t)s * d.c_out + co) * d.n_out + aa) * ldp + ((int64_t)sp * d.c_in + ci) * d.n_in + bb;
@@ -427,10 +445,10 @@ __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ 
       }
       for (int idx = threadIdx.x; idx < KT * AB; idx += 256) {
         const int t = idx % AB, kk = idx / AB, ab = ab0 + t, k = k0 + kk;
-        ms_[t][kk] = (ab < nab && k < d.K) ? M[((int64_t)s * d.K + k) * nab + ab] : 0.f;
+        ms_[t][kk] = (ab < ab_end && k < d.K) ? M[((int64_t)s * d.K + k) * nab + ab] : 0.f;
       }
       __syncthreads();
-      const int nt = min(AB, nab - ab0);
+      const int nt = min(AB, ab_end - ab0);
       for (int t = 0; t < nt; ++t) {
         const float4 g4 = *reinterpret_cast<const float4*>(&gs[t][ty * 4]);
         const float4 m4 = *reinterpret_cast<const float4*>(&ms_[t][tx * 4]);
@@ -447,12 +465,22 @@ __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ 
     const int pr = p0 + ty * 4 + i;
     if (pr >= npairs) continue;
     const int co = pr / d.c_in, ci = pr % d.c_in;
-    float* out = dw + ((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K;
+    float* out = dwp + part * part_stride + ((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int k = k0 + tx * 4 + j;
       if (k < d.K) out[k] = in_win ? acc[i][j] : 0.f;
     }
+  }
+}
+
+// dw[i] = sum over parts in order (deterministic)
+__global__ void sum_parts_kernel(const float* __restrict__ dwp, int64_t part_stride, int nparts, int64_t n,
+                                 float* __restrict__ dw) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float a = 0.f;
+    for (int p = 0; p < nparts; ++p) a += dwp[p * part_stride + i];
+    dw[i] = a;
   }
 }
 
@@ -472,12 +500,24 @@ __global__ void reduce_db_kernel(const __grid_constant__ LscDims d, const float*
   if (threadIdx.x == 0) db[co * d.s_out + s] = acc;
 }
 
+size_t reduce_dw_scratch_floats(const LscDims& d) {
+  const int nparts = (d.n_out * d.n_in + kDwAbPart - 1) / kDwAbPart;
+  return (size_t)nparts * d.c_out * d.s_out * d.c_in * d.s_in * d.K;
+}
+
 cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int64_t split_stride, int splits,
-                             const float* M, const float* q, float* dw, float* db, cudaStream_t st) {
+                             const float* M, const float* q, float* dw, float* db, float* scratch, cudaStream_t st) {
   if (dw) {
-    dim3 grid((unsigned)((d.K + 63) / 64), (unsigned)((d.c_out * d.c_in + 63) / 64), (unsigned)(d.s_out * d.s_in));
-    { reduce_dw_kernel<<<grid, 256, 0, st>>>(d, P, ldp, split_stride, splits, M, dw); count_launch(); }
+    const int nparts = (d.n_out * d.n_in + kDwAbPart - 1) / kDwAbPart;
+    const int64_t n = (int64_t)d.c_out * d.s_out * d.c_in * d.s_in * d.K;
+    dim3 grid((unsigned)((d.K + 63) / 64), (unsigned)((d.c_out * d.c_in + 63) / 64),
+              (unsigned)(d.s_out * d.s_in * nparts));
+    { reduce_dw_kernel<<<grid, 256, 0, st>>>(d, P, ldp, split_stride, splits, M, scratch, n); count_launch(); }
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned g = (unsigned)std::min<int64_t>(4096, (n + 255) / 256);
+    { sum_parts_kernel<<<g, 256, 0, st>>>(scratch, n, nparts, n, dw); count_launch(); }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (db) {
