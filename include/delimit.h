@@ -270,6 +270,18 @@ delimit_status delimit_device_error(void* stream, int* code);
  * cross-check the two).  Has no counterpart in the paper. */
 delimit_status delimit_set_tensor_cores(int enable);
 
+/* Tracing: while enabled, every group of kernel launches made by a call is
+ * bracketed by CUDA events recorded on the call's stream.  Enabling (or
+ * disabling) clears the record.  delimit_trace_summary synchronises on the
+ * recorded events and writes JSON {"name": {"n": launches, "ms": total device
+ * time}, ...} into buf (truncated to cap - 1 characters); it returns the full
+ * length.  Names: signal2sh_tc, sh2signal_tc, signal2sh_bwd_tc,
+ * sh2signal_bwd_tc, transform_simt, lsc_build_w, lsc_fwd_gemm, lsc_dgrad_gemm,
+ * lsc_wgrad_gemm, lsc_rowsum, lsc_reduce_dw, lsc_gemm_simt, lsc_wgrad_simt.
+ * No counterpart in the paper. */
+delimit_status delimit_trace_enable(int enable);
+int64_t delimit_trace_summary(char* buf, size_t cap);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (host-side count, for instrumentation).  No counterpart in the paper. */
 uint64_t delimit_kernel_launches(void);

@@ -74,6 +74,8 @@ SIGNATURES = {
     "delimit_device_error": (C.c_int, [_vp, _ip]),
     "delimit_set_tensor_cores": (C.c_int, [C.c_int]),
     "delimit_kernel_launches": (C.c_uint64, []),
+    "delimit_trace_enable": (C.c_int, [C.c_int]),
+    "delimit_trace_summary": (C.c_int64, [C.c_char_p, C.c_size_t]),
     "delimit_status_string": (C.c_char_p, [C.c_int]),
     "delimit_last_error": (C.c_char_p, []),
     "delimit_version": (C.c_int, []),
@@ -216,6 +218,19 @@ def device_error(stream_ptr: int = 0):
     code = C.c_int()
     st = get().delimit_device_error(_vp(stream_ptr), C.byref(code))
     return st, code.value
+
+
+def trace_enable(on: bool):
+    check(get().delimit_trace_enable(1 if on else 0), "delimit_trace_enable")
+
+
+def trace_summary() -> dict:
+    """Per-name launch counts and total device milliseconds since tracing was enabled."""
+    import json
+    n = get().delimit_trace_summary(None, 0)
+    buf = C.create_string_buffer(int(n) + 1)
+    get().delimit_trace_summary(buf, len(buf))
+    return json.loads(buf.value.decode())
 
 
 def exported_names():

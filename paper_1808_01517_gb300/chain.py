@@ -121,6 +121,33 @@ class Chain:
         return dict(signal2sh=s2sh, lsc_forward=lsc_gemm + build_w, sh2signal=sh2s, sh2signal_backward=sh2s,
                     lsc_backward=2 * lsc_gemm + build_w + 2.0 * pairs * co * ci * N * N * K, signal2sh_backward=s2sh)
 
+    def kernel_work(self) -> dict:
+        """Algorithmic work per launch of each traced kernel group: (flops, compulsory HBM bytes)."""
+        cfg, b = self.cfg, self.basis
+        V, S, N, ci, co, K = cfg.n_vox, b.n_shells, b.n_coef, cfg.c_in, cfg.c_out, self.geom.K
+        e = 2 if self.dtype == torch.bfloat16 else 4
+        win = np.array([[abs(s - p) <= 1 if cfg.window == "adjacent" else (s == p if cfg.window == "same" else True)
+                         for p in range(S)] for s in range(S)])
+        pairs = int(win.sum())
+        r = self.rows
+        gemm = 2.0 * pairs * (co * N) * (ci * N) * V
+        build = 2.0 * pairs * co * ci * N * N * K
+        wbytes = 2.0 * e * r["c_out"] * r["c_in"]
+        fl = self.flops()
+        by = self.bytes()
+        return {
+            "lsc_fwd_gemm": (gemm, e * V * (r["c_in"] + r["c_out"])),
+            "lsc_dgrad_gemm": (gemm, e * V * (r["c_out"] + r["c_in"])),
+            "lsc_wgrad_gemm": (gemm, e * V * (r["c_out"] + r["c_in"])),
+            "lsc_build_w": (build, wbytes),
+            "lsc_reduce_dw": (build, 4.0 * r["c_out"] * r["c_in"]),
+            "lsc_rowsum": (1.0 * r["c_out"] * V, e * V * r["c_out"]),
+            "signal2sh_tc": (fl["signal2sh"], by["signal2sh"]),
+            "sh2signal_tc": (fl["sh2signal"], by["sh2signal"]),
+            "sh2signal_bwd_tc": (fl["sh2signal_backward"], by["sh2signal_backward"]),
+            "signal2sh_bwd_tc": (fl["signal2sh_backward"], by["signal2sh_backward"]),
+        }
+
     def bytes(self) -> dict:
         """Compulsory HBM bytes per call (activations read + written once)."""
         e = 2 if self.dtype == torch.bfloat16 else 4

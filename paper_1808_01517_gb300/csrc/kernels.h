@@ -91,6 +91,20 @@ cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int6
 // sets the thread-local message returned by delimit_last_error()
 void set_last_error(const std::string& msg);
 
+// Tracing: while enabled (delimit_trace_enable), a TraceScope brackets the launches
+// made during its lifetime with CUDA events on `st`, recorded under `name`.
+class TraceScope {
+ public:
+  TraceScope(const char* name, cudaStream_t st);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+
+ private:
+  int idx_;
+  cudaStream_t st_;
+};
+
 // host-side count of kernels launched by the library (instrumentation)
 void count_launch();
 uint64_t launch_count();

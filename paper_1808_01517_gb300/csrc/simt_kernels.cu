@@ -102,6 +102,7 @@ static cudaError_t transform_dispatch(const TransformArgs& a, int n_groups, int 
 
 cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_out, int in_t, int out_t,
                                   cudaStream_t st) {
+  TraceScope trace("transform_simt", st);
   if (a.n_vox == 0) return cudaSuccess;
   if (in_t == 0 && out_t == 0) return transform_dispatch<float, float>(a, n_groups, max_out, st);
   if (in_t == 1 && out_t == 0) return transform_dispatch<__nv_bfloat16, float>(a, n_groups, max_out, st);
@@ -217,6 +218,7 @@ __global__ void build_bias_kernel(const __grid_constant__ LscDims d, const float
 
 cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, const float* M, const float* q,
                            void* W, void* Wt, float* bias_vec, int w_t, cudaStream_t st) {
+  TraceScope trace("lsc_build_w", st);
   const size_t es = w_t == 0 ? 4 : 2;
   const int nab = d.n_out * d.n_in, npairs = d.c_out * d.c_in;
   cudaError_t e;
@@ -312,6 +314,7 @@ __global__ void __launch_bounds__(256) row_gemm_simt_kernel(const __grid_constan
 }
 
 cudaError_t launch_row_gemm_simt(const RowGemmArgs& a, int n_groups, int max_R, int act_t, cudaStream_t st) {
+  TraceScope trace("lsc_gemm_simt", st);
   if (a.n_vox == 0) return cudaSuccess;
   dim3 grid((unsigned)((a.n_vox + 127) / 128), (unsigned)((max_R + 127) / 128), n_groups);
   if (act_t == 0)
@@ -395,6 +398,7 @@ __global__ void __launch_bounds__(256) wgrad_simt_kernel(const __grid_constant__
 
 cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int max_N, int splits, int act_t,
                               cudaStream_t st) {
+  TraceScope trace("lsc_wgrad_simt", st);
   const int mtiles = (max_M + 127) / 128;
   dim3 grid((unsigned)((max_N + 1 + 127) / 128), (unsigned)(mtiles * n_groups), (unsigned)splits);
   if (act_t == 0)
@@ -507,6 +511,7 @@ size_t reduce_dw_scratch_floats(const LscDims& d) {
 
 cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int64_t split_stride, int splits,
                              const float* M, const float* q, float* dw, float* db, float* scratch, cudaStream_t st) {
+  TraceScope trace("lsc_reduce_dw", st);
   if (dw) {
     const int nparts = (d.n_out * d.n_in + kDwAbPart - 1) / kDwAbPart;
     const int64_t n = (int64_t)d.c_out * d.s_out * d.c_in * d.s_in * d.K;

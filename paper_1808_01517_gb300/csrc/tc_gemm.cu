@@ -686,6 +686,7 @@ bool tc_gemm_supported(const LscDims& d, int64_t n_vox, int64_t ld_in, int64_t l
 
 cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* Wt, const float* bias, void* Y, int64_t n_vox,
                            int64_t ldx, int64_t ldy, int* err, cudaStream_t st) {
+  TraceScope trace("lsc_fwd_gemm", st);
   CUtensorMap ma, mb;
   if (!make_map(&ma, X, (uint64_t)n_vox, (uint64_t)d.rows_in, (uint64_t)ldx, 64, kBK)) return cudaErrorInvalidValue;
   if (!make_map(&mb, Wt, (uint64_t)d.ldWt, (uint64_t)d.rows_in, (uint64_t)d.ldWt, 64, kBK)) return cudaErrorInvalidValue;
@@ -718,6 +719,7 @@ cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* Wt, cons
 
 cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* dX, int64_t n_vox, int64_t lddy,
                          int64_t lddx, int* err, cudaStream_t st) {
+  TraceScope trace("lsc_dgrad_gemm", st);
   CUtensorMap ma, mb;
   if (!make_map(&ma, dY, (uint64_t)n_vox, (uint64_t)d.rows_out, (uint64_t)lddy, 64, kBK)) return cudaErrorInvalidValue;
   if (!make_map(&mb, W, (uint64_t)d.ldW, (uint64_t)d.rows_out, (uint64_t)d.ldW, 64, kBK)) return cudaErrorInvalidValue;
@@ -782,11 +784,13 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
   if (e != cudaSuccess) return e;
   const int sms = std::max(1, dev_info().sms);
   if (p.total_tiles > 0) {
+    TraceScope trace("lsc_wgrad_gemm", st);
     { kern<<<(unsigned)std::min<int64_t>(p.total_tiles, sms), kThreads, smem, st>>>(ma, mb, p); count_launch(); }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   const int64_t warps = d.rows_out * splits;
+  TraceScope trace_rs("lsc_rowsum", st);
   { rowsum_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
       reinterpret_cast<const __nv_bfloat16*>(dY), lddy, d.rows_out, n_vox, vps, splits, P, ldp, split_stride, d.rows_in); count_launch(); }
   return cudaGetLastError();

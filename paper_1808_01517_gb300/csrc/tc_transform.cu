@@ -371,6 +371,8 @@ cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X,
                                 int64_t ldx, int64_t ldy, int out_t, int* err_word, cudaStream_t st) {
   auto fn = tf_encode();
   if (!fn) return cudaErrorNotSupported;
+  static const char* kNames[4] = {"signal2sh_tc", "sh2signal_tc", "signal2sh_bwd_tc", "sh2signal_bwd_tc"};
+  TraceScope trace(kNames[kind & 3], st);
   TfParams p;
   memset(&p, 0, sizeof p);
   const bool x_is_sig = (kind == 0 || kind == 3);  // input rows in the signal layout
