@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ Ls
         wk[pp][kk] = v;
       }
       __syncthreads();
-      for (int kk = 0; kk < nk; ++kk) {
+#pragma unroll 7
+      for (int kk = 0; kk < nk; ++kk) {  // unrolled: several k rows of loads in flight
         const float* mk = Ms + (int64_t)(k0 + kk) * nab;
         float mv[kBwMaxPer];
 #pragma unroll
