@@ -156,3 +156,58 @@ class Chain:
                     sh2signal=e * V * (r["c_out"] + r["s_out"]), sh2signal_backward=e * V * (r["s_out"] + r["c_out"]),
                     lsc_backward=e * V * (r["c_out"] + 2 * r["c_in"]),
                     signal2sh_backward=e * V * (r["c_in"] + r["s_in"]))
+
+
+class HostPipeline:
+    """Runs the chain on inputs in pinned host memory and returns every step's outputs
+    to pinned host memory, overlapping the copies with the compute.
+
+    Two Chain instances (same tables, separate buffers) alternate between steps.
+    Stream ``h2d`` copies step i's inputs, ``comp`` runs step i, ``d2h`` copies its
+    outputs back; events order the three so that a chain's buffers are refilled only
+    after its previous step's compute and copy-back are done.
+    """
+
+    def __init__(self, chains):
+        assert len(chains) == 2
+        self.chains = chains
+        self.h2d, self.comp, self.d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        ev = lambda: torch.cuda.Event()  # noqa: E731
+        self.in_ready = [ev(), ev()]
+        self.comp_done = [ev(), ev()]
+        self.out_done = [ev(), ev()]
+        self.started = [False, False]
+
+    @staticmethod
+    def host_buffers(chain):
+        pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True)  # noqa: E731
+        return {"s_in": pin(chain.s_in), "ds_out": pin(chain.ds_out)}, \
+               {"s_out": pin(chain.s_out), "ds_in": pin(chain.ds_in), "dw": pin(chain.dw), "db": pin(chain.db)}
+
+    def step(self, i: int, host_in: dict, host_out: dict):
+        j = i % 2
+        ch = self.chains[j]
+        with torch.cuda.stream(self.h2d):
+            if self.started[j]:
+                self.h2d.wait_event(self.comp_done[j])  # the previous step on this chain has read its inputs
+            ch.s_in.copy_(host_in["s_in"], non_blocking=True)
+            ch.ds_out.copy_(host_in["ds_out"], non_blocking=True)
+            self.in_ready[j].record(self.h2d)
+        with torch.cuda.stream(self.comp):
+            self.comp.wait_event(self.in_ready[j])
+            if self.started[j]:
+                self.comp.wait_event(self.out_done[j])  # outputs of the previous step on this chain are copied out
+            ch.step(stream=self.comp.cuda_stream)
+            self.comp_done[j].record(self.comp)
+        with torch.cuda.stream(self.d2h):
+            self.d2h.wait_event(self.comp_done[j])
+            host_out["s_out"].copy_(ch.s_out, non_blocking=True)
+            host_out["ds_in"].copy_(ch.ds_in, non_blocking=True)
+            host_out["dw"].copy_(ch.dw, non_blocking=True)
+            host_out["db"].copy_(ch.db, non_blocking=True)
+            self.out_done[j].record(self.d2h)
+        self.started[j] = True
+
+    def synchronize(self):
+        for s in (self.h2d, self.comp, self.d2h):
+            s.synchronize()
