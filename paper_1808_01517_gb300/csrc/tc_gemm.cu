@@ -310,13 +310,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 struct WgGroup {
   int64_t m_row0, x_row0, n_col0;
   int M, N, m_tiles, n_tiles;
-  int ones_row;  // row of the last N tile replaced by ones (bias-gradient row sums), or -1
 };
 
 struct WgParams {
   WgGroup g[kMaxGroups];
   int n_groups, splits;
-  int64_t tiles_per_split, total_tiles, vps, n_vox, ldp, split_stride, ones_col;
+  int64_t tiles_per_split, total_tiles, vps, n_vox, ldp, split_stride;
   float* P;
   int* err;
 };
@@ -424,8 +423,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       wg_decode(p, t, split, g, mt, nt);
       const int64_t vs = (int64_t)split * p.vps, ve = min(p.n_vox, vs + p.vps);
       const int nkb = (int)((ve - vs + 63) / 64);
-      const int ones_row = p.g[g].ones_row;
-      const bool ones_tile = ones_row >= 0 && nt == p.g[g].n_tiles - 1;
       if (!wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.err, kErrTmemEmpty)) break;
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
@@ -437,25 +434,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t a_src = sbase + stage * STAGE_BYTES, b_src = a_src + A_BYTES;
-        if (ones_tile) {
-          // overwrite B row `ones_row` with 1 for the voxels of this block (0 past the end):
-          // the row's 128 bytes are its eight 16-byte chunks, permuted by the 128-byte swizzle
-          uint4* row = reinterpret_cast<uint4*>(smem + stage * STAGE_BYTES + A_BYTES + ones_row * 128);
-          const int64_t v0 = vs + (int64_t)kb * 64;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const int lc = c ^ (ones_row & 7);
-            uint32_t w4[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int64_t va = v0 + lc * 8 + 2 * i;
-              const uint32_t lo = va < ve ? 0x3F80u : 0u, hi = va + 1 < ve ? 0x3F80u : 0u;  // bf16 1.0
-              w4[i] = lo | (hi << 16);
-            }
-            row[c] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-          }
-          fence_proxy_async_smem();
-        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           // K-major, 128-byte swizzle: rows 128 B apart, 8-row groups 1024 B apart (SBO);
@@ -492,30 +470,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int m = mt * 128 + q * 32 + lane;
       float* prow = p.P + (int64_t)split * p.split_stride + (G.m_row0 + m) * p.ldp + G.n_col0;
-      float* pones = p.P + (int64_t)split * p.split_stride + (G.m_row0 + m) * p.ldp + p.ones_col;
-      // columns up to N, plus the ones column (index N) in the last tile when the group has one
-      const int n_lim = G.N + ((G.ones_row >= 0 && nt == G.n_tiles - 1) ? 1 : 0);
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
-      for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < n_lim; k0 += 4) {
+      for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
         uint32_t rv[4][16];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int c0 = 32 * (k0 + u) + 16 * half;
-          if (c0 < BN && nt * BN + c0 < n_lim) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+          if (c0 < BN && nt * BN + c0 < G.N) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
         }
         tmem_wait_ld();
         if (m < G.M) {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int nbase = nt * BN + 32 * (k0 + u) + 16 * half;
-            if (32 * (k0 + u) + 16 * half < BN && nbase < n_lim) {
+            if (32 * (k0 + u) + 16 * half < BN && nbase < G.N) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                if (nbase + j < G.N)
-                  prow[nbase + j] = __uint_as_float(rv[u][j]);
-                else if (nbase + j == G.N && n_lim > G.N)
-                  *pones = __uint_as_float(rv[u][j]);
-              }
+              for (int j = 0; j < 16; ++j)
+                if (nbase + j < G.N) prow[nbase + j] = __uint_as_float(rv[u][j]);
             }
           }
         }
@@ -787,7 +758,6 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
   memset(&p, 0, sizeof p);
   const int per_in = d.c_in * d.n_in, per_out = d.c_out * d.n_out;
   p.tiles_per_split = 0;
-  bool all_ones = true;  // every group folds its row sums into the GEMM
   for (int s = 0; s < d.s_out; ++s) {
     WgGroup& G = p.g[s];
     G.m_row0 = (int64_t)s * per_out;
@@ -797,8 +767,6 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
     G.N = (d.win_hi[s] - d.win_lo[s]) * per_in;
     G.m_tiles = (G.M + 127) / 128;
     G.n_tiles = (G.N + BN - 1) / BN;
-    G.ones_row = (G.N % BN) ? G.N % BN : -1;
-    all_ones = all_ones && G.ones_row >= 0;
     p.tiles_per_split += (int64_t)G.m_tiles * G.n_tiles;
   }
   p.n_groups = d.s_out;
@@ -808,7 +776,6 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
   p.n_vox = n_vox;
   p.ldp = ldp;
   p.split_stride = split_stride;
-  p.ones_col = d.rows_in;
   p.P = P;
   p.err = err;
   const size_t smem = smem_bytes<BN, S>(128 * 128, BN * 128);
@@ -822,7 +789,6 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (all_ones) return cudaSuccess;
   const int64_t warps = d.rows_out * splits;
   TraceScope trace_rs("lsc_rowsum", st);
   { rowsum_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
