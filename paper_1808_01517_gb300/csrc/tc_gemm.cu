@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int A_BYTES = 2 * kBoxBytes;        // 128 voxels x 64 K rows
   constexpr int B_BYTES = (BN / 64) * kBoxBytes;  // BN columns x 64 K rows
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  constexpr int STG_BYTES = STAGED ? BN * 128 * 2 : 0;  // [BN rows][64 voxels] x 2 halves, BF16
+  constexpr int HB = BN / 2;                             // columns per staged pass
+  constexpr int STG_BYTES = STAGED ? HB * 128 * 2 : 0;  // [HB rows][64 voxels] x 2 voxel halves, BF16
   constexpr uint32_t TMEM_COLS = (2 * BN <= 256) ? 256 : 512;
   constexpr uint32_t IDESC = idesc_bf16(128, BN, true, true);
 
@@ -231,65 +232,99 @@ __global__ void __launch_bounds__(kThreads, 1)
       vox_decode(p, t, g, mt, nt);
       const VoxGroup& G = p.g[g];
       bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTmemFull);
-      if (STAGED) ok = ok && wait_bounded(stg_free_bar, (uint32_t)(it & 1) ^ 1u, abort_flag, p.err, kErrTmemEmpty);
+      if (STAGED) ok = ok && wait_bounded(stg_free_bar, (uint32_t)((2 * it) & 1) ^ 1u, abort_flag, p.err, kErrTmemEmpty);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const int64_t vox = (int64_t)mt * 128 + q * 32 + lane;
       const bool vok = vox < p.n_vox;
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
-      for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
-        uint32_t rv[4][16];
+      if (STAGED) {
+        // two passes of HB columns through one staging tile, each stored by TMA
+        bool alive = true;
+        for (int pass = 0; pass < 2 && alive; ++pass) {
+          const int use = 2 * it + pass;
+          if (pass == 1) {
+            bool okf = wait_bounded(stg_free_bar, (uint32_t)(use & 1) ^ 1u, abort_flag, p.err, kErrTmemEmpty);
+            if (!__all_sync(0xffffffffu, okf)) {
+              alive = false;
+              break;
+            }
+          }
+          const int cbeg = pass * HB;
+          for (int k0 = 0; 32 * k0 + 16 * half < HB; k0 += 4) {
+            uint32_t rv[4][16];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int c0 = 32 * (k0 + u) + 16 * half;
-          if (c0 < BN && nt * BN + c0 < G.N) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+            for (int u = 0; u < 4; ++u) {
+              const int c0 = cbeg + 32 * (k0 + u) + 16 * half;
+              if (c0 < cbeg + HB) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+            }
+            tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int c0 = cbeg + 32 * (k0 + u) + 16 * half;
+              const int nbase = nt * BN + c0;
+              if (c0 < cbeg + HB) {
+                __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(stg_ptr) + (size_t)h * HB * 64 + (c0 - cbeg) * 64 + xl;
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                  const float bv = (p.bias && nbase + jj < G.N) ? __ldg(p.bias + G.y_row0 + nbase + jj) : 0.f;
+                  dst[jj * 64] = __float2bfloat16_rn(__uint_as_float(rv[u][jj]) + bv);
+                }
+              }
+            }
+          }
+          if (pass == 1) tc_fence_before();
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            if (pass == 1) mbar_arrive(tempty_bar(acc));
+            mbar_arrive(stg_ready_bar);
+          }
+          if (warp == 2) {
+            bool lead_ok = true;
+            if (lane == 0) {
+              lead_ok = wait_bounded(stg_ready_bar, (uint32_t)(use & 1), abort_flag, p.err, kErrTmemFull);
+              if (lead_ok) {
+                const uint32_t src = smem_u32(stg_ptr);
+                tma_store_3d(&mapY, src, mt * 128, nt * BN + cbeg, g);
+                tma_store_3d(&mapY, src + HB * 128, mt * 128 + 64, nt * BN + cbeg, g);
+                bulk_commit();
+                bulk_wait_read<0>();
+                mbar_arrive(stg_free_bar);
+              }
+            }
+            if (!__shfl_sync(0xffffffffu, lead_ok ? 1 : 0, 0)) alive = false;
+          }
         }
-        tmem_wait_ld();
+        if (!alive) break;
+      } else {
+        for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
+          uint32_t rv[4][16];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int c0 = 32 * (k0 + u) + 16 * half;
-          const int nbase = nt * BN + c0;
-          if (c0 < BN && nbase < G.N) {
-            float bv[16];
+          for (int u = 0; u < 4; ++u) {
+            const int c0 = 32 * (k0 + u) + 16 * half;
+            if (c0 < BN && nt * BN + c0 < G.N) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+          }
+          tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              bv[j] = (p.bias && nbase + j < G.N) ? __ldg(p.bias + G.y_row0 + nbase + j) : 0.f;
-            if (STAGED) {
-              __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(stg_ptr) + (size_t)h * BN * 64;
+          for (int u = 0; u < 4; ++u) {
+            const int c0 = 32 * (k0 + u) + 16 * half;
+            const int nbase = nt * BN + c0;
+            if (c0 < BN && nbase < G.N) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) stg[(c0 + j) * 64 + xl] = __float2bfloat16_rn(__uint_as_float(rv[u][j]) + bv[j]);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int n = nbase + j;
-                if (n < G.N && vok)
-                  p.Y[(G.y_row0 + n) * p.ldy + vox] = __float2bfloat16_rn(__uint_as_float(rv[u][j]) + bv[j]);
+              for (int jj = 0; jj < 16; ++jj) {
+                const int n = nbase + jj;
+                if (n < G.N && vok) {
+                  const float bv = p.bias ? __ldg(p.bias + G.y_row0 + n) : 0.f;
+                  p.Y[(G.y_row0 + n) * p.ldy + vox] = __float2bfloat16_rn(__uint_as_float(rv[u][jj]) + bv);
+                }
               }
             }
           }
         }
-      }
-      tc_fence_before();
-      if (STAGED) fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(tempty_bar(acc));
-        if (STAGED) mbar_arrive(stg_ready_bar);
-      }
-      if (STAGED && warp == 2) {
-        bool lead_ok = true;
-        if (lane == 0) {
-          lead_ok = wait_bounded(stg_ready_bar, (uint32_t)(it & 1), abort_flag, p.err, kErrTmemFull);
-          if (lead_ok) {
-            const uint32_t src = smem_u32(stg_ptr);
-            tma_store_3d(&mapY, src, mt * 128, nt * BN, g);
-            tma_store_3d(&mapY, src + BN * 128, mt * 128 + 64, nt * BN, g);
-            bulk_commit();
-            bulk_wait_read<0>();
-            mbar_arrive(stg_free_bar);
-          }
-        }
-        if (!__shfl_sync(0xffffffffu, lead_ok ? 1 : 0, 0)) break;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty_bar(acc));
       }
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
@@ -589,7 +624,7 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, 
 template <int BN, bool STAGED>
 constexpr int vox_stages() {
   // operand ring + (staged) one BN x 128 BF16 output tile within ~210 KiB
-  return STAGED ? (BN == 256 ? 3 : (BN == 192 ? 4 : 5)) : ((BN == 256) ? 4 : (BN == 192 ? 5 : 6));
+  return STAGED ? (BN == 256 ? 4 : (BN == 192 ? 5 : 6)) : ((BN == 256) ? 4 : (BN == 192 ? 5 : 6));
 }
 
 template <int BN, int STAGES>
@@ -601,7 +636,7 @@ template <int BN, bool STAGED>
 cudaError_t launch_vox(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& my, const VoxParams& p,
                        cudaStream_t st) {
   constexpr int S = vox_stages<BN, STAGED>();
-  const size_t smem = smem_bytes<BN, S>(2 * kBoxBytes, (BN / 64) * kBoxBytes) + (STAGED ? BN * 256 : 0) + 16;
+  const size_t smem = smem_bytes<BN, S>(2 * kBoxBytes, (BN / 64) * kBoxBytes) + (STAGED ? BN * 128 : 0) + 16;
   auto kern = vox_gemm_kernel<BN, S, STAGED>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -647,7 +682,7 @@ cudaError_t run_vox(const CUtensorMap& ma, const CUtensorMap& mb, VoxParams& p, 
     auto fn = encode_fn();
     cuuint64_t dims[3] = {(cuuint64_t)p.n_vox, (cuuint64_t)p.g[0].N, (cuuint64_t)p.n_groups};
     cuuint64_t strides[2] = {(cuuint64_t)ldy * 2, (cuuint64_t)(p.g[0].N * ldy * 2)};
-    cuuint32_t box[3] = {64, (cuuint32_t)bn, 1};
+    cuuint32_t box[3] = {64, (cuuint32_t)(bn / 2), 1};
     cuuint32_t es[3] = {1, 1, 1};
     staged = fn(&my, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Y, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -749,7 +784,7 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* 
 
 cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float* P, int64_t ldp, int64_t split_stride,
                          int splits, int64_t vps, int64_t n_vox, int64_t lddy, int64_t ldx, int* err, cudaStream_t st) {
-  constexpr int BN = 256, S = 3;
+  constexpr int BN = 256, S = 4;
   CUtensorMap ma, mb;
   if (!make_map(&ma, dY, (uint64_t)n_vox, (uint64_t)d.rows_out, (uint64_t)lddy, 64, 128)) return cudaErrorInvalidValue;
   if (!make_map(&mb, X, (uint64_t)n_vox, (uint64_t)d.rows_in, (uint64_t)ldx, 64, BN)) return cudaErrorInvalidValue;

@@ -185,16 +185,18 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
       ok = ok && wait_bounded(stg_free_bar(buf), use_par ^ 1u, abort_flag, p.err, kErrTEmpty);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      uint8_t* stg = stg_ptr + (size_t)buf * p.stg_bytes + (size_t)h * G.n_out * 64 * ES;
+      // each voxel half holds n_mma rows (a multiple of 16): the stores below need no bounds
+      // checks; the TMA store reads only the first n_out rows of each half
+      uint8_t* stg = stg_ptr + (size_t)buf * p.stg_bytes + (size_t)h * G.n_mma * 64 * ES;
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
       // this warp's chunks: c0 = 16 * (2k + half); up to four loads in flight per wait
-      for (int k0 = 0; 32 * k0 + 16 * half < G.n_out; k0 += 4) {
+      for (int k0 = 0; 32 * k0 + 16 * half < G.n_mma; k0 += 4) {
         uint32_t rv[4][16];
         int nld = 0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int c0 = 32 * (k0 + u) + 16 * half;
-          if (c0 < G.n_out) {
+          if (c0 < G.n_mma) {
             tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
             nld = u + 1;
           }
@@ -204,15 +206,14 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
         for (int u = 0; u < 4; ++u) {
           const int c0 = 32 * (k0 + u) + 16 * half;
           if (u < nld) {
+            if (OUT_F32) {
+              float* dst = reinterpret_cast<float*>(stg) + c0 * 64 + xl;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if (c0 + j < G.n_out) {
-                const float v = __uint_as_float(rv[u][j]);
-                if (OUT_F32)
-                  reinterpret_cast<float*>(stg)[(c0 + j) * 64 + xl] = v;
-                else
-                  reinterpret_cast<__nv_bfloat16*>(stg)[(c0 + j) * 64 + xl] = __float2bfloat16_rn(v);
-              }
+              for (int j = 0; j < 16; ++j) dst[j * 64] = __uint_as_float(rv[u][j]);
+            } else {
+              __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(stg) + c0 * 64 + xl;
+#pragma unroll
+              for (int j = 0; j < 16; ++j) dst[j * 64] = __float2bfloat16_rn(__uint_as_float(rv[u][j]));
             }
           }
         }
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
           if (lead_ok) {
             const uint32_t src = stg_base + (uint32_t)(buf * p.stg_bytes);
             tma_store_3d(&p.mapY[g], src, mt * 128, 0, c);
-            tma_store_3d(&p.mapY[g], src + (uint32_t)(G.n_out * 64 * ES), mt * 128 + 64, 0, c);
+            tma_store_3d(&p.mapY[g], src + (uint32_t)(G.n_mma * 64 * ES), mt * 128 + 64, 0, c);
             bulk_commit();
             // the previous tile's store has finished reading its buffer: release it
             bulk_wait_read<1>();
@@ -363,7 +364,7 @@ bool tc_transform_supported(const TcBasisTables& t, int kind, int64_t ldx, int64
   int nmax = 0;
   for (int s = 0; s < t.n_shells; ++s) nmax = std::max(nmax, t.n_out[s][kind]);
   const size_t stage = size_t(kmax) * 256;
-  const size_t stg = 2 * (size_t(2 * nmax * 64 * (out_t == 0 ? 4 : 2)) + 1024);
+  const size_t stg = 2 * (size_t(2 * ((nmax + 15) / 16 * 16) * 64 * (out_t == 0 ? 4 : 2)) + 1024);
   return btot + 2 * stage + stg + 4096 <= kSmemLimit;
 }
 
@@ -439,7 +440,8 @@ cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X,
   p.channels = C;
   p.m_tiles = (int)((n_vox + 127) / 128);
   p.stage_bytes = kmax * 256;
-  p.stg_bytes = (2 * nmax * 64 * es + 1023) / 1024 * 1024;
+  const int nmma_max = (nmax + 15) / 16 * 16;
+  p.stg_bytes = (2 * nmma_max * 64 * es + 1023) / 1024 * 1024;
   p.b_total = (boff + 1023) / 1024 * 1024;
   const size_t fixed = 1024 + p.b_total + 2 * (size_t)p.stg_bytes + 16 * 8 + 128;
   int stages = (int)((kSmemLimit - fixed) / p.stage_bytes);
