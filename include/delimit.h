@@ -170,6 +170,14 @@ delimit_status delimit_lsc_geometry_tables(const delimit_lsc_geometry* geom, int
                                            double* M, double* q, int64_t* nb_indptr, int64_t* nb_indices,
                                            int64_t* row_index, unsigned char* window);
 
+/* LSC call flags.  DELIMIT_LSC_OPERATOR_READY: `workspace` already holds the
+ * collapsed operator (and, for a forward, the bias vector) built by an earlier
+ * forward or backward call with the same geometry, sizes, dtype, w and b; the
+ * call skips rebuilding it.  The operator sits at the start of the workspace in
+ * both layouts, so a backward may reuse the workspace of the forward it
+ * follows (give the forward a backward-sized workspace). */
+#define DELIMIT_LSC_OPERATOR_READY 1u
+
 /* Device workspace bytes needed by delimit_lsc_forward (backward = 0) or
  * delimit_lsc_backward (backward = 1) for these sizes; 0 on invalid input. */
 size_t delimit_lsc_workspace_size(const delimit_lsc_geometry* geom, int64_t n_vox, int c_in, int c_out,
@@ -190,8 +198,8 @@ size_t delimit_lsc_workspace_size(const delimit_lsc_geometry* geom, int64_t n_vo
  *   workspace >= delimit_lsc_workspace_size(..., 0) bytes, 256-byte aligned. */
 delimit_status delimit_lsc_forward(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
                                    const float* b, void* sh_out, int64_t n_vox, int c_in, int c_out,
-                                   int64_t ld_in, int64_t ld_out, delimit_dtype act_t, void* workspace,
-                                   size_t ws_bytes, void* stream);
+                                   int64_t ld_in, int64_t ld_out, delimit_dtype act_t, unsigned flags,
+                                   void* workspace, size_t ws_bytes, void* stream);
 
 /* LSC backward for upstream gradient d_out (SH rows of the output):
  *   d_in  = adjoint of the forward in sh_in (same layout as sh_in), or NULL
@@ -202,7 +210,7 @@ delimit_status delimit_lsc_forward(const delimit_lsc_geometry* geom, const void*
 delimit_status delimit_lsc_backward(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
                                     const void* d_out, void* d_in, float* dw, float* db, int64_t n_vox,
                                     int c_in, int c_out, int64_t ld_in, int64_t ld_out, delimit_dtype act_t,
-                                    void* workspace, size_t ws_bytes, void* stream);
+                                    unsigned flags, void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Helpers of the learned network and whole-volume inference (no counterpart */

@@ -31,6 +31,7 @@ ERR_WORKSPACE = 8
 
 F32 = 0
 BF16 = 1
+OPERATOR_READY = 1
 HOST_ONLY = 1
 EVAL_ONLY = 2
 WINDOW_SAME, WINDOW_ADJACENT, WINDOW_ALL = 0, 1, -1
@@ -59,10 +60,10 @@ SIGNATURES = {
     "delimit_lsc_geometry_info": (C.c_int, [_vp, _ip, _ip, _ip, _ip, _ip, _i64p]),
     "delimit_lsc_geometry_tables": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _i64p, _i64p, _i64p, C.POINTER(C.c_ubyte)]),
     "delimit_lsc_workspace_size": (C.c_size_t, [_vp, _i64, C.c_int, C.c_int, C.c_int, C.c_int]),
-    "delimit_lsc_forward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64, C.c_int, _vp,
-                                      C.c_size_t, _vp]),
+    "delimit_lsc_forward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64, C.c_int, C.c_uint,
+                                      _vp, C.c_size_t, _vp]),
     "delimit_lsc_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64,
-                                       C.c_int, _vp, C.c_size_t, _vp]),
+                                       C.c_int, C.c_uint, _vp, C.c_size_t, _vp]),
     "delimit_leaky_relu": (C.c_int, [_vp, _vp, _i64, _i64, _i64, _i64, C.c_float, C.c_int, _vp]),
     "delimit_leaky_relu_backward": (C.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, C.c_float, C.c_int, _vp]),
     "delimit_mask_compact_workspace_size": (C.c_size_t, [_i64]),

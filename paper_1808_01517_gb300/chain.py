@@ -88,7 +88,7 @@ class Chain:
         rec(1)
         L.check(lib.delimit_lsc_forward(gh, self.c_in_buf.data_ptr(), self.w.data_ptr(), self.b.data_ptr(),
                                         self.c_out_buf.data_ptr(), V, ci, co, self.c_in_buf.stride(0),
-                                        self.c_out_buf.stride(0), t, ws, self.ws_f, st), "delimit_lsc_forward")
+                                        self.c_out_buf.stride(0), t, 0, ws, self.ws_b, st), "delimit_lsc_forward")
         rec(2)
         L.check(lib.delimit_sh2signal(bh, self.c_out_buf.data_ptr(), self.s_out.data_ptr(), V, co,
                                       self.c_out_buf.stride(0), self.s_out.stride(0), t, t, st), "delimit_sh2signal")
@@ -99,7 +99,8 @@ class Chain:
         rec(4)
         L.check(lib.delimit_lsc_backward(gh, self.c_in_buf.data_ptr(), self.w.data_ptr(), self.dc_out.data_ptr(),
                                          self.dc_in.data_ptr(), self.dw.data_ptr(), self.db.data_ptr(), V, ci, co,
-                                         self.c_in_buf.stride(0), self.dc_out.stride(0), t, ws, self.ws_b, st),
+                                         self.c_in_buf.stride(0), self.dc_out.stride(0), t, L.OPERATOR_READY, ws,
+                                         self.ws_b, st),
                 "delimit_lsc_backward")
         rec(5)
         L.check(lib.delimit_signal2sh_backward(bh, self.dc_in.data_ptr(), self.ds_in.data_ptr(), V, ci,

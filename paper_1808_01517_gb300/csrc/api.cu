@@ -554,7 +554,7 @@ static delimit_status lsc_common_checks(const delimit_lsc_geometry* g, int64_t n
 
 delimit_status delimit_lsc_forward(const delimit_lsc_geometry* g, const void* sh_in, const float* w, const float* b,
                                    void* sh_out, int64_t n_vox, int c_in, int c_out, int64_t ld_in, int64_t ld_out,
-                                   delimit_dtype act_t, void* ws, size_t ws_bytes, void* stream) {
+                                   delimit_dtype act_t, unsigned flags, void* ws, size_t ws_bytes, void* stream) {
   LscPlan p;
   delimit_status st = lsc_common_checks(g, n_vox, c_in, c_out, act_t, ws, ws_bytes, false, p);
   if (st != DELIMIT_OK) return st;
@@ -567,8 +567,11 @@ delimit_status delimit_lsc_forward(const delimit_lsc_geometry* g, const void* sh
   void* W = base + p.off_W;
   void* Wt = base + p.off_Wt;
   float* bias = reinterpret_cast<float*>(base + p.off_bias);
-  cudaError_t e = launch_build_w(p.d, w, b, g->d_M, g->d_q, W, Wt, bias, int(act_t), cs);
-  if (e != cudaSuccess) return cuda_fail(e, "build_w launch");
+  cudaError_t e = cudaSuccess;
+  if (!(flags & DELIMIT_LSC_OPERATOR_READY)) {
+    e = launch_build_w(p.d, w, b, g->d_M, g->d_q, W, Wt, bias, int(act_t), cs);
+    if (e != cudaSuccess) return cuda_fail(e, "build_w launch");
+  }
   const LscDims& d = p.d;
   if (act_t == DELIMIT_BF16 && tc_gemm_supported(d, n_vox, ld_in, ld_out)) {
     e = tc_lsc_forward(d, sh_in, Wt, bias, sh_out, n_vox, ld_in, ld_out, g->err_word, cs);
@@ -602,7 +605,8 @@ delimit_status delimit_lsc_forward(const delimit_lsc_geometry* g, const void* sh
 
 delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* sh_in, const float* w, const void* d_out,
                                     void* d_in, float* dw, float* db, int64_t n_vox, int c_in, int c_out, int64_t ld_in,
-                                    int64_t ld_out, delimit_dtype act_t, void* ws, size_t ws_bytes, void* stream) {
+                                    int64_t ld_out, delimit_dtype act_t, unsigned flags, void* ws, size_t ws_bytes,
+                                    void* stream) {
   LscPlan p;
   delimit_status st = lsc_common_checks(g, n_vox, c_in, c_out, act_t, ws, ws_bytes, true, p);
   if (st != DELIMIT_OK) return st;
@@ -632,8 +636,10 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
   if (d_in) {
     void* W = base + p.off_W;
     void* Wt = base + p.off_Wt;
-    e = launch_build_w(d, w, nullptr, g->d_M, g->d_q, W, Wt, nullptr, int(act_t), cs);
-    if (e != cudaSuccess) return cuda_fail(e, "build_w launch");
+    if (!(flags & DELIMIT_LSC_OPERATOR_READY)) {
+      e = launch_build_w(d, w, nullptr, g->d_M, g->d_q, W, Wt, nullptr, int(act_t), cs);
+      if (e != cudaSuccess) return cuda_fail(e, "build_w launch");
+    }
     bool all_fed = true;
     for (int sp = 0; sp < d.s_in; ++sp) all_fed = all_fed && d.rwin_hi[sp] > d.rwin_lo[sp];
     if (act_t == DELIMIT_BF16 && all_fed && tc_gemm_supported(d, n_vox, ld_in, ld_out)) {

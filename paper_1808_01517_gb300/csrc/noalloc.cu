@@ -36,7 +36,7 @@ delimit_status delimit_lsc_forward_noalloc(const delimit_lsc_geometry* geom, con
                                            const float* b, void* sh_out, int64_t n_vox, int c_in, int c_out,
                                            int64_t ld_in, int64_t ld_out, delimit_dtype act_t, void* stream) {
   const size_t need = delimit_lsc_workspace_size(geom, n_vox, c_in, c_out, act_t, 0);
-  if (need == 0) return delimit_lsc_forward(geom, sh_in, w, b, sh_out, n_vox, c_in, c_out, ld_in, ld_out, act_t,
+  if (need == 0) return delimit_lsc_forward(geom, sh_in, w, b, sh_out, n_vox, c_in, c_out, ld_in, ld_out, act_t, 0u,
                                             nullptr, 0, stream);  // reports the argument error
   if (need > kScratchBytes) {
     delimit::set_last_error("delimit_lsc_forward_noalloc: these sizes need " + std::to_string(need) +
@@ -63,8 +63,8 @@ delimit_status delimit_lsc_forward_noalloc(const delimit_lsc_geometry* geom, con
     }
     ptr = g_scratch_addr[dev];
   }
-  return delimit_lsc_forward(geom, sh_in, w, b, sh_out, n_vox, c_in, c_out, ld_in, ld_out, act_t, ptr, kScratchBytes,
-                             stream);
+  return delimit_lsc_forward(geom, sh_in, w, b, sh_out, n_vox, c_in, c_out, ld_in, ld_out, act_t, 0u, ptr,
+                             kScratchBytes, stream);
 }
 
 }  // extern "C"

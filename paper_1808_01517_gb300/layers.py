@@ -82,25 +82,35 @@ def transform(kind: str, basis: L.SHBasis, x: torch.Tensor, channels: int, out_d
     return out
 
 
+def lsc_workspace(geom: L.LSCGeometry, n_vox: int, c_in: int, c_out: int, dtype, backward: bool, device="cuda"):
+    """(keep-alive tensor, 256-byte aligned pointer, bytes) of an LSC workspace."""
+    ws_n = geom.workspace_size(n_vox, c_in, c_out, _DT[dtype], backward)
+    ws = torch.empty(ws_n + 256, dtype=torch.uint8, device=device)
+    return ws, (ws.data_ptr() + 255) // 256 * 256, ws_n
+
+
 def lsc_forward(geom: L.LSCGeometry, x: torch.Tensor, w: torch.Tensor, b: torch.Tensor | None, c_in: int,
-                c_out: int, out: torch.Tensor | None = None) -> torch.Tensor:
+                c_out: int, out: torch.Tensor | None = None, workspace=None) -> torch.Tensor:
+    """``workspace``: optional (tensor, ptr, bytes) from lsc_workspace; a backward-sized
+    workspace lets the following backward reuse the operator built here."""
     x = as_act(x)
     n_vox = x.shape[1]
     if out is None:
         out = empty_act(geom.s_out * c_out * geom.n_out, n_vox, x.dtype, x.device)
-    ws_n = geom.workspace_size(n_vox, c_in, c_out, _code(x), False)
-    ws = torch.empty(ws_n + 256, dtype=torch.uint8, device=x.device)
-    wsp = (ws.data_ptr() + 255) // 256 * 256
+    _, wsp, ws_n = workspace if workspace is not None else lsc_workspace(geom, n_vox, c_in, c_out, x.dtype, False,
+                                                                         x.device)
     w = w.detach().contiguous().float()
     bp = b.detach().contiguous().float().data_ptr() if b is not None else None
     L.check(L.get().delimit_lsc_forward(geom.handle, x.data_ptr(), w.data_ptr(), bp, out.data_ptr(), n_vox, c_in,
-                                        c_out, x.stride(0), out.stride(0), _code(x), wsp, ws_n, _stream()),
+                                        c_out, x.stride(0), out.stride(0), _code(x), 0, wsp, ws_n, _stream()),
             "delimit_lsc_forward")
     return out
 
 
 def lsc_backward(geom: L.LSCGeometry, x: torch.Tensor, w: torch.Tensor, d_out: torch.Tensor, c_in: int, c_out: int,
-                 need_input: bool = True, need_weight: bool = True, need_bias: bool = True):
+                 need_input: bool = True, need_weight: bool = True, need_bias: bool = True, workspace=None,
+                 operator_ready: bool = False):
+    """``workspace`` + ``operator_ready``: reuse the operator a forward built in this workspace."""
     x = as_act(x)
     d_out = as_act(d_out.to(x.dtype))
     n_vox = x.shape[1]
@@ -108,13 +118,14 @@ def lsc_backward(geom: L.LSCGeometry, x: torch.Tensor, w: torch.Tensor, d_out: t
     w = w.detach().contiguous().float()
     dw = torch.empty_like(w) if need_weight else None
     db = torch.empty((c_out, geom.s_out), dtype=torch.float32, device=x.device) if need_bias else None
-    ws_n = geom.workspace_size(n_vox, c_in, c_out, _code(x), True)
-    ws = torch.empty(ws_n + 256, dtype=torch.uint8, device=x.device)
-    wsp = (ws.data_ptr() + 255) // 256 * 256
+    if workspace is None:
+        workspace, operator_ready = lsc_workspace(geom, n_vox, c_in, c_out, x.dtype, True, x.device), False
+    _, wsp, ws_n = workspace
     L.check(L.get().delimit_lsc_backward(
         geom.handle, x.data_ptr(), w.data_ptr(), d_out.data_ptr(), d_in.data_ptr() if d_in is not None else None,
         dw.data_ptr() if dw is not None else None, db.data_ptr() if db is not None else None, n_vox, c_in, c_out,
-        x.stride(0), d_out.stride(0), _code(x), wsp, ws_n, _stream()), "delimit_lsc_backward")
+        x.stride(0), d_out.stride(0), _code(x), L.OPERATOR_READY if operator_ready else 0, wsp, ws_n, _stream()),
+        "delimit_lsc_backward")
     return d_in, dw, db
 
 
@@ -140,14 +151,20 @@ class _LSCFn(torch.autograd.Function):
         ctx.geom, ctx.c_in, ctx.c_out = geom, c_in, c_out
         ctx.has_b = b is not None
         ctx.save_for_backward(x, w)
-        return lsc_forward(geom, x, w, b, c_in, c_out)
+        # a backward-sized workspace: the backward reuses the operator built here
+        ws = lsc_workspace(geom, x.shape[1], c_in, c_out, x.dtype, True, x.device) \
+            if any(ctx.needs_input_grad) else None
+        ctx.ws = ws
+        return lsc_forward(geom, x, w, b, c_in, c_out, workspace=ws)
 
     @staticmethod
     def backward(ctx, g):
         x, w = ctx.saved_tensors
         d_in, dw, db = lsc_backward(ctx.geom, x, w, g, ctx.c_in, ctx.c_out, need_input=ctx.needs_input_grad[0],
                                     need_weight=ctx.needs_input_grad[1],
-                                    need_bias=ctx.has_b and ctx.needs_input_grad[2])
+                                    need_bias=ctx.has_b and ctx.needs_input_grad[2], workspace=ctx.ws,
+                                    operator_ready=ctx.ws is not None)
+        ctx.ws = None
         return d_in, dw, db, None, None, None
 
 

@@ -143,15 +143,39 @@ def test_lsc_zero_voxels_and_workspace_errors():
     ws = torch.empty(ws_n + 256, dtype=torch.uint8, device="cuda")
     wsp = (ws.data_ptr() + 255) // 256 * 256
     st = lib.delimit_lsc_backward(lg.handle, None, w.data_ptr(), None, None, dw.data_ptr(), db.data_ptr(), 0, 1, 8,
-                                  8, 8, L.BF16, wsp, ws_n, None)
+                                  8, 8, L.BF16, 0, wsp, ws_n, None)
     torch.cuda.synchronize()
     assert st == L.OK and float(dw.abs().sum()) == 0 and float(db.abs().sum()) == 0
     x = layers.empty_act(45, 100, torch.bfloat16)
     y = layers.empty_act(8 * 45, 100, torch.bfloat16)
     need = lg.workspace_size(100, 1, 8, L.BF16, False)
     st = lib.delimit_lsc_forward(lg.handle, x.data_ptr(), w.data_ptr(), None, y.data_ptr(), 100, 1, 8, x.stride(0),
-                                 y.stride(0), L.BF16, wsp, need - 1, None)
+                                 y.stride(0), L.BF16, 0, wsp, need - 1, None)
     assert st == L.ERR_WORKSPACE
     st = lib.delimit_lsc_forward(lg.handle, x.data_ptr(), w.data_ptr(), None, y.data_ptr(), 100, 1, 8, x.stride(0),
-                                 y.stride(0), L.BF16, wsp + 16, need, None)
+                                 y.stride(0), L.BF16, 0, wsp + 16, need, None)
     assert st == L.ERR_ALIGNMENT
+
+
+@pytest.mark.parametrize("tc", [True, False])
+def test_backward_reuses_forward_operator(tc):
+    """A backward flagged OPERATOR_READY on the forward's workspace gives the same
+    bits as a backward that rebuilds the collapsed operator itself."""
+    cfg = CASES["adjacent"]
+    og, lg = _setup(cfg)
+    c, w, b, d = _inputs(og, cfg, seed=5)
+    ci, co = cfg["ci"], cfg["co"]
+    x = _dev(sh_to_rows(c), torch.bfloat16)
+    g = _dev(sh_to_rows(d), torch.bfloat16)
+    wt, bt = torch.from_numpy(w).float().cuda(), torch.from_numpy(b).float().cuda()
+    L.set_tensor_cores(tc)
+    try:
+        ws = layers.lsc_workspace(lg, x.shape[1], ci, co, torch.bfloat16, True)
+        layers.lsc_forward(lg, x, wt, bt, ci, co, workspace=ws)
+        got = layers.lsc_backward(lg, x, wt, g, ci, co, workspace=ws, operator_ready=True)
+        ref = layers.lsc_backward(lg, x, wt, g, ci, co)
+        torch.cuda.synchronize()
+    finally:
+        L.set_tensor_cores(True)
+    for a, r in zip(got, ref):
+        assert torch.equal(a, r)

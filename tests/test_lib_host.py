@@ -150,3 +150,14 @@ def test_eval_only_basis():
     assert np.all(P == 0)
     with pytest.raises(L.DelimitError):
         L.LSCGeometry(lb, 8, 1, 0.4, 2, 6, "same", host_only=True)
+
+
+def test_binding_constants_match_header():
+    txt = open(os.path.join(ROOT, "include", "delimit.h")).read()
+    vals = {m[0]: int(m[1]) for m in re.findall(r"\b(DELIMIT_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt)}
+    vals |= {m[0]: int(m[1]) for m in re.findall(r"#define\s+(DELIMIT_[A-Z0-9_]+)\s+\(?(-?\d+)u?\)?", txt)}
+    for name in ["OK", "ERR_INVALID_ARG", "ERR_RANK_DEFICIENT", "ERR_UNSUPPORTED", "ERR_ALIGNMENT", "ERR_CUDA",
+                 "ERR_DEVICE_TIMEOUT", "ERR_OOM", "ERR_WORKSPACE", "F32", "BF16", "HOST_ONLY", "EVAL_ONLY",
+                 "WINDOW_SAME", "WINDOW_ADJACENT", "WINDOW_ALL"]:
+        assert vals["DELIMIT_" + name] == getattr(L, name), name
+    assert vals["DELIMIT_LSC_OPERATOR_READY"] == L.OPERATOR_READY

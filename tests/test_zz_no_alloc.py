@@ -26,7 +26,7 @@ def _regular_forward(geom, x, w, b, ci, co, out):
     ws = torch.empty(ws_n + 256, dtype=torch.uint8, device="cuda")
     wsp = (ws.data_ptr() + 255) // 256 * 256
     L.check(L.get().delimit_lsc_forward(geom.handle, x.data_ptr(), w.data_ptr(), b.data_ptr(), out.data_ptr(),
-                                        x.shape[1], ci, co, x.stride(0), out.stride(0), layers._code(x), wsp, ws_n,
+                                        x.shape[1], ci, co, x.stride(0), out.stride(0), layers._code(x), 0, wsp, ws_n,
                                         torch.cuda.current_stream().cuda_stream), "delimit_lsc_forward")
 
 
