@@ -478,15 +478,28 @@ struct LscPlan {
 };
 
 int wgrad_splits(const LscDims& d, int64_t n_vox, int64_t* vps) {
-  // enough CTAs to fill the GPU about twice; each split at least 4096 voxels
+  // The weight-gradient GEMM runs persistent clusters of two CTAs (76 on 152 SMs)
+  // over (voxel split, shell, row-tile pair, column tile).  Pick the split count
+  // (1..8, each split at least 4096 voxels) whose tile count fills whole waves
+  // best; every extra split costs one more FP32 partial of the weight gradient.
   int64_t tiles = 0;
   for (int s = 0; s < d.s_out; ++s) {
-    const int64_t M = int64_t(d.c_out) * d.n_out, N = int64_t(d.win_hi[s] - d.win_lo[s]) * d.c_in * d.n_in + 1;
-    tiles += ((M + 127) / 128) * ((N + 127) / 128);
+    const int64_t M = int64_t(d.c_out) * d.n_out, N = int64_t(d.win_hi[s] - d.win_lo[s]) * d.c_in * d.n_in;
+    tiles += ((M + 255) / 256) * ((N + 255) / 256);
   }
-  int splits = int(std::max<int64_t>(1, (2 * 152 + tiles - 1) / std::max<int64_t>(1, tiles)));
-  splits = int(std::min<int64_t>(splits, std::max<int64_t>(1, n_vox / 4096)));
-  splits = std::min(splits, 64);
+  tiles = std::max<int64_t>(tiles, 1);
+  const int64_t slots = 76;
+  const int max_splits = int(std::max<int64_t>(1, std::min<int64_t>(8, n_vox / 4096)));
+  int splits = 1;
+  double best = 1e30;
+  for (int sp = 1; sp <= max_splits; ++sp) {
+    const double waves = double((tiles * sp + slots - 1) / slots) / sp;  // in units of one full-K tile
+    const double cost = waves * (1.0 + 0.02 * (sp - 1));
+    if (cost < best - 1e-9) {
+      best = cost;
+      splits = sp;
+    }
+  }
   int64_t per = (n_vox + splits - 1) / splits;
   per = (per + 127) / 128 * 128;
   if (per == 0) per = 128;

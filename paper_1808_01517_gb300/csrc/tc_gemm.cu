@@ -22,6 +22,8 @@
 #include <cstdlib>
 #include <atomic>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "tc_gemm.h"
 #include "tc_ptx.cuh"
@@ -83,18 +85,27 @@ __device__ __forceinline__ void vox_decode(const VoxParams& p, int64_t t, int& g
 // STAGED: the epilogue writes the tile to shared memory and stores it with TMA
 // through mapY (3-D {voxels, N rows of a group, groups}: rows past a group's N
 // are clipped); otherwise each lane stores its voxel's columns directly.
-template <int BN, int STAGES, bool STAGED>
+// CL = 2: a cluster of two CTAs computes a 256-voxel x BN tile with 2-SM MMAs
+// (M = 256): each CTA stages its own 128 voxels of A and BN/2 of the BN
+// operator columns, so a CTA takes in half the operator bytes per FLOP of the
+// single-CTA form.  The even CTA arms the stage barriers and issues the MMAs;
+// each CTA's TMEM receives its own 128 voxels x BN accumulator, drained by its
+// own epilogue, which hands the buffer back on the even CTA's barrier.
+// p.total_tiles counts cluster tiles (voxel-tile pairs x operator tiles).
+template <int BN, int STAGES, bool STAGED, int PASSES, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     vox_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const __grid_constant__ CUtensorMap mapY, const __grid_constant__ VoxParams p) {
   using namespace ptx;
-  constexpr int A_BYTES = 2 * kBoxBytes;        // 128 voxels x 64 K rows
-  constexpr int B_BYTES = (BN / 64) * kBoxBytes;  // BN columns x 64 K rows
+  static_assert(CL == 1 || CL == 2, "one CTA or a CTA pair");
+  static_assert(CL == 1 || (BN / 2) % 64 == 0, "each CTA of a pair holds whole 64-column operator atoms");
+  constexpr int A_BYTES = 2 * kBoxBytes;               // 128 voxels x 64 K rows
+  constexpr int B_BYTES = (BN / CL / 64) * kBoxBytes;  // this CTA's BN/CL columns x 64 K rows
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  constexpr int HB = BN / 2;                             // columns per staged pass
+  constexpr int HB = BN / PASSES;                        // columns per staged pass
   constexpr int STG_BYTES = STAGED ? HB * 128 * 2 : 0;  // [HB rows][64 voxels] x 2 voxel halves, BF16
   constexpr uint32_t TMEM_COLS = (2 * BN <= 256) ? 256 : 512;
-  constexpr uint32_t IDESC = idesc_bf16(128, BN, true, true);
+  constexpr uint32_t IDESC = idesc_bf16(128 * CL, BN, true, true);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -113,6 +124,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t drain_bar = smem_u32(bars + 2 * STAGES + 4);
   const uint32_t stg_ready_bar = smem_u32(bars + 2 * STAGES + 5);
   const uint32_t stg_free_bar = smem_u32(bars + 2 * STAGES + 6);
+  const int rank = CL > 1 ? (int)cluster_rank() : 0;
+  const int64_t t_first = CL > 1 ? (int64_t)cluster_id_x() : (int64_t)blockIdx.x;
+  const int64_t t_step = CL > 1 ? (int64_t)cluster_count_x() : (int64_t)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -121,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), kEpiWarps);
+      mbar_init(tempty_bar(b), CL * kEpiWarps);  // both CTAs' epilogues release the pair's accumulator
     }
     mbar_init(drain_bar, 1);
     mbar_init(stg_ready_bar, kEpiWarps);
@@ -132,9 +146,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     prefetch_tmap(&mapB);
     if (STAGED) prefetch_tmap(&mapY);
   }
+  if (CL > 1) cluster_sync();  // the peer's barriers exist before any copy or commit reaches them
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
-    tmem_relinquish();
+    if (CL > 1) {
+      tmem_alloc_pair(smem_u32(tmem_slot), TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -142,14 +162,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producer (both CTAs of a pair) ----------------
     int stage = 0;
     uint32_t phase = 0;
     int pend[STAGES];
     for (int s = 0; s < STAGES; ++s) pend[s] = -1;
-    for (int64_t t = blockIdx.x; t < p.total_tiles && !*abort_flag; t += gridDim.x) {
+    for (int64_t t = t_first; t < p.total_tiles && !*abort_flag; t += t_step) {
       int g, mt, nt;
       vox_decode(p, t, g, mt, nt);
+      mt = mt * CL + rank;
       const VoxGroup& G = p.g[g];
       const int nkb = (G.K + kBK - 1) / kBK;
       bool ok = true;
@@ -159,13 +180,23 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         const uint32_t a_dst = sbase + stage * STAGE_BYTES, b_dst = a_dst + A_BYTES;
-        mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
         const int krow = G.a_k0 + kb * kBK;
-        tma_load_2d(&mapA, full_bar(stage), a_dst, mt * 128, krow);
-        tma_load_2d(&mapA, full_bar(stage), a_dst + kBoxBytes, mt * 128 + 64, krow);
+        const int ncol = G.b_n0 + nt * BN + rank * (BN / CL);
+        if (CL > 1) {
+          // both CTAs' bytes complete on the even CTA's barrier, which that CTA arms
+          const uint32_t fb = mapa_shared(full_bar(stage), 0);
+          if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), CL * STAGE_BYTES);
+          tma_load_2d_pair(&mapA, fb, a_dst, mt * 128, krow);
+          tma_load_2d_pair(&mapA, fb, a_dst + kBoxBytes, mt * 128 + 64, krow);
 #pragma unroll
-        for (int j = 0; j < BN / 64; ++j)
-          tma_load_2d(&mapB, full_bar(stage), b_dst + j * kBoxBytes, G.b_n0 + nt * BN + j * 64, krow);
+          for (int j = 0; j < BN / CL / 64; ++j) tma_load_2d_pair(&mapB, fb, b_dst + j * kBoxBytes, ncol + j * 64, krow);
+        } else {
+          mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
+          tma_load_2d(&mapA, full_bar(stage), a_dst, mt * 128, krow);
+          tma_load_2d(&mapA, full_bar(stage), a_dst + kBoxBytes, mt * 128 + 64, krow);
+#pragma unroll
+          for (int j = 0; j < BN / 64; ++j) tma_load_2d(&mapB, full_bar(stage), b_dst + j * kBoxBytes, ncol + j * 64, krow);
+        }
         pend[stage] = (int)phase;
         if (++stage == STAGES) {
           stage = 0;
@@ -174,16 +205,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
     }
-    // copies still in flight complete before the CTA may exit
-    for (int s = 0; s < STAGES; ++s)
-      if (pend[s] >= 0) wait_drain(full_bar(s), (uint32_t)pend[s], p.err, kErrDrain);
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
+    // copies still in flight complete before the CTA may exit (a pair's odd CTA is
+    // covered by the even CTA's drain and the closing cluster barrier)
+    if (rank == 0)
+      for (int s = 0; s < STAGES; ++s)
+        if (pend[s] >= 0) wait_drain(full_bar(s), (uint32_t)pend[s], p.err, kErrDrain);
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ---------------- MMA issuer (the even CTA of a pair) ----------------
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int64_t t = blockIdx.x; t < p.total_tiles && !*abort_flag; t += gridDim.x) {
+    for (int64_t t = t_first; t < p.total_tiles && !*abort_flag; t += t_step) {
       int g, mt, nt;
       vox_decode(p, t, g, mt, nt);
       const int nkb = (p.g[g].K + kBK - 1) / kBK;
@@ -204,20 +237,32 @@ __global__ void __launch_bounds__(kThreads, 1)
           // 8-row K groups 1024 B apart (SBO); 16 K rows = 2048 B per MMA.
           const uint64_t ad = umma_desc(a_src + k * 2048, kBoxBytes, 1024, kSwizzle128B);
           const uint64_t bd = umma_desc(b_src + k * 2048, kBoxBytes, 1024, kSwizzle128B);
-          mma_bf16(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+          if (CL > 1)
+            mma_bf16_pair(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+          else
+            mma_bf16(d_tmem, ad, bd, IDESC, (kb | k) != 0);
         }
-        mma_commit(empty_bar(stage));
+        if (CL > 1)
+          mma_commit_pair_mc(empty_bar(stage), 0x3);  // both CTAs' producers refill this stage
+        else
+          mma_commit(empty_bar(stage));
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1u;
         }
       }
       if (!ok) break;
-      mma_commit(tfull_bar(acc));
+      if (CL > 1)
+        mma_commit_pair_mc(tfull_bar(acc), 0x3);
+      else
+        mma_commit(tfull_bar(acc));
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
-    mma_commit(drain_bar);
+    if (CL > 1)
+      mma_commit_pair(drain_bar);
+    else
+      mma_commit(drain_bar);
     wait_drain(drain_bar, 0, p.err, kErrDrain);
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
@@ -227,23 +272,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t acc_phase = 0;
     int it = 0;
     const int h = q >> 1, xl = (q & 1) * 32 + lane;
-    for (int64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x, ++it) {
+    for (int64_t t = t_first; t < p.total_tiles; t += t_step, ++it) {
       int g, mt, nt;
       vox_decode(p, t, g, mt, nt);
+      mt = mt * CL + rank;
       const VoxGroup& G = p.g[g];
       bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTmemFull);
-      if (STAGED) ok = ok && wait_bounded(stg_free_bar, (uint32_t)((2 * it) & 1) ^ 1u, abort_flag, p.err, kErrTmemEmpty);
+      if (STAGED) ok = ok && wait_bounded(stg_free_bar, (uint32_t)((PASSES * it) & 1) ^ 1u, abort_flag, p.err, kErrTmemEmpty);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const int64_t vox = (int64_t)mt * 128 + q * 32 + lane;
       const bool vok = vox < p.n_vox;
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+      // accumulator released to the MMA issuer (the even CTA's barrier for a pair)
+      const uint32_t tempty = CL > 1 ? mapa_shared(tempty_bar(acc), 0) : tempty_bar(acc);
       if (STAGED) {
-        // two passes of HB columns through one staging tile, each stored by TMA
+        // PASSES passes of HB columns through one staging tile, each stored by TMA
         bool alive = true;
-        for (int pass = 0; pass < 2 && alive; ++pass) {
-          const int use = 2 * it + pass;
-          if (pass == 1) {
+        for (int pass = 0; pass < PASSES && alive; ++pass) {
+          const int use = PASSES * it + pass;
+          if (pass > 0) {
             bool okf = wait_bounded(stg_free_bar, (uint32_t)(use & 1) ^ 1u, abort_flag, p.err, kErrTmemEmpty);
             if (!__all_sync(0xffffffffu, okf)) {
               alive = false;
@@ -273,11 +321,16 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
           }
-          if (pass == 1) tc_fence_before();
+          if (pass == PASSES - 1) tc_fence_before();
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) {
-            if (pass == 1) mbar_arrive(tempty_bar(acc));
+            if (pass == PASSES - 1) {
+              if (CL > 1)
+                mbar_arrive_cluster(tempty);
+              else
+                mbar_arrive(tempty);
+            }
             mbar_arrive(stg_ready_bar);
           }
           if (warp == 2) {
@@ -324,7 +377,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(tempty_bar(acc));
+        if (lane == 0) {
+          if (CL > 1)
+            mbar_arrive_cluster(tempty);
+          else
+            mbar_arrive(tempty);
+        }
       }
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
@@ -333,9 +391,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  // a pair frees its TMEM once both epilogues are done with it; after this point no
+  // copy, commit or arrival of either CTA targets the other
+  if (CL > 1) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, TMEM_COLS);
+    if (CL > 1)
+      tmem_dealloc_pair(tmem_base, TMEM_COLS);
+    else
+      tmem_dealloc(tmem_base, TMEM_COLS);
   }
 }
 
@@ -367,16 +431,21 @@ __device__ __forceinline__ void wg_decode(const WgParams& p, int64_t t, int& spl
   nt = (int)(r % p.g[g].n_tiles);
 }
 
-template <int BN, int STAGES>
+// CL = 2: a cluster of two CTAs computes a 256-row x BN tile with 2-SM MMAs:
+// each CTA stages its own 128 output rows of dY and BN/2 of the BN input rows
+// of X; the even CTA arms the stage barriers and issues the MMAs, each CTA
+// drains its own 128 rows.  m_tiles in the groups then counts row-tile pairs.
+template <int BN, int STAGES, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     wgrad_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                  const __grid_constant__ WgParams p) {
   using namespace ptx;
-  constexpr int A_BYTES = 128 * 128;  // 128 rows x 64 voxels
-  constexpr int B_BYTES = BN * 128;   // BN rows x 64 voxels
+  static_assert(CL == 1 || CL == 2, "one CTA or a CTA pair");
+  constexpr int A_BYTES = 128 * 128;      // 128 rows x 64 voxels
+  constexpr int B_BYTES = BN / CL * 128;  // this CTA's BN/CL rows x 64 voxels
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   constexpr uint32_t TMEM_COLS = (2 * BN <= 256) ? 256 : 512;
-  constexpr uint32_t IDESC = idesc_bf16(128, BN, false, false);
+  constexpr uint32_t IDESC = idesc_bf16(128 * CL, BN, false, false);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -391,6 +460,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto tfull_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
   auto tempty_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
   const uint32_t drain_bar = smem_u32(bars + 2 * STAGES + 4);
+  const int rank = CL > 1 ? (int)cluster_rank() : 0;
+  const int64_t t_first = CL > 1 ? (int64_t)cluster_id_x() : (int64_t)blockIdx.x;
+  const int64_t t_step = CL > 1 ? (int64_t)cluster_count_x() : (int64_t)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -399,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), kEpiWarps);
+      mbar_init(tempty_bar(b), CL * kEpiWarps);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -407,9 +479,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     prefetch_tmap(&mapA);
     prefetch_tmap(&mapB);
   }
+  if (CL > 1) cluster_sync();  // the peer's barriers exist before any copy or commit reaches them
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
-    tmem_relinquish();
+    if (CL > 1) {
+      tmem_alloc_pair(smem_u32(tmem_slot), TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -421,9 +499,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0;
     int pend[STAGES];
     for (int s = 0; s < STAGES; ++s) pend[s] = -1;
-    for (int64_t t = blockIdx.x; t < p.total_tiles && !*abort_flag; t += gridDim.x) {
+    for (int64_t t = t_first; t < p.total_tiles && !*abort_flag; t += t_step) {
       int split, g, mt, nt;
       wg_decode(p, t, split, g, mt, nt);
+      mt = mt * CL + rank;
       const WgGroup& G = p.g[g];
       const int64_t vs = (int64_t)split * p.vps, ve = min(p.n_vox, vs + p.vps);
       const int nkb = (int)((ve - vs + 63) / 64);
@@ -434,10 +513,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         const uint32_t a_dst = sbase + stage * STAGE_BYTES, b_dst = a_dst + A_BYTES;
-        mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
         const int vx = (int)(vs + (int64_t)kb * 64);
-        tma_load_2d(&mapA, full_bar(stage), a_dst, vx, (int)(G.m_row0 + (int64_t)mt * 128));
-        tma_load_2d(&mapB, full_bar(stage), b_dst, vx, (int)(G.x_row0 + (int64_t)nt * BN));
+        const int arow = (int)(G.m_row0 + (int64_t)mt * 128);
+        const int brow = (int)(G.x_row0 + (int64_t)nt * BN + rank * (BN / CL));
+        if (CL > 1) {
+          const uint32_t fb = mapa_shared(full_bar(stage), 0);
+          if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), CL * STAGE_BYTES);
+          tma_load_2d_pair(&mapA, fb, a_dst, vx, arow);
+          tma_load_2d_pair(&mapB, fb, b_dst, vx, brow);
+        } else {
+          mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
+          tma_load_2d(&mapA, full_bar(stage), a_dst, vx, arow);
+          tma_load_2d(&mapB, full_bar(stage), b_dst, vx, brow);
+        }
         pend[stage] = (int)phase;
         if (++stage == STAGES) {
           stage = 0;
@@ -446,14 +534,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
     }
-    for (int s = 0; s < STAGES; ++s)
-      if (pend[s] >= 0) wait_drain(full_bar(s), (uint32_t)pend[s], p.err, kErrDrain);
-  } else if (warp == 1 && lane == 0) {
+    if (rank == 0)
+      for (int s = 0; s < STAGES; ++s)
+        if (pend[s] >= 0) wait_drain(full_bar(s), (uint32_t)pend[s], p.err, kErrDrain);
+  } else if (warp == 1 && lane == 0 && rank == 0) {
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int64_t t = blockIdx.x; t < p.total_tiles && !*abort_flag; t += gridDim.x) {
+    for (int64_t t = t_first; t < p.total_tiles && !*abort_flag; t += t_step) {
       int split, g, mt, nt;
       wg_decode(p, t, split, g, mt, nt);
       const int64_t vs = (int64_t)split * p.vps, ve = min(p.n_vox, vs + p.vps);
@@ -475,29 +564,42 @@ __global__ void __launch_bounds__(kThreads, 1)
           // 16 voxels = 32 B per MMA inside the swizzle atom.
           const uint64_t ad = umma_desc(a_src + k * 32, 16, 1024, kSwizzle128B);
           const uint64_t bd = umma_desc(b_src + k * 32, 16, 1024, kSwizzle128B);
-          mma_bf16(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+          if (CL > 1)
+            mma_bf16_pair(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+          else
+            mma_bf16(d_tmem, ad, bd, IDESC, (kb | k) != 0);
         }
-        mma_commit(empty_bar(stage));
+        if (CL > 1)
+          mma_commit_pair_mc(empty_bar(stage), 0x3);
+        else
+          mma_commit(empty_bar(stage));
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1u;
         }
       }
       if (!ok) break;
-      mma_commit(tfull_bar(acc));
+      if (CL > 1)
+        mma_commit_pair_mc(tfull_bar(acc), 0x3);
+      else
+        mma_commit(tfull_bar(acc));
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
-    mma_commit(drain_bar);
+    if (CL > 1)
+      mma_commit_pair(drain_bar);
+    else
+      mma_commit(drain_bar);
     wait_drain(drain_bar, 0, p.err, kErrDrain);
   } else if (warp >= 2) {
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;  // 16-column chunks 2k + half
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+    for (int64_t t = t_first; t < p.total_tiles; t += t_step) {
       int split, g, mt, nt;
       wg_decode(p, t, split, g, mt, nt);
+      mt = mt * CL + rank;
       const WgGroup& G = p.g[g];
       bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTmemFull);
       ok = __all_sync(0xffffffffu, ok);
@@ -528,16 +630,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty_bar(acc));
+      if (lane == 0) {
+        if (CL > 1)
+          mbar_arrive_cluster(mapa_shared(tempty_bar(acc), 0));
+        else
+          mbar_arrive(tempty_bar(acc));
+      }
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
   }
   tc_fence_before();
   __syncthreads();
+  // a pair frees its TMEM once both epilogues are done with it; after this point no
+  // copy, commit or arrival of either CTA targets the other
+  if (CL > 1) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, TMEM_COLS);
+    if (CL > 1)
+      tmem_dealloc_pair(tmem_base, TMEM_COLS);
+    else
+      tmem_dealloc(tmem_base, TMEM_COLS);
   }
 }
 
@@ -621,10 +734,16 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, bool STAGED>
+// forward tiles: one staged pass of the full tile (measured faster than two half passes)
+constexpr int kFwdPasses = 1;
+
+// operand stages that fit beside the staging tile in the ~226 KiB a CTA may use
+template <int BN, bool STAGED, int CL>
 constexpr int vox_stages() {
-  // operand ring + (staged) one BN x 128 BF16 output tile within ~210 KiB
-  return STAGED ? (BN == 256 ? 4 : (BN == 192 ? 5 : 6)) : ((BN == 256) ? 4 : (BN == 192 ? 5 : 6));
+  constexpr int stage = 2 * kBoxBytes + (BN / CL / 64) * kBoxBytes;
+  constexpr int stg = STAGED ? BN / kFwdPasses * 256 : 0;
+  constexpr int n = (226 * 1024 - 2048 - stg) / stage;
+  return n > 8 ? 8 : n;
 }
 
 template <int BN, int STAGES>
@@ -632,18 +751,100 @@ constexpr size_t smem_bytes(int a_bytes, int b_bytes) {
   return 1024 + (size_t)STAGES * (a_bytes + b_bytes) + (2 * STAGES + 5) * 8 + 16;
 }
 
-template <int BN, bool STAGED>
+int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return (v && *v) ? atoi(v) : dflt;
+}
+
+// CTAs per cluster of one GEMM: DELIMIT_GEMM_CLUSTER (1 or 2) overrides the
+// per-GEMM default (2 = operator tile multicast).
+int gemm_cluster(int dflt) {
+  const int v = env_int("DELIMIT_GEMM_CLUSTER", dflt);
+  return v == 1 ? 1 : 2;
+}
+
+// Clusters of `cl` CTAs of `kern` (with `smem` bytes) that fit on the device at
+// once; 0 if the query fails.  Cached per device and kernel.
+int max_active_clusters(const void* kern, size_t smem, int cl) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<int, const void*>, int>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& c : cache)
+    if (c.first.first == dev && c.first.second == kern) return c.second;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(cl * 64));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cache.push_back({{dev, kern}, n});
+  return n;
+}
+
+// Persistent launch: min(tiles, resident) CTAs (cl = 1) or clusters of cl CTAs.
+template <typename... Params, typename... Args>
+cudaError_t launch_persistent(void (*kern)(Params...), int64_t tiles, int cl, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (cl > 1) {
+    const int clusters = max_active_clusters(reinterpret_cast<const void*>(kern), smem, cl);
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    cfg.gridDim = dim3((unsigned)(std::min<int64_t>(tiles, clusters) * cl));
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  } else {
+    cfg.gridDim = dim3((unsigned)std::min<int64_t>(tiles, std::max(1, dev_info().sms)));
+  }
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+  count_launch();
+  return e;
+}
+
+template <int BN, bool STAGED, int CL>
 cudaError_t launch_vox(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& my, const VoxParams& p,
                        cudaStream_t st) {
-  constexpr int S = vox_stages<BN, STAGED>();
-  const size_t smem = smem_bytes<BN, S>(2 * kBoxBytes, (BN / 64) * kBoxBytes) + (STAGED ? BN * 128 : 0) + 16;
-  auto kern = vox_gemm_kernel<BN, S, STAGED>;
+  constexpr int S = vox_stages<BN, STAGED, CL>();
+  const size_t smem =
+      smem_bytes<BN, S>(2 * kBoxBytes, (BN / CL / 64) * kBoxBytes) + (STAGED ? BN / kFwdPasses * 256 : 0) + 16;
+  auto kern = vox_gemm_kernel<BN, S, STAGED, kFwdPasses, CL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int sms = std::max(1, dev_info().sms);
-  const unsigned grid = (unsigned)std::min<int64_t>(p.total_tiles, sms);
-  { kern<<<grid, kThreads, smem, st>>>(ma, mb, my, p); count_launch(); }
+  e = launch_persistent(kern, p.total_tiles, CL, smem, st, ma, mb, my, p);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+template <int BN, bool STAGED>
+cudaError_t launch_vox_cl(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& my, VoxParams& p, int cl,
+                          cudaStream_t st) {
+  if constexpr ((BN / 2) % 64 == 0) {
+    if (cl > 1) {
+      p.total_tiles = (int64_t)((p.m_tiles + 1) / 2) * p.tiles_per_m;
+      return launch_vox<BN, STAGED, 2>(ma, mb, my, p, st);
+    }
+  }
+  p.total_tiles = (int64_t)p.m_tiles * p.tiles_per_m;
+  return launch_vox<BN, STAGED, 1>(ma, mb, my, p, st);
 }
 
 // choose the N tile that wastes the fewest columns over the groups (ties: larger)
@@ -664,8 +865,11 @@ int pick_bn(const int* Ns, int n) {
 
 // The staged epilogue is used when every group has the same N (one 3-D output
 // map covers them) and the tile is at most 192 wide (ring + tile fit in smem).
-cudaError_t run_vox(const CUtensorMap& ma, const CUtensorMap& mb, VoxParams& p, int bn, bool staged_ok,
+// cl = 2 runs CTA pairs with 2-SM MMAs; a pair splits its bn operator columns
+// into two halves of whole 64-column atoms, so bn = 192 becomes 256 there.
+cudaError_t run_vox(const CUtensorMap& ma, const CUtensorMap& mb, VoxParams& p, int bn, bool staged_ok, int cl,
                     void* Y, int64_t ldy, cudaStream_t st) {
+  if (cl > 1 && bn == 192) bn = 256;
   p.tiles_per_m = 0;
   bool same_n = true;
   for (int i = 0; i < p.n_groups; ++i) {
@@ -677,12 +881,12 @@ cudaError_t run_vox(const CUtensorMap& ma, const CUtensorMap& mb, VoxParams& p, 
   if (p.total_tiles == 0) return cudaSuccess;
   CUtensorMap my;
   memset(&my, 0, sizeof my);
-  bool staged = staged_ok && same_n && bn <= 192;
+  bool staged = staged_ok && same_n && (bn <= 192 || cl > 1);
   if (staged) {
     auto fn = encode_fn();
     cuuint64_t dims[3] = {(cuuint64_t)p.n_vox, (cuuint64_t)p.g[0].N, (cuuint64_t)p.n_groups};
     cuuint64_t strides[2] = {(cuuint64_t)ldy * 2, (cuuint64_t)(p.g[0].N * ldy * 2)};
-    cuuint32_t box[3] = {64, (cuuint32_t)(bn / 2), 1};
+    cuuint32_t box[3] = {64, (cuuint32_t)(bn / kFwdPasses), 1};
     cuuint32_t es[3] = {1, 1, 1};
     staged = fn(&my, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Y, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -690,20 +894,16 @@ cudaError_t run_vox(const CUtensorMap& ma, const CUtensorMap& mb, VoxParams& p, 
   }
   if (staged) {
     switch (bn) {
-      case 192: return launch_vox<192, true>(ma, mb, my, p, st);
-      default: return launch_vox<128, true>(ma, mb, my, p, st);
+      case 256: return launch_vox_cl<256, true>(ma, mb, my, p, cl, st);
+      case 192: return launch_vox_cl<192, true>(ma, mb, my, p, cl, st);
+      default: return launch_vox_cl<128, true>(ma, mb, my, p, cl, st);
     }
   }
   switch (bn) {
-    case 256: return launch_vox<256, false>(ma, mb, my, p, st);
-    case 192: return launch_vox<192, false>(ma, mb, my, p, st);
-    default: return launch_vox<128, false>(ma, mb, my, p, st);
+    case 256: return launch_vox_cl<256, false>(ma, mb, my, p, cl, st);
+    case 192: return launch_vox_cl<192, false>(ma, mb, my, p, cl, st);
+    default: return launch_vox_cl<128, false>(ma, mb, my, p, cl, st);
   }
-}
-
-int env_int(const char* name, int dflt) {
-  const char* v = getenv(name);
-  return (v && *v) ? atoi(v) : dflt;
 }
 
 }  // namespace
@@ -749,7 +949,7 @@ cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* Wt, cons
   int bn = pick_bn(Ns, d.s_out);
   if (bn == 256) bn = ((Ns[0] % 192) == 0) ? 192 : 128;
   bn = env_int("DELIMIT_FWD_BN", bn);
-  return run_vox(ma, mb, p, bn, env_int("DELIMIT_FWD_STAGED", 1) != 0, Y, ldy, st);
+  return run_vox(ma, mb, p, bn, env_int("DELIMIT_FWD_STAGED", 1) != 0, gemm_cluster(2), Y, ldy, st);
 }
 
 cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* dX, int64_t n_vox, int64_t lddy,
@@ -778,16 +978,28 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* 
   p.Y = reinterpret_cast<__nv_bfloat16*>(dX);
   p.bias = nullptr;
   p.err = err;
-  return run_vox(ma, mb, p, env_int("DELIMIT_DGRAD_BN", pick_bn(Ns, d.s_in)), env_int("DELIMIT_DGRAD_STAGED", 0) != 0,
-                 dX, lddx, st);
+  return run_vox(ma, mb, p, env_int("DELIMIT_DGRAD_BN", pick_bn(Ns, d.s_in)),
+                 env_int("DELIMIT_DGRAD_STAGED", 0) != 0, gemm_cluster(2), dX, lddx, st);
+}
+
+template <int BN, int S, int CL>
+cudaError_t launch_wgrad(const CUtensorMap& ma, const CUtensorMap& mb, const WgParams& p, cudaStream_t st) {
+  const size_t smem = smem_bytes<BN, S>(128 * 128, BN / CL * 128);
+  auto kern = wgrad_kernel<BN, S, CL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = launch_persistent(kern, p.total_tiles, CL, smem, st, ma, mb, p);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float* P, int64_t ldp, int64_t split_stride,
                          int splits, int64_t vps, int64_t n_vox, int64_t lddy, int64_t ldx, int* err, cudaStream_t st) {
-  constexpr int BN = 256, S = 4;
+  constexpr int BN = 256;
+  const int cl = gemm_cluster(2);
   CUtensorMap ma, mb;
   if (!make_map(&ma, dY, (uint64_t)n_vox, (uint64_t)d.rows_out, (uint64_t)lddy, 64, 128)) return cudaErrorInvalidValue;
-  if (!make_map(&mb, X, (uint64_t)n_vox, (uint64_t)d.rows_in, (uint64_t)ldx, 64, BN)) return cudaErrorInvalidValue;
+  if (!make_map(&mb, X, (uint64_t)n_vox, (uint64_t)d.rows_in, (uint64_t)ldx, 64, BN / cl)) return cudaErrorInvalidValue;
   if (vps % 64 != 0) return cudaErrorInvalidValue;
   WgParams p;
   memset(&p, 0, sizeof p);
@@ -800,7 +1012,7 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
     G.n_col0 = G.x_row0;
     G.M = per_out;
     G.N = (d.win_hi[s] - d.win_lo[s]) * per_in;
-    G.m_tiles = (G.M + 127) / 128;
+    G.m_tiles = ((G.M + 127) / 128 + cl - 1) / cl;  // tile pairs with clusters of two
     G.n_tiles = (G.N + BN - 1) / BN;
     p.tiles_per_split += (int64_t)G.m_tiles * G.n_tiles;
   }
@@ -813,15 +1025,11 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
   p.split_stride = split_stride;
   p.P = P;
   p.err = err;
-  const size_t smem = smem_bytes<BN, S>(128 * 128, BN * 128);
-  auto kern = wgrad_kernel<BN, S>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int sms = std::max(1, dev_info().sms);
+  cudaError_t e = cudaSuccess;
   if (p.total_tiles > 0) {
     TraceScope trace("lsc_wgrad_gemm", st);
-    { kern<<<(unsigned)std::min<int64_t>(p.total_tiles, sms), kThreads, smem, st>>>(ma, mb, p); count_launch(); }
-    e = cudaGetLastError();
+    // stages: 4 x 48 KiB for one CTA, 6 x 32 KiB per CTA of a pair
+    e = cl > 1 ? launch_wgrad<BN, 6, 2>(ma, mb, p, st) : launch_wgrad<BN, 4, 1>(ma, mb, p, st);
     if (e != cudaSuccess) return e;
   }
   const int64_t warps = d.rows_out * splits;

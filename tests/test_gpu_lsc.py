@@ -2,7 +2,8 @@
 
 All calls go through the C ABI.  FP32 path: relative L2 <= 1e-5 per output;
 BF16 path (bf16 activations, fp32 accumulation, fp32 master weights): <= 1e-2.
-Both the tensor-core and the CUDA-core BF16 kernels are checked.
+Both the tensor-core and the CUDA-core BF16 kernels are checked, the former
+with and without two-CTA clusters (odd voxel-tile and row-tile counts included).
 """
 import numpy as np
 import pytest
@@ -73,9 +74,12 @@ def _gpu_lsc(lg, c, w, b, d, ci, co, prec):
             rows_to_sh(din.float().cpu().numpy(), lg.s_in, ci, lg.n_in), dw.cpu().numpy(), db.cpu().numpy())
 
 
-@pytest.mark.parametrize("prec,tc", [("f32", False), ("bf16", True), ("bf16", False)])
+@pytest.mark.parametrize("prec,tc,cluster", [("f32", False, 2), ("bf16", True, 2), ("bf16", True, 1),
+                                             ("bf16", False, 2)])
 @pytest.mark.parametrize("case", list(CASES))
-def test_lsc_vs_oracle(case, prec, tc):
+def test_lsc_vs_oracle(case, prec, tc, cluster, monkeypatch):
+    # cluster: CTAs per cluster of the tensor-core GEMMs (2 = operator tiles multicast)
+    monkeypatch.setenv("DELIMIT_GEMM_CLUSTER", str(cluster))
     cfg = CASES[case]
     og, lg = _setup(cfg)
     c, w, b, d = _inputs(og, cfg)
