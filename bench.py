@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--no-extras", action="store_true", help="skip fp32 / e2e / cpu legs (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip fp32 / e2e / cpu / transform legs (profiling runs)")
+    ap.add_argument("--transform-vox", type=int, default=1 << 20,
+                    help="voxels of the stand-alone transform leg (one channel, 3 x 90 directions)")
     return ap.parse_args()
 
 
@@ -354,6 +356,8 @@ def main():
         torch.cuda.empty_cache()
         # ---- end to end through host buffers ----
         extras["e2e"] = run_e2e(ch, args.e2e_steps)
+        # ---- stand-alone transforms at 1,048,576 voxels (FP32 and BF16-in / FP32-out) ----
+        extras["transforms"] = run_transforms(cfg, dirs, bvals, args.transform_vox, hbm)
         # ---- oracle on the host cores ----
         vps, nv, tw = time_oracle(cfg, dirs, bvals, args.cpu_seconds)
         extras["cpu_baseline"] = {"value": vps, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
@@ -372,6 +376,7 @@ def main():
         line.update({k: v for k, v in extras.items() if k in ("e2e", "cpu_baseline")})
         line["fp32"] = extras.get("fp32")
         line["err_vs_oracle_bf16"] = extras.get("err_vs_oracle_bf16")
+        line["transforms"] = extras.get("transforms")
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -400,6 +405,62 @@ def sampled_errors(ch, cfg, dirs, bvals, idx):
     got_d = rows_to_vcd(ch.ds_in[:, idx], cfg.c_in)
     rel = lambda a, r: float(np.linalg.norm(a - r) / np.linalg.norm(r))  # noqa: E731
     return {"s_out": rel(got_s, s_out), "ds_in": rel(got_d, ds_in), "voxels": int(len(idx))}
+
+
+def run_transforms(cfg, dirs, bvals, V, hbm_gbs, steps=20, warm=3, n_check=4096):
+    """Signal2SH and SH2Signal alone on V voxels of a one-channel 3 x 90-direction
+    fibre signal, FP32 in / FP32 out and BF16 in / FP32 out.  Per variant: device
+    time (CUDA events on the launch stream, inputs larger than L2), algorithmic
+    bytes (input read once, output written once), fraction of the measured HBM
+    copy bandwidth, and relative L2 error against the FP64 oracle on n_check
+    sampled voxels."""
+    import torch
+    from oracle import sh as osh
+    from paper_1808_01517_gb300 import _lib as L
+    from paper_1808_01517_gb300 import layers, synth
+    basis = L.SHBasis(dirs, bvals, cfg.order, cfg.lam)
+    ob = osh.SHBasisOracle(dirs, bvals, cfg.order, cfg.lam)
+    S, N, nd = basis.n_shells, basis.n_coef, basis.n_dirs
+    sig32 = layers.empty_act(nd, V, torch.float32)
+    sig32.copy_(synth.fibre_signal_torch(dirs, bvals, V, seed=cfg.seed + 5))
+    sh32 = layers.transform("signal2sh", basis, sig32, 1)
+    idx = synth.voxel_subset(V, n_check, seed=cfg.seed + 98)
+    idx_t = torch.from_numpy(idx).cuda()
+    out = {}
+    for kind, src32 in (("signal2sh", sig32), ("sh2signal", sh32)):
+        for tag, dt in (("f32", torch.float32), ("bf16_in", torch.bfloat16)):
+            x = layers.empty_act(src32.shape[0], V, dt)
+            x.copy_(src32)
+            rows_out = S * N if kind == "signal2sh" else nd
+            y = layers.empty_act(rows_out, V, torch.float32)
+            for _ in range(warm):
+                layers.transform(kind, basis, x, 1, torch.float32, out=y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(steps):
+                layers.transform(kind, basis, x, 1, torch.float32, out=y)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            by = x.shape[0] * V * x.element_size() + rows_out * V * 4
+            # FP64 oracle on the sampled voxels, from the same (rounded) input values
+            xin = x[:, idx_t].double().cpu().numpy()
+            if kind == "signal2sh":
+                ref = ob.signal2sh(xin.T[:, None, :])[:, 0]  # [n, S, N]
+                ref_rows = ref.transpose(1, 2, 0).reshape(S * N, -1)
+            else:
+                ref = ob.sh2signal(xin.T.reshape(-1, S, N)[:, None])  # [n, 1, dirs]
+                ref_rows = ref[:, 0].T
+            got = y[:, idx_t].double().cpu().numpy()
+            err = float(np.linalg.norm(got - ref_rows) / np.linalg.norm(ref_rows))
+            out[f"{kind}_{tag}"] = {"ms": ms, "voxels_per_s": V / (ms * 1e-3), "bytes": int(by),
+                                    "gbs": by / (ms * 1e-3) / 1e9, "frac_hbm": by / (ms * 1e-3) / 1e9 / hbm_gbs,
+                                    "err_vs_oracle": err}
+            del x, y
+    out["config"] = {"n_vox": V, "channels": 1, "shells": list(cfg.dirs_per_shell), "sh_order": cfg.order,
+                     "check_voxels": n_check, "timed_steps": steps}
+    return out
 
 
 def run_e2e(ch, steps):

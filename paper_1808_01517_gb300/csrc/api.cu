@@ -485,7 +485,7 @@ int wgrad_splits(const LscDims& d, int64_t n_vox, int64_t* vps) {
   int64_t tiles = 0;
   for (int s = 0; s < d.s_out; ++s) {
     const int64_t M = int64_t(d.c_out) * d.n_out, N = int64_t(d.win_hi[s] - d.win_lo[s]) * d.c_in * d.n_in;
-    tiles += ((M + 255) / 256) * ((N + 255) / 256);
+    tiles += ((M + 255) / 256) * ((N + 239) / 240);  // row-tile pairs x 240-column tiles
   }
   tiles = std::max<int64_t>(tiles, 1);
   const int64_t slots = 76;
@@ -508,6 +508,12 @@ int wgrad_splits(const LscDims& d, int64_t n_vox, int64_t* vps) {
   *vps = per;
   return splits;
 }
+
+// Whether the forward reads the transposed operator Wt (the CUDA-core path always
+// does; the tensor-core path only when W's column blocks carry padding).  The same
+// answer in a forward and the backward that follows keeps DELIMIT_LSC_OPERATOR_READY
+// valid between them.
+bool needs_wt(const LscDims& d, bool tc) { return !tc || !tc_forward_reads_w(d); }
 
 bool make_plan(const delimit_lsc_geometry* g, int64_t n_vox, int c_in, int c_out, delimit_dtype t, LscPlan& p) {
   if (!g || c_in < 1 || c_out < 1 || n_vox < 0 || c_in > 4096 || c_out > 4096 || !valid_dtype(t)) return false;
@@ -581,13 +587,14 @@ delimit_status delimit_lsc_forward(const delimit_lsc_geometry* g, const void* sh
   void* Wt = base + p.off_Wt;
   float* bias = reinterpret_cast<float*>(base + p.off_bias);
   cudaError_t e = cudaSuccess;
+  const LscDims& d = p.d;
+  const bool tc = act_t == DELIMIT_BF16 && tc_gemm_supported(d, n_vox, ld_in, ld_out);
   if (!(flags & DELIMIT_LSC_OPERATOR_READY)) {
-    e = launch_build_w(p.d, w, b, g->d_M, g->d_q, W, Wt, bias, int(act_t), cs);
+    e = launch_build_w(d, w, b, g->d_M, g->d_q, W, needs_wt(d, tc) ? Wt : nullptr, bias, int(act_t), cs);
     if (e != cudaSuccess) return cuda_fail(e, "build_w launch");
   }
-  const LscDims& d = p.d;
-  if (act_t == DELIMIT_BF16 && tc_gemm_supported(d, n_vox, ld_in, ld_out)) {
-    e = tc_lsc_forward(d, sh_in, Wt, bias, sh_out, n_vox, ld_in, ld_out, g->err_word, cs);
+  if (tc) {
+    e = tc_lsc_forward(d, sh_in, W, Wt, bias, sh_out, n_vox, ld_in, ld_out, g->err_word, cs);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core LSC forward launch");
     return DELIMIT_OK;
   }
@@ -650,7 +657,8 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
     void* W = base + p.off_W;
     void* Wt = base + p.off_Wt;
     if (!(flags & DELIMIT_LSC_OPERATOR_READY)) {
-      e = launch_build_w(d, w, nullptr, g->d_M, g->d_q, W, Wt, nullptr, int(act_t), cs);
+      const bool tc = act_t == DELIMIT_BF16 && tc_gemm_supported(d, n_vox, ld_in, ld_out);
+      e = launch_build_w(d, w, nullptr, g->d_M, g->d_q, W, needs_wt(d, tc) ? Wt : nullptr, nullptr, int(act_t), cs);
       if (e != cudaSuccess) return cuda_fail(e, "build_w launch");
     }
     bool all_fed = true;

@@ -84,8 +84,144 @@ __global__ void __launch_bounds__(128) transform_simt_kernel(const __grid_consta
   }
 }
 
+// ---------------------------------------------------------------------------
+// Grouped transform with staged tiles (n_in, n_out <= 120).  A persistent block
+// walks tiles (group, channel, 128 voxels); the group's operator T^T
+// [n_in][12 x OG] stays in shared memory while the group lasts, each tile's
+// input rows [n_in][128 voxels] arrive by cp.async (all rows in flight at once).
+// Thread (q, og) computes 4 voxels (4q..4q+3) x 12 outputs: per input row one
+// vector load of x, three of T^T, 48 FMAs.  A warp holds 32 consecutive voxel
+// quads of one output group, so every output row is one 512-byte (FP32) run.
+// ---------------------------------------------------------------------------
+constexpr int kTfVox = 128, kTfOpt = 12, kTfMaxOut = 120;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ float4 ld_x4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ld_x4(const __nv_bfloat16* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                     __uint_as_float(u.y & 0xffff0000u));
+}
+__device__ __forceinline__ void st_y4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st_y4(__nv_bfloat16* p, float a, float b, float c, float d) {
+  __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  uint2 u;
+  u.x = *reinterpret_cast<uint32_t*>(&lo);
+  u.y = *reinterpret_cast<uint32_t*>(&hi);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(32 * (kTfMaxOut / kTfOpt)) transform_staged_kernel(const __grid_constant__ TransformArgs a,
+                                                                                     int n_groups, int og_count,
+                                                                                     int max_in) {
+  extern __shared__ float4 tf_smem4[];
+  float* Tt = reinterpret_cast<float*>(tf_smem4);                 // [max_in][12 * og_count]
+  Tin* Xs = reinterpret_cast<Tin*>(Tt + max_in * kTfOpt * og_count);  // [max_in][128]
+  const int ldt = kTfOpt * og_count;
+  const int tid = threadIdx.x, q = tid % 32, og = tid / 32;
+  const int64_t vt_count = (a.n_vox + kTfVox - 1) / kTfVox;
+  const int64_t per_group = vt_count * a.channels;
+  const int64_t total = per_group * n_groups;
+  constexpr int kChunkElems = 16 / sizeof(Tin);  // elements per 16-byte copy
+  constexpr int kChunksPerRow = kTfVox / kChunkElems;
+  int cur_g = -1;
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    const int g = (int)(t / per_group);
+    const int64_t r = t % per_group;
+    const int c = (int)(r / vt_count);
+    const int64_t v0 = (r % vt_count) * kTfVox;
+    const TransformGroup& G = a.g[g];
+    __syncthreads();  // the previous tile's reads of Xs (and Tt) are done
+    // input rows of this tile: all copies in flight at once, zero past n_vox
+    const Tin* X = reinterpret_cast<const Tin*>(a.X) + (G.x_row0 + (int64_t)c * G.x_cstride) * a.ldx + v0;
+    const uint32_t xs_base = (uint32_t)__cvta_generic_to_shared(Xs);
+    for (int i = tid; i < G.n_in * kChunksPerRow; i += blockDim.x) {
+      const int j = i / kChunksPerRow, ch = i % kChunksPerRow;
+      const int64_t vv = v0 + (int64_t)ch * kChunkElems;
+      const int64_t left = a.n_vox - vv;
+      const int bytes = left >= kChunkElems ? 16 : (left > 0 ? (int)left * (int)sizeof(Tin) : 0);
+      const Tin* src = X + (int64_t)j * a.ldx + (int64_t)ch * kChunkElems;
+      cp_async16(xs_base + (uint32_t)((j * kTfVox + ch * kChunkElems) * sizeof(Tin)), bytes > 0 ? src : X, bytes);
+    }
+    if (g != cur_g) {  // the group's operator, transposed: Tt[j][o] = T[o][j], zero past n_out
+      for (int i = tid; i < G.n_in * ldt; i += blockDim.x) {
+        const int j = i / ldt, o = i % ldt;
+        Tt[i] = o < G.n_out ? G.T[(int64_t)o * G.n_in + j] : 0.f;
+      }
+      cur_g = g;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (og * kTfOpt < G.n_out) {
+      float acc[kTfOpt][4];
+#pragma unroll
+      for (int o = 0; o < kTfOpt; ++o)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[o][v] = 0.f;
+      const float* tcol = Tt + og * kTfOpt;
+      const Tin* xq = Xs + 4 * q;
+#pragma unroll 2
+      for (int j = 0; j < G.n_in; ++j) {
+        const float4 x = ld_x4(xq + j * kTfVox);
+        const float4 t0 = *reinterpret_cast<const float4*>(tcol + j * ldt);
+        const float4 t1 = *reinterpret_cast<const float4*>(tcol + j * ldt + 4);
+        const float4 t2 = *reinterpret_cast<const float4*>(tcol + j * ldt + 8);
+        const float tv[kTfOpt] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, t2.x, t2.y, t2.z, t2.w};
+#pragma unroll
+        for (int o = 0; o < kTfOpt; ++o) {
+          acc[o][0] = fmaf(tv[o], x.x, acc[o][0]);
+          acc[o][1] = fmaf(tv[o], x.y, acc[o][1]);
+          acc[o][2] = fmaf(tv[o], x.z, acc[o][2]);
+          acc[o][3] = fmaf(tv[o], x.w, acc[o][3]);
+        }
+      }
+      Tout* Y = reinterpret_cast<Tout*>(a.Y) + (G.y_row0 + (int64_t)c * G.y_cstride + og * kTfOpt) * a.ldy + v0 + 4 * q;
+      const int64_t nv = a.n_vox - (v0 + 4 * q);
+#pragma unroll
+      for (int o = 0; o < kTfOpt; ++o) {
+        if (og * kTfOpt + o < G.n_out) {
+          Tout* y = Y + (int64_t)o * a.ldy;
+          if (nv >= 4) {
+            st_y4(y, acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              if (v < nv) stf(y + v, acc[o][v]);
+          }
+        }
+      }
+    }
+  }
+}
+
 template <typename Tin, typename Tout>
 static cudaError_t transform_dispatch(const TransformArgs& a, int n_groups, int max_out, cudaStream_t st) {
+  int max_in = 0;
+  for (int g = 0; g < n_groups; ++g) max_in = std::max(max_in, a.g[g].n_in);
+  if (max_out <= kTfMaxOut && max_in <= 128) {
+    const int og_count = (max_out + kTfOpt - 1) / kTfOpt;
+    const int threads = 32 * og_count;
+    const size_t smem = (size_t)max_in * kTfOpt * og_count * sizeof(float) + (size_t)max_in * kTfVox * sizeof(Tin);
+    auto kern = transform_staged_kernel<Tin, Tout>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (a.n_vox + kTfVox - 1) / kTfVox * a.channels * n_groups;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(1, per_sm) * sms));
+    { kern<<<grid, threads, smem, st>>>(a, n_groups, og_count, max_in); count_launch(); }
+    return cudaGetLastError();
+  }
   constexpr int VPT = 2;
   const unsigned gx = (unsigned)((a.n_vox + 128 * VPT - 1) / (128 * VPT));
   if (max_out <= 16) {
@@ -113,20 +249,25 @@ cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_
 // ---------------------------------------------------------------------------
 // Collapsed LSC operator.  For every shell pair (s, s') in the window
 //   W[(s,co,a)][(s',ci,b)] = sum_k w[co,s,ci,s',k] M_s[k][a][b]
-// One block: 8 channel pairs (co, ci) of one shell pair and all n_out x n_in
-// entries (a, b).  M_s[k] rows stream from L2 (k outer); each thread keeps
-// 8 pairs x ceil(n_out*n_in / 256) accumulators.  The finished blocks go to
-// shared memory and are written to W (runs along b) and Wt (runs along a).
-// Shell pairs outside the window write zeros.
+// One block: 8 channel pairs (co, ci) of one shell pair and up to 2048 (a, b)
+// entries.  Chunks of 8 kernel points of M_s (8 x 2048 floats) and of w are
+// staged in shared memory with coalesced loads; each thread then accumulates
+// 8 pairs x 8 consecutive (a, b) entries (64 FMAs per 4 vector shared loads).
+// The finished block goes back through shared memory and is written to W
+// (runs along b) and Wt (runs along a), one warp per run.  Shell pairs outside
+// the window write zeros.
 // ---------------------------------------------------------------------------
-constexpr int kBwPairs = 8, kBwMaxPer = 8, kBwChunk = 256 * kBwMaxPer;  // (a,b) entries per block
+constexpr int kBwPairs = 8, kBwChunk = 2048, kBwKC = 8;  // pairs, (a,b) entries, kernel points per stage
+static_assert(kBwKC >= kBwPairs, "the M stage buffer holds the finished block");
 
 template <typename TW>
 __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
                                                       const float* __restrict__ M, TW* __restrict__ W,
                                                       TW* __restrict__ Wt) {
-  extern __shared__ float blk[];  // [kBwPairs][kBwChunk]
-  __shared__ float wk[kBwPairs][64];
+  extern __shared__ float4 blk4[];  // [kBwKC][kBwChunk] M stage; later [kBwPairs][kBwChunk] results
+  float* blk = reinterpret_cast<float*>(blk4);
+  __shared__ __align__(16) float wk[kBwKC][kBwPairs];
+  const int tid = threadIdx.x;
   const int pair = blockIdx.y;  // s * s_in + s'
   const int s = pair / d.s_in, sp = pair % d.s_in;
   const bool in_win = sp >= d.win_lo[s] && sp < d.win_hi[s];
@@ -134,77 +275,96 @@ __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ Ls
   const int p0 = blockIdx.x * kBwPairs;
   const int np = min(kBwPairs, npairs - p0);
   const int ab0 = blockIdx.z * kBwChunk, nabc = min(kBwChunk, nab - ab0);  // this block's (a,b) range
-  const float* Ms = M + (int64_t)s * d.K * nab;
-  float acc[kBwPairs][kBwMaxPer];
+  float acc[kBwPairs][8];
 #pragma unroll
   for (int p = 0; p < kBwPairs; ++p)
 #pragma unroll
-    for (int e = 0; e < kBwMaxPer; ++e) acc[p][e] = 0.f;
+    for (int e = 0; e < 8; ++e) acc[p][e] = 0.f;
   if (in_win) {
-    for (int k0 = 0; k0 < d.K; k0 += 64) {
-      const int nk = min(64, d.K - k0);
+    const float* Ms = M + (int64_t)s * d.K * nab + ab0 + tid;
+    for (int k0 = 0; k0 < d.K; k0 += kBwKC) {
+      const int nk = min(kBwKC, d.K - k0);
       __syncthreads();
-      for (int idx = threadIdx.x; idx < kBwPairs * 64; idx += 256) {
-        const int pp = idx / 64, kk = idx % 64, pr = p0 + pp;
+      // stage M_s[k0 .. k0+7][ab0 .. ab0+2047]: element tid + 256 e of each row (zero past the range)
+      for (int kk = 0; kk < kBwKC; ++kk) {
+        const float* row = Ms + (int64_t)(k0 + kk) * nab;
+        float* dst = blk + kk * kBwChunk + tid;
+        if (kk < nk && nabc == kBwChunk) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) dst[256 * e] = __ldg(row + 256 * e);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) dst[256 * e] = (kk < nk && tid + 256 * e < nabc) ? __ldg(row + 256 * e) : 0.f;
+        }
+      }
+      if (tid < kBwKC * kBwPairs) {
+        const int kk = tid / kBwPairs, pp = tid % kBwPairs, pr = p0 + pp;
         float v = 0.f;
         if (pp < np && kk < nk) {
           const int co = pr / d.c_in, ci = pr % d.c_in;
           v = w[((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K + k0 + kk];
         }
-        wk[pp][kk] = v;
+        wk[kk][pp] = v;
       }
       __syncthreads();
-#pragma unroll 7
-      for (int kk = 0; kk < nk; ++kk) {  // unrolled: several k rows of loads in flight
-        const float* mk = Ms + (int64_t)(k0 + kk) * nab;
-        float mv[kBwMaxPer];
 #pragma unroll
-        for (int e = 0; e < kBwMaxPer; ++e) {
-          const int t = threadIdx.x + 256 * e;
-          mv[e] = t < nabc ? __ldg(mk + ab0 + t) : 0.f;
-        }
+      for (int kk = 0; kk < kBwKC; ++kk) {
+        const float4 m0 = blk4[kk * (kBwChunk / 4) + 2 * tid], m1 = blk4[kk * (kBwChunk / 4) + 2 * tid + 1];
+        const float4 w0 = *reinterpret_cast<const float4*>(&wk[kk][0]);
+        const float4 w1 = *reinterpret_cast<const float4*>(&wk[kk][4]);
+        const float mv[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-        for (int p = 0; p < kBwPairs; ++p) {
-          const float wv = wk[p][kk];
+        for (int p = 0; p < kBwPairs; ++p)
 #pragma unroll
-          for (int e = 0; e < kBwMaxPer; ++e) acc[p][e] = fmaf(wv, mv[e], acc[p][e]);
-        }
+          for (int e = 0; e < 8; ++e) acc[p][e] = fmaf(wv[p], mv[e], acc[p][e]);
       }
     }
   }
   __syncthreads();
+  // results [p][t], t = 8 tid + e
 #pragma unroll
-  for (int p = 0; p < kBwPairs; ++p)
-#pragma unroll
-    for (int e = 0; e < kBwMaxPer; ++e) {
-      const int t = threadIdx.x + 256 * e;
-      if (t < nabc) blk[p * kBwChunk + t] = acc[p][e];
-    }
-  __syncthreads();
-  // W: row (s, co, a), columns s'*in_blk + ci*n_in + b: consecutive threads along b
-  for (int idx = threadIdx.x; idx < np * nabc; idx += 256) {
-    const int p = idx / nabc, t = idx % nabc, pr = p0 + p, ab = ab0 + t;
-    const int co = pr / d.c_in, ci = pr % d.c_in, aa = ab / d.n_in, bb = ab % d.n_in;
-    const int64_t r = ((int64_t)s * d.c_out + co) * d.n_out + aa;
-    stf(W + r * d.ldW + (int64_t)sp * d.in_blk + (int64_t)ci * d.n_in + bb, blk[p * kBwChunk + t]);
+  for (int p = 0; p < kBwPairs; ++p) {
+    blk4[p * (kBwChunk / 4) + 2 * tid] = make_float4(acc[p][0], acc[p][1], acc[p][2], acc[p][3]);
+    blk4[p * (kBwChunk / 4) + 2 * tid + 1] = make_float4(acc[p][4], acc[p][5], acc[p][6], acc[p][7]);
   }
-  // Wt: row (s', ci, b), columns s*out_blk + co*n_out + a: consecutive threads along a when the
-  // block holds all (a,b) entries, in (a,b) order otherwise
-  const bool whole = nabc == nab;
-  for (int idx = threadIdx.x; idx < np * nabc; idx += 256) {
-    const int p = idx / nabc, t = idx % nabc, pr = p0 + p;
-    int aa, bb;
-    if (whole) {
-      bb = t / d.n_out;
-      aa = t % d.n_out;
-    } else {
-      aa = (ab0 + t) / d.n_in;
-      bb = (ab0 + t) % d.n_in;
+  __syncthreads();
+  // Stores: one warp per output row segment, lanes along the contiguous index; the
+  // segment loops carry no division (pairs outer, rows strided by warp inner).
+  const int warp = tid / 32, lane = tid % 32;
+  const int a_lo = ab0 / d.n_in, a_hi = (ab0 + nabc - 1) / d.n_in;  // a range touched by this chunk
+  const int na = a_hi - a_lo + 1;
+  const int b_lo = na > 1 ? 0 : ab0 % d.n_in, b_hi = na > 1 ? d.n_in - 1 : (ab0 + nabc - 1) % d.n_in;
+  const int nb = b_hi - b_lo + 1;
+  int co = p0 / d.c_in, ci = p0 % d.c_in;
+  for (int p = 0; p < np; ++p) {
+    const float* src = blk + p * kBwChunk;  // src[a * n_in + b - ab0] for this pair
+    // W: row (s, co, a), columns s'*in_blk + ci*n_in + b
+    TW* wrow = W + (((int64_t)s * d.c_out + co) * d.n_out + a_lo) * d.ldW + (int64_t)sp * d.in_blk + (int64_t)ci * d.n_in;
+    for (int ai = warp; ai < na; ai += 8) {
+      const int aa = a_lo + ai;
+      TW* dst = wrow + (int64_t)ai * d.ldW;
+      for (int bb = lane; bb < d.n_in; bb += 32) {
+        const int t = aa * d.n_in + bb;
+        if (t >= ab0 && t < ab0 + nabc) stf(dst + bb, src[t - ab0]);
+      }
     }
-    const int co = pr / d.c_in, ci = pr % d.c_in;
-    const int64_t r = ((int64_t)sp * d.c_in + ci) * d.n_in + bb;
-    stf(Wt + r * d.ldWt + (int64_t)s * d.out_blk + (int64_t)co * d.n_out + aa,
-        blk[p * kBwChunk + (aa * d.n_in + bb) - ab0]);
+    // Wt: row (s', ci, b), columns s*out_blk + co*n_out + a (when the caller wants it)
+    TW* wtrow = Wt ? Wt + (((int64_t)sp * d.c_in + ci) * d.n_in + b_lo) * d.ldWt + (int64_t)s * d.out_blk +
+                         (int64_t)co * d.n_out
+                   : nullptr;
+    for (int bi = warp; wtrow && bi < nb; bi += 8) {
+      const int bb = b_lo + bi;
+      TW* dst = wtrow + (int64_t)bi * d.ldWt;
+      for (int aa = a_lo + lane; aa <= a_hi; aa += 32) {
+        const int t = aa * d.n_in + bb;
+        if (t >= ab0 && t < ab0 + nabc) stf(dst + aa, src[t - ab0]);
+      }
+    }
+    if (++ci == d.c_in) {
+      ci = 0;
+      ++co;
+    }
   }
 }
 
@@ -228,13 +388,13 @@ cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, con
     e = cudaMemsetAsync(W, 0, (size_t)d.rows_out * d.ldW * es, st);
     if (e != cudaSuccess) return e;
   }
-  if (d.out_blk != (int64_t)d.c_out * d.n_out) {
+  if (Wt && d.out_blk != (int64_t)d.c_out * d.n_out) {
     e = cudaMemsetAsync(Wt, 0, (size_t)d.rows_in * d.ldWt * es, st);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((unsigned)((npairs + kBwPairs - 1) / kBwPairs), (unsigned)(d.s_out * d.s_in),
             (unsigned)((nab + kBwChunk - 1) / kBwChunk));
-  const size_t smem = sizeof(float) * kBwPairs * kBwChunk;
+  const size_t smem = sizeof(float) * kBwKC * kBwChunk;  // = kBwPairs * kBwChunk for the results
   if (w_t == 0) {
     e = cudaFuncSetAttribute(build_w_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

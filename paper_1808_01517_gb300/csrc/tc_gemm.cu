@@ -45,6 +45,7 @@ enum : int {
 constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // + TMA warp + MMA warp
 constexpr int kBK = 64;            // K rows (or voxels) per stage
+constexpr int kWgradBN = 240;      // weight-gradient column tile (divides 720-multiples: 1440, 2160)
 constexpr int kBoxBytes = 64 * 128;  // one 64 x 64 BF16 box, 128-byte rows
 
 }  // namespace
@@ -60,11 +61,13 @@ struct VoxGroup {
   int b_n0, N;      // first operator column (multiple of 8), valid output columns
   int64_t y_row0;   // first output row
   int n_tiles;
+  int bn_last;      // width of the group's last operator tile (<= BN, whole 64-column atoms per CTA)
 };
 
 struct VoxParams {
   VoxGroup g[kMaxGroups];
   int n_groups, m_tiles, tiles_per_m;
+  int b_kmajor;  // operator stored [N rows][K contiguous] (K-major) instead of [K rows][N contiguous]
   int64_t total_tiles, n_vox, ldy;
   __nv_bfloat16* Y;
   const float* bias;
@@ -173,6 +176,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mt = mt * CL + rank;
       const VoxGroup& G = p.g[g];
       const int nkb = (G.K + kBK - 1) / kBK;
+      const int tile_bn = nt == G.n_tiles - 1 ? G.bn_last : BN;
+      // MN-major operator: 64-column boxes of this CTA's tile_bn / CL columns; K-major: one
+      // box of BN / CL rows (a narrow tile loads rows it does not use)
+      const int nbox = tile_bn / CL / 64;
+      const uint32_t bytes = (uint32_t)(A_BYTES + (p.b_kmajor ? B_BYTES : nbox * kBoxBytes));
       bool ok = true;
       for (int kb = 0; kb < nkb; ++kb) {
         if (!wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, p.err, kErrEmpty)) {
@@ -181,21 +189,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const uint32_t a_dst = sbase + stage * STAGE_BYTES, b_dst = a_dst + A_BYTES;
         const int krow = G.a_k0 + kb * kBK;
-        const int ncol = G.b_n0 + nt * BN + rank * (BN / CL);
+        const int ncol = G.b_n0 + nt * BN + rank * (tile_bn / CL);
         if (CL > 1) {
           // both CTAs' bytes complete on the even CTA's barrier, which that CTA arms
           const uint32_t fb = mapa_shared(full_bar(stage), 0);
-          if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), CL * STAGE_BYTES);
+          if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), CL * bytes);
           tma_load_2d_pair(&mapA, fb, a_dst, mt * 128, krow);
           tma_load_2d_pair(&mapA, fb, a_dst + kBoxBytes, mt * 128 + 64, krow);
-#pragma unroll
-          for (int j = 0; j < BN / CL / 64; ++j) tma_load_2d_pair(&mapB, fb, b_dst + j * kBoxBytes, ncol + j * 64, krow);
+          if (p.b_kmajor)
+            tma_load_2d_pair(&mapB, fb, b_dst, krow, ncol);
+          else
+            for (int j = 0; j < nbox; ++j) tma_load_2d_pair(&mapB, fb, b_dst + j * kBoxBytes, ncol + j * 64, krow);
         } else {
-          mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
+          mbar_arrive_expect_tx(full_bar(stage), bytes);
           tma_load_2d(&mapA, full_bar(stage), a_dst, mt * 128, krow);
           tma_load_2d(&mapA, full_bar(stage), a_dst + kBoxBytes, mt * 128 + 64, krow);
-#pragma unroll
-          for (int j = 0; j < BN / 64; ++j) tma_load_2d(&mapB, full_bar(stage), b_dst + j * kBoxBytes, ncol + j * 64, krow);
+          if (p.b_kmajor)
+            tma_load_2d(&mapB, full_bar(stage), b_dst, krow, ncol);
+          else
+            for (int j = 0; j < nbox; ++j) tma_load_2d(&mapB, full_bar(stage), b_dst + j * kBoxBytes, ncol + j * 64, krow);
         }
         pend[stage] = (int)phase;
         if (++stage == STAGES) {
@@ -220,6 +232,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int g, mt, nt;
       vox_decode(p, t, g, mt, nt);
       const int nkb = (p.g[g].K + kBK - 1) / kBK;
+      const bool bk = p.b_kmajor != 0;
+      const uint32_t idesc = idesc_bf16(128 * CL, nt == p.g[g].n_tiles - 1 ? p.g[g].bn_last : BN, true, !bk);
       if (!wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.err, kErrTmemEmpty)) break;
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
@@ -234,13 +248,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int k = 0; k < kBK / 16; ++k) {
           // MN-major, 128-byte swizzle: 64-element MN atoms kBoxBytes apart (LBO),
-          // 8-row K groups 1024 B apart (SBO); 16 K rows = 2048 B per MMA.
+          // 8-row K groups 1024 B apart (SBO); 16 K rows = 2048 B per MMA.  K-major
+          // operator: rows 128 B apart, 8-row groups 1024 B apart, 16 K = 32 B per MMA.
           const uint64_t ad = umma_desc(a_src + k * 2048, kBoxBytes, 1024, kSwizzle128B);
-          const uint64_t bd = umma_desc(b_src + k * 2048, kBoxBytes, 1024, kSwizzle128B);
+          const uint64_t bd = bk ? umma_desc(b_src + k * 32, 16, 1024, kSwizzle128B)
+                                 : umma_desc(b_src + k * 2048, kBoxBytes, 1024, kSwizzle128B);
           if (CL > 1)
-            mma_bf16_pair(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+            mma_bf16_pair(d_tmem, ad, bd, idesc, (kb | k) != 0);
           else
-            mma_bf16(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+            mma_bf16(d_tmem, ad, bd, idesc, (kb | k) != 0);
         }
         if (CL > 1)
           mma_commit_pair_mc(empty_bar(stage), 0x3);  // both CTAs' producers refill this stage
@@ -441,10 +457,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                  const __grid_constant__ WgParams p) {
   using namespace ptx;
   static_assert(CL == 1 || CL == 2, "one CTA or a CTA pair");
+  static_assert(BN <= 256 && BN % 16 == 0 && (BN / CL) % 8 == 0, "N tile: whole 8-row groups per CTA");
   constexpr int A_BYTES = 128 * 128;      // 128 rows x 64 voxels
   constexpr int B_BYTES = BN / CL * 128;  // this CTA's BN/CL rows x 64 voxels
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  constexpr uint32_t TMEM_COLS = (2 * BN <= 256) ? 256 : 512;
+  constexpr uint32_t TMEM_COLS = 512;      // two accumulators, 256 columns apart
   constexpr uint32_t IDESC = idesc_bf16(128 * CL, BN, false, false);
 
   extern __shared__ uint8_t smem_raw[];
@@ -549,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nkb = (int)((ve - vs + 63) / 64);
       if (!wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.err, kErrTmemEmpty)) break;
       tc_fence_after();
-      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
       bool ok = true;
       for (int kb = 0; kb < nkb; ++kb) {
         if (!wait_bounded(full_bar(stage), phase, abort_flag, p.err, kErrFull)) {
@@ -607,7 +624,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int m = mt * 128 + q * 32 + lane;
       float* prow = p.P + (int64_t)split * p.split_stride + (G.m_row0 + m) * p.ldp + G.n_col0;
-      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 256);
       for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
         uint32_t rv[4][16];
 #pragma unroll
@@ -654,6 +671,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// host side
 // Row sums of dY per voxel split (the bias-gradient column of the weight gradient).
 __global__ void __launch_bounds__(256) rowsum_kernel(const __nv_bfloat16* __restrict__ dY, int64_t lddy, int64_t rows,
                                                      int64_t n_vox, int64_t vps, int splits, float* __restrict__ P,
@@ -683,8 +702,6 @@ __global__ void __launch_bounds__(256) rowsum_kernel(const __nv_bfloat16* __rest
   if (lane == 0) P[(int64_t)split * split_stride + row * ldp + col] = acc;
 }
 
-// ---------------------------------------------------------------------------
-// host side
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -865,15 +882,30 @@ int pick_bn(const int* Ns, int n) {
 
 // The staged epilogue is used when every group has the same N (one 3-D output
 // map covers them) and the tile is at most 192 wide (ring + tile fit in smem).
+// The operator (B) as stored: MN-major [K rows][N columns] or K-major [N rows][K columns].
+struct OperatorView {
+  const void* ptr;
+  uint64_t rows, cols, ld;  // elements
+  bool kmajor;
+};
+
 // cl = 2 runs CTA pairs with 2-SM MMAs; a pair splits its bn operator columns
 // into two halves of whole 64-column atoms, so bn = 192 becomes 256 there.
-cudaError_t run_vox(const CUtensorMap& ma, const CUtensorMap& mb, VoxParams& p, int bn, bool staged_ok, int cl,
+cudaError_t run_vox(const CUtensorMap& ma, const OperatorView& B, VoxParams& p, int bn, bool staged_ok, int cl,
                     void* Y, int64_t ldy, cudaStream_t st) {
   if (cl > 1 && bn == 192) bn = 256;
+  // MN-major: 64-column x 64-K-row boxes; K-major: 64-K x (bn / cl)-row boxes
+  CUtensorMap mb;
+  if (!make_map(&mb, B.ptr, B.cols, B.rows, B.ld, 64, B.kmajor ? (uint32_t)(bn / cl) : (uint32_t)kBK))
+    return cudaErrorInvalidValue;
+  p.b_kmajor = B.kmajor ? 1 : 0;
   p.tiles_per_m = 0;
   bool same_n = true;
+  const int atom = 64 * (cl > 1 && (bn / 2) % 64 == 0 ? 2 : 1);  // last-tile granularity
   for (int i = 0; i < p.n_groups; ++i) {
     p.g[i].n_tiles = (p.g[i].N + bn - 1) / bn;
+    const int rem = p.g[i].N - (p.g[i].n_tiles - 1) * bn;
+    p.g[i].bn_last = std::min(bn, (rem + atom - 1) / atom * atom);
     p.tiles_per_m += p.g[i].n_tiles;
     same_n = same_n && p.g[i].N == p.g[0].N && p.g[i].y_row0 == (int64_t)i * p.g[0].N;
   }
@@ -919,12 +951,21 @@ bool tc_gemm_supported(const LscDims& d, int64_t n_vox, int64_t ld_in, int64_t l
   return true;
 }
 
-cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* Wt, const float* bias, void* Y, int64_t n_vox,
-                           int64_t ldx, int64_t ldy, int* err, cudaStream_t st) {
+bool tc_forward_reads_w(const LscDims& d) { return d.in_blk == (int64_t)d.c_in * d.n_in; }
+
+cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const void* Wt, const float* bias, void* Y,
+                           int64_t n_vox, int64_t ldx, int64_t ldy, int* err, cudaStream_t st) {
   TraceScope trace("lsc_fwd_gemm", st);
-  CUtensorMap ma, mb;
+  CUtensorMap ma;
   if (!make_map(&ma, X, (uint64_t)n_vox, (uint64_t)d.rows_in, (uint64_t)ldx, 64, kBK)) return cudaErrorInvalidValue;
-  if (!make_map(&mb, Wt, (uint64_t)d.ldWt, (uint64_t)d.rows_in, (uint64_t)d.ldWt, 64, kBK)) return cudaErrorInvalidValue;
+  // Without per-shell column padding the input-feature index of W's columns equals the
+  // row index of X, so W serves as the K-major operator and Wt is not needed.
+  const bool kmajor = tc_forward_reads_w(d);
+  OperatorView B;
+  if (kmajor)
+    B = OperatorView{W, (uint64_t)d.rows_out, (uint64_t)d.ldW, (uint64_t)d.ldW, true};
+  else
+    B = OperatorView{Wt, (uint64_t)d.rows_in, (uint64_t)d.ldWt, (uint64_t)d.ldWt, false};
   VoxParams p;
   memset(&p, 0, sizeof p);
   const int per_in = d.c_in * d.n_in, per_out = d.c_out * d.n_out;
@@ -933,7 +974,7 @@ cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* Wt, cons
     VoxGroup& G = p.g[s];
     G.a_k0 = d.win_lo[s] * per_in;
     G.K = (d.win_hi[s] - d.win_lo[s]) * per_in;
-    G.b_n0 = (int)(s * d.out_blk);
+    G.b_n0 = (int)(kmajor ? (int64_t)s * per_out : s * d.out_blk);  // first operator row (K-major) or column
     G.N = per_out;
     G.y_row0 = (int64_t)s * per_out;
     Ns[s] = G.N;
@@ -949,15 +990,15 @@ cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* Wt, cons
   int bn = pick_bn(Ns, d.s_out);
   if (bn == 256) bn = ((Ns[0] % 192) == 0) ? 192 : 128;
   bn = env_int("DELIMIT_FWD_BN", bn);
-  return run_vox(ma, mb, p, bn, env_int("DELIMIT_FWD_STAGED", 1) != 0, gemm_cluster(2), Y, ldy, st);
+  return run_vox(ma, B, p, bn, env_int("DELIMIT_FWD_STAGED", 1) != 0, gemm_cluster(2), Y, ldy, st);
 }
 
 cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* dX, int64_t n_vox, int64_t lddy,
                          int64_t lddx, int* err, cudaStream_t st) {
   TraceScope trace("lsc_dgrad_gemm", st);
-  CUtensorMap ma, mb;
+  CUtensorMap ma;
   if (!make_map(&ma, dY, (uint64_t)n_vox, (uint64_t)d.rows_out, (uint64_t)lddy, 64, kBK)) return cudaErrorInvalidValue;
-  if (!make_map(&mb, W, (uint64_t)d.ldW, (uint64_t)d.rows_out, (uint64_t)d.ldW, 64, kBK)) return cudaErrorInvalidValue;
+  const OperatorView B{W, (uint64_t)d.rows_out, (uint64_t)d.ldW, (uint64_t)d.ldW, false};
   VoxParams p;
   memset(&p, 0, sizeof p);
   const int per_in = d.c_in * d.n_in, per_out = d.c_out * d.n_out;
@@ -978,7 +1019,7 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* 
   p.Y = reinterpret_cast<__nv_bfloat16*>(dX);
   p.bias = nullptr;
   p.err = err;
-  return run_vox(ma, mb, p, env_int("DELIMIT_DGRAD_BN", pick_bn(Ns, d.s_in)),
+  return run_vox(ma, B, p, env_int("DELIMIT_DGRAD_BN", pick_bn(Ns, d.s_in)),
                  env_int("DELIMIT_DGRAD_STAGED", 0) != 0, gemm_cluster(2), dX, lddx, st);
 }
 
@@ -995,7 +1036,7 @@ cudaError_t launch_wgrad(const CUtensorMap& ma, const CUtensorMap& mb, const WgP
 
 cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float* P, int64_t ldp, int64_t split_stride,
                          int splits, int64_t vps, int64_t n_vox, int64_t lddy, int64_t ldx, int* err, cudaStream_t st) {
-  constexpr int BN = 256;
+  constexpr int BN = kWgradBN;
   const int cl = gemm_cluster(2);
   CUtensorMap ma, mb;
   if (!make_map(&ma, dY, (uint64_t)n_vox, (uint64_t)d.rows_out, (uint64_t)lddy, 64, 128)) return cudaErrorInvalidValue;
@@ -1028,10 +1069,12 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
   cudaError_t e = cudaSuccess;
   if (p.total_tiles > 0) {
     TraceScope trace("lsc_wgrad_gemm", st);
-    // stages: 4 x 48 KiB for one CTA, 6 x 32 KiB per CTA of a pair
-    e = cl > 1 ? launch_wgrad<BN, 6, 2>(ma, mb, p, st) : launch_wgrad<BN, 4, 1>(ma, mb, p, st);
+    // stages: 4 x 46 KiB for one CTA, 7 x 31 KiB per CTA of a pair
+    e = cl > 1 ? launch_wgrad<BN, 7, 2>(ma, mb, p, st) : launch_wgrad<BN, 4, 1>(ma, mb, p, st);
     if (e != cudaSuccess) return e;
   }
+  // bias-gradient column: row sums of dY per split (a separate HBM-bound pass; an extra
+  // N = 16 MMA per step inside the GEMM measured slower, each MMA re-reads the A tile)
   const int64_t warps = d.rows_out * splits;
   TraceScope trace_rs("lsc_rowsum", st);
   { rowsum_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(

@@ -31,7 +31,10 @@ cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X,
 // LSC GEMMs (BF16 activations, FP32 accumulation in TMEM)
 bool tc_gemm_supported(const LscDims& d, int64_t n_vox, int64_t ld_in, int64_t ld_out);
 // Y[(s,co,a), v] = sum_{k in win(s)} Wt[k][s*out_blk + (co,a)] X[k, v] + bias[(s,co,a)]
-cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* Wt, const float* bias, void* Y,
+// (= sum_k W[(s,co,a)][k] X[k, v]).  When tc_forward_reads_w(d) (no per-shell column
+// padding in W) the kernel reads W as a K-major operator and Wt may be absent.
+bool tc_forward_reads_w(const LscDims& d);
+cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const void* Wt, const float* bias, void* Y,
                            int64_t n_vox, int64_t ldx, int64_t ldy, int* err_word, cudaStream_t st);
 // dX[(s',ci,b), v] = sum_{k in rwin(s')} W[k][s'*in_blk + (ci,b)] dY[k, v]
 cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* dX, int64_t n_vox, int64_t lddy,

@@ -33,7 +33,7 @@ def _run(kind, lb, x_rows, C, in_dt, out_dt):
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 @pytest.mark.parametrize("tc", [True, False])
-@pytest.mark.parametrize("case", ["c1", "multishell_ragged", "channels"])
+@pytest.mark.parametrize("case", ["c1", "multishell_ragged", "channels", "wide_shell"])
 def test_transforms_vs_oracle(prec, tc, case):
     L.set_tensor_cores(tc)
     try:
@@ -43,9 +43,12 @@ def test_transforms_vs_oracle(prec, tc, case):
         elif case == "multishell_ragged":  # 3 x 90 directions, ragged voxel count
             dirs, bvals = synth.multishell_table([90, 90, 90], [1000, 2000, 3000], seed=1808)
             order, lam, V, C = 8, 0.006, 3001, 1
-        else:  # channels and unequal shells
+        elif case == "channels":  # channels and unequal shells
             dirs, bvals = synth.multishell_table([30, 45], [1000, 2000], seed=7)
             order, lam, V, C = 4, 0.06, 515, 16
+        else:  # 150 directions, order 10: beyond the staged CUDA-core kernel's 128 inputs / 120 outputs
+            dirs, bvals = synth.multishell_table([150], [2000], seed=9)
+            order, lam, V, C = 10, 0.006, 300, 2
         ob = osh.SHBasisOracle(dirs, bvals, order, lam)
         lb = L.SHBasis(dirs, bvals, order, lam)
         m = ob.m
