@@ -30,6 +30,28 @@ sys.path.insert(0, HERE)
 METRIC = "voxels/s, Signal2SH->LSC->SH2Signal fwd+bwd, BF16 vs FP32 at stated error vs FP64 oracle"
 UNIT = "voxels/s"
 
+# DRAM traffic (read + write) of one launch from an ncu capture of the 16,384-voxel
+# case (profiles/lsc_kernels_16384vox_ncu.md), scaled by the voxel count; valid only
+# while the kernel's sources hash to the value recorded with the capture.
+NCU_TRAFFIC = {
+    "lsc_fwd_gemm": {"bytes": 361.6e6, "n_vox": 16384, "sources": ("csrc/tc_gemm.cu", "csrc/tc_ptx.cuh"),
+                     "sha256_16": "2dd6c299a8c8e4f6"},
+}
+
+
+def ncu_traffic(kernel: str, n_vox: int):
+    import hashlib
+    rec = NCU_TRAFFIC.get(kernel)
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for rel in rec["sources"]:
+        with open(os.path.join(HERE, "paper_1808_01517_gb300", rel), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest()[:16] != rec["sha256_16"]:
+        return None  # the kernel changed since the counters were taken
+    return rec["bytes"] * n_vox / rec["n_vox"]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -326,7 +348,7 @@ def main():
     else:
         roofline = {"bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": hbm, "unit": "GB/s",
                     "frac": kernels[dom]["gbs"] / hbm, "peak_source": f"{peak_src} hbm_gbs"}
-    roofline.update({"traffic": None, "kernel": dom, "kernel_avg_ms": kernels[dom]["avg_ms"],
+    roofline.update({"traffic": ncu_traffic(dom, V), "kernel": dom, "kernel_avg_ms": kernels[dom]["avg_ms"],
                      "step_tflops": sum(fl.values()) / (ms * 1e-3) / 1e12})
     roofline["step_frac_of_tensor_peak"] = roofline["step_tflops"] / tf_sust
 

@@ -195,7 +195,10 @@ size_t delimit_lsc_workspace_size(const delimit_lsc_geometry* geom, int64_t n_vo
  *   b       device float32 [c_out, S_out], or NULL for no bias
  *   sh_out  device, SH rows (S_out x c_out x N_out) x n_vox, ld_out
  *   act_t   dtype of sh_in and sh_out
- *   workspace >= delimit_lsc_workspace_size(..., 0) bytes, 256-byte aligned. */
+ *   flags   0 or DELIMIT_LSC_OPERATOR_READY (the workspace already holds this
+ *           call's collapsed operator and bias vector; see above)
+ *   workspace >= delimit_lsc_workspace_size(..., 0) bytes, 256-byte aligned.
+ * BF16 runs on tcgen05 (FP32 accumulation), F32 on CUDA cores. */
 delimit_status delimit_lsc_forward(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
                                    const float* b, void* sh_out, int64_t n_vox, int c_in, int c_out,
                                    int64_t ld_in, int64_t ld_out, delimit_dtype act_t, unsigned flags,
@@ -205,8 +208,11 @@ delimit_status delimit_lsc_forward(const delimit_lsc_geometry* geom, const void*
  *   d_in  = adjoint of the forward in sh_in (same layout as sh_in), or NULL
  *   dw    = float32 [c_out, S_out, c_in, S_in, K] (zero outside the window), or NULL
  *   db    = float32 [c_out, S_out], or NULL
+ *   flags = DELIMIT_LSC_OPERATOR_READY reuses the operator a forward with the same
+ *   geometry, sizes, dtype and w built in this workspace (b is not needed here).
  * All outputs are overwritten (not accumulated).  Reductions over voxels are
- * deterministic (fixed split and order). */
+ * deterministic (fixed split and order).
+ *   workspace >= delimit_lsc_workspace_size(..., 1) bytes, 256-byte aligned. */
 delimit_status delimit_lsc_backward(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
                                     const void* d_out, void* d_in, float* dw, float* db, int64_t n_vox,
                                     int c_in, int c_out, int64_t ld_in, int64_t ld_out, delimit_dtype act_t,
