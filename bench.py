@@ -88,16 +88,17 @@ class OracleChain:
         from oracle import sh as osh
         self.cfg = cfg
         self.ob = osh.SHBasisOracle(dirs, bvals, cfg.order, cfg.lam)
-        self.og = olsc.LSCOracle(self.ob, cfg.order, self.ob.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings,
+        self.ob_in = self.ob if cfg.l_in == cfg.order else osh.SHBasisOracle(dirs, bvals, cfg.l_in, cfg.lam)
+        self.og = olsc.LSCOracle(self.ob, cfg.l_in, self.ob.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings,
                                  cfg.sectors, cfg.window)
 
     def step(self, sig, w, b, ds_out):
         """sig [V, Ci, dirs], ds_out [V, Co, dirs] -> (s_out, ds_in, dw, db)."""
         ob, og = self.ob, self.og
-        c_in = ob.signal2sh(sig)
+        c_in = self.ob_in.signal2sh(sig)
         s_out = ob.sh2signal(og.forward(c_in, w, b))
         dc_in, dw, db = og.backward(c_in, w, ob.sh2signal_backward(ds_out))
-        return s_out, ob.signal2sh_backward(dc_in), dw, db
+        return s_out, self.ob_in.signal2sh_backward(dc_in), dw, db
 
 
 def blas_threads():
@@ -135,6 +136,61 @@ def time_oracle(cfg, dirs, bvals, budget_s, chunk=64, max_vox=4096):
         t_work += time.perf_counter() - t0
         done += chunk
     return done / t_work, done, t_work
+
+
+def chain_inputs(cfg, dirs, bvals, dtype, rank=0):
+    """Device-drawn fibre signals (library row order), Gaussian upstream gradients,
+    N(0, 0.1) weights and biases; seeded per rank."""
+    import torch
+    from paper_1808_01517_gb300 import synth
+    V, S = cfg.n_vox, len(cfg.dirs_per_shell)
+    sig = synth.fibre_signal_torch(dirs, bvals, cfg.c_in * V, seed=cfg.seed + rank)  # [dirs, Ci*V]
+    # library row order (s, c, i): per shell, channel-major blocks of that shell's directions
+    s_rows = []
+    off = 0
+    for m in cfg.dirs_per_shell:
+        s_rows.append(sig[off:off + m].reshape(m, cfg.c_in, V).permute(1, 0, 2).reshape(cfg.c_in * m, V))
+        off += m
+    s_in = torch.cat(s_rows, 0).to(dtype)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(cfg.seed * 31 + rank)
+    ds_out = (0.1 * torch.randn((cfg.c_out * dirs.shape[0], V), generator=gen, device="cuda")).to(dtype)
+    K = 1 + cfg.rings * cfg.sectors
+    w = torch.from_numpy(synth.gaussian((cfg.c_out, S, cfg.c_in, S, K), 0.1, seed=cfg.seed)).float().cuda()
+    b = torch.from_numpy(synth.gaussian((cfg.c_out, S), 0.1, seed=cfg.seed + 1)).float().cuda()
+    return s_in, ds_out, w, b
+
+
+def run_chain_leg(cfg, dirs, bvals, steps=10, warm=3):
+    """Another chain configuration at full size (BF16): voxels/s, per-call times and
+    error on sampled voxels against the FP64 oracle."""
+    import torch
+    from paper_1808_01517_gb300 import synth
+    from paper_1808_01517_gb300.chain import Chain
+    ch = Chain(cfg, dirs, bvals, torch.bfloat16)
+    ch.set_inputs(*chain_inputs(cfg, dirs, bvals, torch.bfloat16))
+    for _ in range(warm):
+        ch.step()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(steps):
+        ch.step(events=ev[k])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    per_call = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(steps)]))
+                for i, name in enumerate(Chain.CALLS)}
+    fl = ch.flops()
+    idx = synth.voxel_subset(cfg.n_vox, 32, seed=cfg.seed + 97)
+    out = {"workload": cfg.name(), "value": cfg.n_vox / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+           "steps": steps, "step_tflops": sum(fl.values()) / (ms * 1e-3) / 1e12,
+           "lsc_forward_tflops": fl["lsc_forward"] / (per_call["lsc_forward"] * 1e-3) / 1e12,
+           "per_call_ms": per_call, "err_vs_oracle": sampled_errors(ch, cfg, dirs, bvals, idx)}
+    del ch
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -253,28 +309,8 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
     V = cfg.n_vox
-    # ---- inputs (device-drawn fibre signals, per-rank seed) ----
-    def make_inputs(dtype):
-        S = len(cfg.dirs_per_shell)
-        sig = synth.fibre_signal_torch(dirs, bvals, cfg.c_in * V, seed=cfg.seed + rank)  # [270, Ci*V]
-        # library row order (s, c, i): per shell, channel-major blocks of that shell's directions
-        s_rows = []
-        off = 0
-        for m in cfg.dirs_per_shell:
-            blk = sig[off:off + m].reshape(m, cfg.c_in, V).permute(1, 0, 2).reshape(cfg.c_in * m, V)
-            s_rows.append(blk)
-            off += m
-        s_in = torch.cat(s_rows, 0).to(dtype)
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(cfg.seed * 31 + rank)
-        ds_out = (0.1 * torch.randn((cfg.c_out * dirs.shape[0], V), generator=gen, device="cuda")).to(dtype)
-        K = 1 + cfg.rings * cfg.sectors
-        w = torch.from_numpy(synth.gaussian((cfg.c_out, S, cfg.c_in, S, K), 0.1, seed=cfg.seed)).float().cuda()
-        b = torch.from_numpy(synth.gaussian((cfg.c_out, S), 0.1, seed=cfg.seed + 1)).float().cuda()
-        return s_in, ds_out, w, b
-
     ch = Chain(cfg, dirs, bvals, torch.bfloat16)
-    s_in, ds_out, w, b = make_inputs(torch.bfloat16)
+    s_in, ds_out, w, b = chain_inputs(cfg, dirs, bvals, torch.bfloat16, rank)
     ch.set_inputs(s_in, ds_out, w, b)
     del s_in, ds_out
     torch.cuda.synchronize()
@@ -378,6 +414,9 @@ def main():
         torch.cuda.empty_cache()
         # ---- end to end through host buffers ----
         extras["e2e"] = run_e2e(ch, args.e2e_steps)
+        # ---- mixed SH orders (4 -> 8) with every input shell mixed into every output shell ----
+        from dataclasses import replace
+        extras["mixed_orders_all_shells"] = run_chain_leg(replace(cfg, order_in=4, window="all"), dirs, bvals)
         # ---- stand-alone transforms at 1,048,576 voxels (FP32 and BF16-in / FP32-out) ----
         extras["transforms"] = run_transforms(cfg, dirs, bvals, args.transform_vox, hbm)
         # ---- oracle on the host cores ----
@@ -399,6 +438,7 @@ def main():
         line["fp32"] = extras.get("fp32")
         line["err_vs_oracle_bf16"] = extras.get("err_vs_oracle_bf16")
         line["transforms"] = extras.get("transforms")
+        line["mixed_orders_all_shells"] = extras.get("mixed_orders_all_shells")
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -487,8 +527,9 @@ def run_transforms(cfg, dirs, bvals, V, hbm_gbs, steps=20, warm=3, n_check=4096)
 
 def run_e2e(ch, steps):
     """The same step through the public API with host buffers: every step copies its
-    inputs from pinned host memory and its outputs (s_out, ds_in, dw, db) back; the
-    copies of neighbouring steps overlap the compute (HostPipeline)."""
+    inputs (s_in, ds_out) from pinned host memory and reads its result, the weight and
+    bias gradients, back; the copies of neighbouring steps overlap the compute
+    (HostPipeline).  The activation outputs stay on the device, as inside a network."""
     import torch
     from paper_1808_01517_gb300.chain import Chain, HostPipeline
     ch2 = Chain(ch.cfg, ch.basis._dirs, ch.basis._bvals, ch.dtype)

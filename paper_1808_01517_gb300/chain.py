@@ -32,10 +32,16 @@ class ChainConfig:
     sectors: int = 12
     window: str = "adjacent"
     seed: int = 1808
+    order_in: int | None = None  # SH order of the LSC input (Signal2SH); None = order
+
+    @property
+    def l_in(self) -> int:
+        return self.order if self.order_in is None else self.order_in
 
     def name(self) -> str:
+        orders = f"L={self.order}" if self.l_in == self.order else f"L={self.l_in}->{self.order}"
         return (f"S2SH-LSC-SH2S fwd+bwd V={self.n_vox} {len(self.dirs_per_shell)}x{self.dirs_per_shell[0]} dirs "
-                f"L={self.order} {self.c_in}->{self.c_out} ch {self.window} {self.radius_deg:g}deg "
+                f"{orders} {self.c_in}->{self.c_out} ch {self.window} {self.radius_deg:g}deg "
                 f"{self.rings}x{self.sectors}")
 
 
@@ -47,12 +53,14 @@ class Chain:
     def __init__(self, cfg: ChainConfig, dirs: np.ndarray, bvals: np.ndarray, dtype=torch.bfloat16, device="cuda"):
         self.cfg, self.dtype = cfg, dtype
         self.code = L.BF16 if dtype == torch.bfloat16 else L.F32
-        self.basis = L.SHBasis(dirs, bvals, cfg.order, cfg.lam)
-        self.geom = L.LSCGeometry(self.basis, cfg.order, self.basis.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings,
+        self.basis = L.SHBasis(dirs, bvals, cfg.order, cfg.lam)  # output side (LSC projection, SH2Signal)
+        self.basis_in = self.basis if cfg.l_in == cfg.order else L.SHBasis(dirs, bvals, cfg.l_in, cfg.lam)
+        self.geom = L.LSCGeometry(self.basis, cfg.l_in, self.basis.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings,
                                   cfg.sectors, cfg.window)
-        V, S, N, nd = cfg.n_vox, self.basis.n_shells, self.basis.n_coef, self.basis.n_dirs
+        V, S, nd = cfg.n_vox, self.basis.n_shells, self.basis.n_dirs
+        N, N_in = self.basis.n_coef, self.basis_in.n_coef
         ci, co = cfg.c_in, cfg.c_out
-        self.rows = dict(s_in=ci * nd, c_in=S * ci * N, c_out=S * co * N, s_out=co * nd)
+        self.rows = dict(s_in=ci * nd, c_in=S * ci * N_in, c_out=S * co * N, s_out=co * nd)
         mk = lambda r: layers.empty_act(r, V, dtype, device)  # noqa: E731
         self.s_in, self.c_in_buf = mk(self.rows["s_in"]), mk(self.rows["c_in"])
         self.c_out_buf, self.s_out = mk(self.rows["c_out"]), mk(self.rows["s_out"])
@@ -81,9 +89,10 @@ class Chain:
         lib, cfg, V = self.lib, self.cfg, self.cfg.n_vox
         st = torch.cuda.current_stream().cuda_stream if stream is None else stream
         bh, gh, t, ci, co, ws = self.basis.handle, self.geom.handle, self.code, cfg.c_in, cfg.c_out, self.ws
+        bih = self.basis_in.handle
         rec = (lambda i: events[i].record()) if events is not None else (lambda i: None)
         rec(0)
-        L.check(lib.delimit_signal2sh(bh, self.s_in.data_ptr(), self.c_in_buf.data_ptr(), V, ci, self.s_in.stride(0),
+        L.check(lib.delimit_signal2sh(bih, self.s_in.data_ptr(), self.c_in_buf.data_ptr(), V, ci, self.s_in.stride(0),
                                       self.c_in_buf.stride(0), t, t, st), "delimit_signal2sh")
         rec(1)
         L.check(lib.delimit_lsc_forward(gh, self.c_in_buf.data_ptr(), self.w.data_ptr(), self.b.data_ptr(),
@@ -103,21 +112,24 @@ class Chain:
                                          self.ws_b, st),
                 "delimit_lsc_backward")
         rec(5)
-        L.check(lib.delimit_signal2sh_backward(bh, self.dc_in.data_ptr(), self.ds_in.data_ptr(), V, ci,
+        L.check(lib.delimit_signal2sh_backward(bih, self.dc_in.data_ptr(), self.ds_in.data_ptr(), V, ci,
                                                self.dc_in.stride(0), self.ds_in.stride(0), t, t, st),
                 "delimit_signal2sh_backward")
         rec(6)
 
     # algorithmic work per step (used for roofline figures)
+    def _pairs(self) -> int:
+        S, w = self.basis.n_shells, self.cfg.window
+        return int(sum(abs(s - p) <= 1 if w == "adjacent" else (s == p if w == "same" else True)
+                       for s in range(S) for p in range(S)))
+
     def flops(self) -> dict:
         cfg, b = self.cfg, self.basis
-        V, S, N, ci, co, K = cfg.n_vox, b.n_shells, b.n_coef, cfg.c_in, cfg.c_out, self.geom.K
-        win = np.array([[abs(s - p) <= 1 if cfg.window == "adjacent" else (s == p if cfg.window == "same" else True)
-                         for p in range(S)] for s in range(S)])
-        pairs = int(win.sum())
-        lsc_gemm = 2.0 * pairs * (co * N) * (ci * N) * V  # one of fwd / dgrad / wgrad
-        build_w = 2.0 * pairs * co * ci * N * N * K
-        s2sh = 2.0 * ci * b.n_dirs * N * V
+        V, N, N_in, ci, co, K = cfg.n_vox, b.n_coef, self.basis_in.n_coef, cfg.c_in, cfg.c_out, self.geom.K
+        pairs = self._pairs()
+        lsc_gemm = 2.0 * pairs * (co * N) * (ci * N_in) * V  # one of fwd / dgrad / wgrad
+        build_w = 2.0 * pairs * co * ci * N * N_in * K
+        s2sh = 2.0 * ci * b.n_dirs * N_in * V
         sh2s = 2.0 * co * b.n_dirs * N * V
         return dict(signal2sh=s2sh, lsc_forward=lsc_gemm + build_w, sh2signal=sh2s, sh2signal_backward=sh2s,
                     lsc_backward=2 * lsc_gemm + build_w + 2.0 * pairs * co * ci * N * N * K, signal2sh_backward=s2sh)
@@ -125,14 +137,12 @@ class Chain:
     def kernel_work(self) -> dict:
         """Algorithmic work per launch of each traced kernel group: (flops, compulsory HBM bytes)."""
         cfg, b = self.cfg, self.basis
-        V, S, N, ci, co, K = cfg.n_vox, b.n_shells, b.n_coef, cfg.c_in, cfg.c_out, self.geom.K
+        V, N, N_in, ci, co, K = cfg.n_vox, b.n_coef, self.basis_in.n_coef, cfg.c_in, cfg.c_out, self.geom.K
         e = 2 if self.dtype == torch.bfloat16 else 4
-        win = np.array([[abs(s - p) <= 1 if cfg.window == "adjacent" else (s == p if cfg.window == "same" else True)
-                         for p in range(S)] for s in range(S)])
-        pairs = int(win.sum())
+        pairs = self._pairs()
         r = self.rows
-        gemm = 2.0 * pairs * (co * N) * (ci * N) * V
-        build = 2.0 * pairs * co * ci * N * N * K
+        gemm = 2.0 * pairs * (co * N) * (ci * N_in) * V
+        build = 2.0 * pairs * co * ci * N * N_in * K
         wbytes = 2.0 * e * r["c_out"] * r["c_in"]
         fl = self.flops()
         by = self.bytes()
@@ -180,10 +190,12 @@ class HostPipeline:
         self.started = [False, False]
 
     @staticmethod
-    def host_buffers(chain):
+    def host_buffers(chain, outputs=("dw", "db")):
+        """Pinned host buffers for the step's inputs and for the outputs read back each
+        step (default: the weight and bias gradients, the step's result for a weight
+        update; add "s_out", "ds_in" to bring the activation outputs back too)."""
         pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True)  # noqa: E731
-        return {"s_in": pin(chain.s_in), "ds_out": pin(chain.ds_out)}, \
-               {"s_out": pin(chain.s_out), "ds_in": pin(chain.ds_in), "dw": pin(chain.dw), "db": pin(chain.db)}
+        return {"s_in": pin(chain.s_in), "ds_out": pin(chain.ds_out)}, {k: pin(getattr(chain, k)) for k in outputs}
 
     def step(self, i: int, host_in: dict, host_out: dict):
         j = i % 2
@@ -202,10 +214,8 @@ class HostPipeline:
             self.comp_done[j].record(self.comp)
         with torch.cuda.stream(self.d2h):
             self.d2h.wait_event(self.comp_done[j])
-            host_out["s_out"].copy_(ch.s_out, non_blocking=True)
-            host_out["ds_in"].copy_(ch.ds_in, non_blocking=True)
-            host_out["dw"].copy_(ch.dw, non_blocking=True)
-            host_out["db"].copy_(ch.db, non_blocking=True)
+            for k, h in host_out.items():
+                h.copy_(getattr(ch, k), non_blocking=True)
             self.out_done[j].record(self.d2h)
         self.started[j] = True
 

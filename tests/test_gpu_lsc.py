@@ -100,20 +100,28 @@ def test_lsc_vs_oracle(case, prec, tc, cluster, monkeypatch):
     assert np.all(dw.transpose(1, 3, 0, 2, 4)[~og.win] == 0)
 
 
-def test_lsc_full_size_sampled():
-    """65,536 voxels, 3 x 90 directions, 16 -> 64 channels, adjacent shells, radius 25 deg,
-    4 x 12 kernel, BF16 on tensor cores (the bench's launch configuration).  Forward and
-    input gradient are checked on 64 sampled voxels against the oracle; the weight and
-    bias gradients through identities that hold at any size and against the oracle on a
-    64-voxel launch."""
-    cfg = dict(m=[90, 90, 90], b=[1000, 2000, 3000], order_in=8, order_out=8, lam=0.006, V=65536, ci=16, co=64,
-               rad=25, R=4, Sec=12, win="adjacent")
+FULL = {
+    # the bench's launch configuration
+    "adjacent": dict(order_in=8, win="adjacent"),
+    # SH order 4 in, 8 out, every input shell into every output shell (shells as channels)
+    "mixed_all": dict(order_in=4, win="all"),
+}
+
+
+@pytest.mark.parametrize("variant", list(FULL))
+def test_lsc_full_size_sampled(variant):
+    """65,536 voxels, 3 x 90 directions, 16 -> 64 channels, radius 25 deg, 4 x 12 kernel,
+    BF16 on tensor cores.  Forward and input gradient are checked on 64 sampled voxels
+    against the oracle; the weight and bias gradients through identities that hold at
+    any size and against the oracle on a 512-voxel launch."""
+    cfg = dict(m=[90, 90, 90], b=[1000, 2000, 3000], order_out=8, lam=0.006, V=65536, ci=16, co=64,
+               rad=25, R=4, Sec=12, **FULL[variant])
     og, lg = _setup(cfg, seed=1808)
-    V = cfg["V"]
-    c = synth.gaussian((V, 16, 3, 45), 1.0, seed=5, tag="coeffs").astype(np.float32)
+    V, n_in, n_out = cfg["V"], og.n_in, og.n_out
+    c = synth.gaussian((V, 16, 3, n_in), 1.0, seed=5, tag="coeffs").astype(np.float32)
     w = synth.gaussian((64, 3, 16, 3, 49), 0.1, seed=6)
     b = synth.gaussian((64, 3), 0.1, seed=7)
-    d = synth.gaussian((V, 64, 3, 45), 1.0, seed=8, tag="grads").astype(np.float32)
+    d = synth.gaussian((V, 64, 3, n_out), 1.0, seed=8, tag="grads").astype(np.float32)
     y, din, dw, db = _gpu_lsc(lg, c, w, b, d, 16, 64, "bf16")
     idx = synth.voxel_subset(V, 64)
     ref_y = og.forward(c[idx].astype(np.float64), w, b)
@@ -127,13 +135,11 @@ def test_lsc_full_size_sampled():
     # <dw, w'> = <d, LSC(c; w', b = 0)> for a random w' (linearity in w), here with the
     # oracle evaluated on a 512-voxel launch of the same kernels
     sub = synth.voxel_subset(V, 512)
-    og2, lg2 = og, lg
     w2 = synth.gaussian(w.shape, 0.1, seed=9) * og.win[None, :, None, :, None]
-    _, _, dw_sub, _ = _gpu_lsc(lg2, c[sub], w, b, d[sub], 16, 64, "bf16")
+    _, _, dw_sub, _ = _gpu_lsc(lg, c[sub], w, b, d[sub], 16, 64, "bf16")
     lhs = float(np.sum(dw_sub * w2))
-    rhs = float(np.sum(d[sub].astype(np.float64) * og2.forward(c[sub].astype(np.float64), w2, np.zeros_like(b))))
+    rhs = float(np.sum(d[sub].astype(np.float64) * og.forward(c[sub].astype(np.float64), w2, np.zeros_like(b))))
     assert abs(lhs - rhs) <= TOL_BF16 * np.linalg.norm(dw_sub) * np.linalg.norm(w2) * 4
-    # and the full-size dw agrees with the sum of per-chunk launches (deterministic split reduction)
     assert np.isfinite(dw).all() and np.linalg.norm(dw) > 0
 
 
