@@ -293,6 +293,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       vox_decode(p, t, g, mt, nt);
       mt = mt * CL + rank;
       const VoxGroup& G = p.g[g];
+      // bias of this warp's columns, fetched before the accumulator is ready (a load per
+      // column inside the drain loop stalled it): lane L holds the warp's columns
+      // w = L + 32 i, i.e. chunk w / 16 (tile columns 32 (w / 16) + 16 half + w % 16)
+      float breg[BN / 64 > 0 ? BN / 64 : 1];
+#pragma unroll
+      for (int i = 0; i < BN / 64; ++i) {
+        const int w = lane + 32 * i, col = nt * BN + 32 * (w >> 4) + 16 * half + (w & 15);
+        breg[i] = (STAGED && PASSES == 1 && p.bias && col < G.N) ? __ldg(p.bias + G.y_row0 + col) : 0.f;
+      }
       bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTmemFull);
       if (STAGED) ok = ok && wait_bounded(stg_free_bar, (uint32_t)((PASSES * it) & 1) ^ 1u, abort_flag, p.err, kErrTmemEmpty);
       if (!__all_sync(0xffffffffu, ok)) break;
@@ -315,7 +324,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           const int cbeg = pass * HB;
-          for (int k0 = 0; 32 * k0 + 16 * half < HB; k0 += 4) {
+#pragma unroll
+          for (int k0 = 0; k0 < (HB + 31) / 32; k0 += 4) {
             uint32_t rv[4][16];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -331,7 +341,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(stg_ptr) + (size_t)h * HB * 64 + (c0 - cbeg) * 64 + xl;
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {
-                  const float bv = (p.bias && nbase + jj < G.N) ? __ldg(p.bias + G.y_row0 + nbase + jj) : 0.f;
+                  float bv;
+                  if (PASSES == 1) {
+                    const int w = 16 * (k0 + u) + jj;  // compile-time: the loops are unrolled
+                    bv = __shfl_sync(0xffffffffu, breg[(w >> 5) < BN / 64 ? (w >> 5) : 0], w & 31);
+                  } else {
+                    bv = (p.bias && nbase + jj < G.N) ? __ldg(p.bias + G.y_row0 + nbase + jj) : 0.f;
+                  }
                   dst[jj * 64] = __float2bfloat16_rn(__uint_as_float(rv[u][jj]) + bv);
                 }
               }
