@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int STAGES = p.stages;
-  // layout: [B images][A stages][2 output staging tiles][barriers]
+  // layout: [B images][A stages][2 output staging tiles [n_mma rows][128 voxels]][barriers]
   const uint32_t sbase = smem_u32(smem);
   const uint32_t a_base = sbase + p.b_total;
   const uint32_t stg_base = a_base + STAGES * p.stage_bytes;
@@ -164,13 +164,12 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
     mma_commit(drain_bar);
     wait_drain(drain_bar, 0, p.err, kErrDrain);
   } else if (warp >= 2) {
-    // TMEM -> registers -> shared staging tile [rows][64 voxels] x 2 halves -> TMA store.
+    // TMEM -> registers -> shared staging tile [rows][128 voxels] -> one TMA store.
     // Two staging buffers; stg_ready (4 warp arrivals) hands a filled buffer to the
     // storing lane, stg_free (1 arrival) returns it once its store has read it.
-    constexpr int ES = OUT_F32 ? 4 : 2;
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;  // which 16-column chunks: 2k + half
-    const int h = q >> 1, xl = (q & 1) * 32 + lane;  // voxel half and voxel within the half
+    const int xl = q * 32 + lane;  // this thread's voxel within the 128-voxel tile
     int acc = 0;
     uint32_t acc_phase = 0;
     int it = 0;
@@ -187,7 +186,8 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
       tc_fence_after();
       // each voxel half holds n_mma rows (a multiple of 16): the stores below need no bounds
       // checks; the TMA store reads only the first n_out rows of each half
-      uint8_t* stg = stg_ptr + (size_t)buf * p.stg_bytes + (size_t)h * G.n_mma * 64 * ES;
+      // staging tile [n_mma rows][128 voxels]: one 256-byte (BF16) run per output row
+      uint8_t* stg = stg_ptr + (size_t)buf * p.stg_bytes;
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
       // this warp's chunks: c0 = 16 * (2k + half); up to four loads in flight per wait
       for (int k0 = 0; 32 * k0 + 16 * half < G.n_mma; k0 += 4) {
@@ -207,13 +207,13 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
           const int c0 = 32 * (k0 + u) + 16 * half;
           if (u < nld) {
             if (OUT_F32) {
-              float* dst = reinterpret_cast<float*>(stg) + c0 * 64 + xl;
+              float* dst = reinterpret_cast<float*>(stg) + c0 * 128 + xl;
 #pragma unroll
-              for (int j = 0; j < 16; ++j) dst[j * 64] = __uint_as_float(rv[u][j]);
+              for (int j = 0; j < 16; ++j) dst[j * 128] = __uint_as_float(rv[u][j]);
             } else {
-              __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(stg) + c0 * 64 + xl;
+              __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(stg) + c0 * 128 + xl;
 #pragma unroll
-              for (int j = 0; j < 16; ++j) dst[j * 64] = __float2bfloat16_rn(__uint_as_float(rv[u][j]));
+              for (int j = 0; j < 16; ++j) dst[j * 128] = __float2bfloat16_rn(__uint_as_float(rv[u][j]));
             }
           }
         }
@@ -232,8 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
           lead_ok = wait_bounded(stg_ready_bar(buf), use_par, abort_flag, p.err, kErrTFull);
           if (lead_ok) {
             const uint32_t src = stg_base + (uint32_t)(buf * p.stg_bytes);
-            tma_store_3d(&p.mapY[g], src, mt * 128, 0, c);
-            tma_store_3d(&p.mapY[g], src + (uint32_t)(G.n_mma * 64 * ES), mt * 128 + 64, 0, c);
+            tma_store_3d(&p.mapY[g], src, mt * 128, 0, c);  // box {128 voxels, n_out rows, 1}
             bulk_commit();
             // the previous tile's store has finished reading its buffer: release it
             bulk_wait_read<1>();
@@ -429,7 +428,7 @@ cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X,
     const char* base = static_cast<const char*>(Y) + G.y_row0 * ldy * es;
     cuuint64_t dims[3] = {(cuuint64_t)n_vox, (cuuint64_t)G.n_out, (cuuint64_t)C};
     cuuint64_t strides[2] = {(cuuint64_t)ldy * es, (cuuint64_t)(G.y_cstride * ldy * es)};
-    cuuint32_t box[3] = {64, (cuuint32_t)G.n_out, 1};
+    cuuint32_t box[3] = {128, (cuuint32_t)G.n_out, 1};
     cuuint32_t esz[3] = {1, 1, 1};
     if (fn(&p.mapY[s], out_t == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
            const_cast<char*>(base), dims, strides, box, esz, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
