@@ -30,12 +30,20 @@ sys.path.insert(0, HERE)
 METRIC = "voxels/s, Signal2SH->LSC->SH2Signal fwd+bwd, BF16 vs FP32 at stated error vs FP64 oracle"
 UNIT = "voxels/s"
 
-# DRAM traffic (read + write) of one launch from an ncu capture of the 16,384-voxel
-# case (profiles/lsc_kernels_16384vox_ncu.md), scaled by the voxel count; valid only
-# while the kernel's sources hash to the value recorded with the capture.
+# DRAM traffic (read + write) of one launch at the 65,536-voxel workload, from the
+# single-pass ncu capture summarised in profiles/lsc_kernels_16384vox_ncu.md (the
+# `dram__bytes_*` metrics, the bench command itself); valid only while the kernel's
+# sources hash to the value recorded with the capture.
+_GEMM = ("csrc/tc_gemm.cu", "csrc/tc_ptx.cuh"), "3054bf3a20325923"
+_TF = ("csrc/tc_transform.cu", "csrc/tc_ptx.cuh"), "13967c03ccaf50b5"
 NCU_TRAFFIC = {
-    "lsc_fwd_gemm": {"bytes": 361.6e6, "n_vox": 16384, "sources": ("csrc/tc_gemm.cu", "csrc/tc_ptx.cuh"),
-                     "sha256_16": "2dd6c299a8c8e4f6"},
+    "lsc_fwd_gemm": {"bytes": 1.600e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "lsc_dgrad_gemm": {"bytes": 2.359e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "lsc_wgrad_gemm": {"bytes": 4.069e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "signal2sh_tc": {"bytes": 0.8136e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
+    "sh2signal_tc": {"bytes": 3.333e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
+    "sh2signal_bwd_tc": {"bytes": 3.358e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
+    "signal2sh_bwd_tc": {"bytes": 0.7845e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
 }
 
 
@@ -50,7 +58,9 @@ def ncu_traffic(kernel: str, n_vox: int):
             h.update(f.read())
     if h.hexdigest()[:16] != rec["sha256_16"]:
         return None  # the kernel changed since the counters were taken
-    return rec["bytes"] * n_vox / rec["n_vox"]
+    if n_vox != rec["n_vox"]:
+        return None  # counters were taken at another workload size
+    return rec["bytes"]
 
 
 def parse():
@@ -372,7 +382,7 @@ def main():
         avg = rec["ms"] / max(1, rec["n"])
         f, bb = work.get(name, (0.0, 0.0))
         kernels[name] = {"launches": rec["n"], "avg_ms": avg, "share": 0.0, "tflops": f / (avg * 1e-3) / 1e12,
-                         "gbs": bb / (avg * 1e-3) / 1e9}
+                         "gbs": bb / (avg * 1e-3) / 1e9, "traffic": ncu_traffic(name, V)}
     tot = sum(v["avg_ms"] * v["launches"] for v in kernels.values()) or 1.0
     for v in kernels.values():
         v["share"] = v["avg_ms"] * v["launches"] / tot
