@@ -123,6 +123,24 @@ delimit_status delimit_sh2signal(const delimit_sh_basis* basis, const void* sh, 
                                  int channels, int64_t ld_sh, int64_t ld_sig, delimit_dtype in_t,
                                  delimit_dtype out_t, void* stream);
 
+/* Signal2SH of selected voxels of a volume with the b = 0 normalisation fused into
+ * the load (Sec. 2.2: the signal is divided by the b = 0 image before fitting):
+ *   sh[(s,c,:), k] = P_s dwi[(s,c,:), index[k]] / b0[index[k]]   for k < n.
+ *   dwi    device, signal rows (channels x directions, layout above) x n_src
+ *          voxels, row stride ld_dwi elements, dtype in_t (no alignment rule)
+ *   b0     device float32 [n_src] (voxels with b0 <= 0 give zero coefficients),
+ *          or NULL for an already normalised signal
+ *   index  device int64 [n], source voxels (e.g. from delimit_mask_compact); an
+ *          index outside [0, n_src) gives zero coefficients and sets the device
+ *          error word (delimit_device_error, code 0x2100)
+ *   sh     device, SH rows x n, ld_sh (16-byte rule), dtype out_t
+ * Errors: INVALID_ARG (null pointers, sizes), UNSUPPORTED (more than 128
+ * directions in a shell or more than 120 coefficients). */
+delimit_status delimit_signal2sh_gather(const delimit_sh_basis* basis, const void* dwi, int64_t ld_dwi,
+                                        int64_t n_src, const float* b0, const int64_t* index, int64_t n,
+                                        void* sh, int64_t ld_sh, int channels, delimit_dtype in_t,
+                                        delimit_dtype out_t, void* stream);
+
 /* Adjoints used by back-propagation: d_sig = P_s^T d_sh and d_sh = B_s^T d_sig. */
 delimit_status delimit_signal2sh_backward(const delimit_sh_basis* basis, const void* d_sh, void* d_sig,
                                           int64_t n_vox, int channels, int64_t ld_sh, int64_t ld_sig,
@@ -273,9 +291,10 @@ delimit_status delimit_lsc_forward_noalloc(const delimit_lsc_geometry* geom, con
 /* ------------------------------------------------------------------------ */
 
 /* Synchronises `stream`, then reads and clears the device error word that
- * bounded device-side waits set when they run out.  *code receives the raw
- * word (0 = none).  Returns DEVICE_TIMEOUT if it was set, CUDA if the
- * synchronisation failed, OK otherwise. */
+ * bounded device-side waits set when they run out (and a gathered Signal2SH sets
+ * for an index out of range, code 0x2100).  *code receives the raw word (0 =
+ * none).  Returns DEVICE_TIMEOUT for a wait that ran out, INVALID_ARG for code
+ * 0x2100, CUDA if the synchronisation failed, OK otherwise. */
 delimit_status delimit_device_error(void* stream, int* code);
 
 /* Process-wide switch, default 1: BF16 steps run on the tcgen05 tensor-core

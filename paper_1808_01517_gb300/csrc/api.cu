@@ -314,6 +314,52 @@ delimit_status delimit_signal2sh(const delimit_sh_basis* b, const void* sig, voi
   return run_transform(b, sig, sh, n_vox, channels, ld_sig, ld_sh, in_t, out_t, stream, kS2SH);
 }
 
+delimit_status delimit_signal2sh_gather(const delimit_sh_basis* b, const void* dwi, int64_t ld_dwi, int64_t n_src,
+                                        const float* b0, const int64_t* index, int64_t n, void* sh, int64_t ld_sh,
+                                        int channels, delimit_dtype in_t, delimit_dtype out_t, void* stream) {
+  if (!b) return fail(DELIMIT_ERR_INVALID_ARG, "basis is NULL");
+  if (!b->on_device) return fail(DELIMIT_ERR_INVALID_ARG, "basis was created with DELIMIT_HOST_ONLY");
+  if (!b->h.has_pinv) return fail(DELIMIT_ERR_INVALID_ARG, "basis was created with DELIMIT_EVAL_ONLY (no pseudo-inverse)");
+  if (n < 0 || n_src < 1 || channels < 1 || channels > 65535 || ld_dwi < n_src)
+    return fail(DELIMIT_ERR_INVALID_ARG, "need n >= 0, n_src >= 1, 1 <= channels <= 65535, ld_dwi >= n_src");
+  if (!valid_dtype(in_t) || !valid_dtype(out_t)) return fail(DELIMIT_ERR_INVALID_ARG, "bad dtype");
+  if (n == 0) return DELIMIT_OK;
+  if (!dwi || !index) return fail(DELIMIT_ERR_INVALID_ARG, "dwi and index must not be NULL");
+  delimit_status st = check_device(b->device);
+  if (st != DELIMIT_OK) return st;
+  if ((st = check_act(sh, ld_sh, n, out_t, "sh")) != DELIMIT_OK) return st;
+  const int N = b->h.N, S = int(b->h.shells.size());
+  TransformArgs a;
+  std::memset(&a, 0, sizeof a);
+  int max_out = 0;
+  for (int s = 0; s < S; ++s) {
+    const ShellHost& shl = b->h.shells[s];
+    if (shl.m > 128 || N > 120) return fail(DELIMIT_ERR_UNSUPPORTED, "gathered Signal2SH: <= 128 directions per shell, <= 120 coefficients");
+    TransformGroup& g = a.g[s];
+    g.T = b->dev[s].P;
+    g.n_out = N;
+    g.n_in = shl.m;
+    g.x_row0 = int64_t(channels) * shl.dir_off;
+    g.x_cstride = shl.m;
+    g.y_row0 = int64_t(s) * channels * N;
+    g.y_cstride = N;
+    max_out = std::max(max_out, N);
+  }
+  a.X = dwi;
+  a.Y = sh;
+  a.n_vox = n;
+  a.ldx = ld_dwi;
+  a.ldy = ld_sh;
+  a.channels = channels;
+  a.index = index;
+  a.b0 = b0;
+  a.n_src = n_src;
+  a.err = b->err_word;
+  cudaError_t e = launch_transform_gather(a, S, max_out, int(in_t), int(out_t), reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gathered Signal2SH launch");
+  return DELIMIT_OK;
+}
+
 delimit_status delimit_sh2signal(const delimit_sh_basis* b, const void* sh, void* sig, int64_t n_vox, int channels,
                                  int64_t ld_sh, int64_t ld_sig, delimit_dtype in_t, delimit_dtype out_t, void* stream) {
   return run_transform(b, sh, sig, n_vox, channels, ld_sh, ld_sig, in_t, out_t, stream, kSH2S);
@@ -743,6 +789,7 @@ delimit_status delimit_device_error(void* stream, int* code) {
   if (code) *code = v;
   if (v) {
     cudaMemset(wd, 0, sizeof(int));
+    if (v == kErrGatherIndex) return fail(DELIMIT_ERR_INVALID_ARG, "gathered Signal2SH: an index outside [0, n_src)");
     char buf[96];
     std::snprintf(buf, sizeof buf, "device wait timed out (code 0x%x)", v);
     return fail(DELIMIT_ERR_DEVICE_TIMEOUT, buf);

@@ -25,11 +25,22 @@ struct TransformArgs {
   void* Y;
   int64_t n_vox, ldx, ldy;
   int channels;
+  // gathered input (Signal2SH of masked voxels): output voxel v reads input column
+  // index[v] < n_src divided by b0[index[v]] (b0 NULL: no division); err gets a code
+  // for an index out of range (that voxel's output is zero)
+  const int64_t* index = nullptr;
+  const float* b0 = nullptr;
+  int64_t n_src = 0;
+  int* err = nullptr;
 };
 
 // dtype codes as in the C ABI: 0 = F32, 1 = BF16
 cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_out, int in_t, int out_t,
                                   cudaStream_t st);
+// the gathered form (a.index set); n_in <= 128 and n_out <= 120 (else cudaErrorInvalidValue)
+cudaError_t launch_transform_gather(const TransformArgs& a, int n_groups, int max_out, int in_t, int out_t,
+                                    cudaStream_t st);
+constexpr int kErrGatherIndex = 0x2100;  // device error word: a gather index outside [0, n_src)
 
 // ---- LSC ----
 struct LscDims {

@@ -8,6 +8,7 @@
 //   reduce_dw        dW -> kernel-point weights dw and bias gradient db
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -117,13 +118,18 @@ __device__ __forceinline__ void st_y4(__nv_bfloat16* p, float a, float b, float 
   *reinterpret_cast<uint2*>(p) = u;
 }
 
-template <typename Tin, typename Tout>
+// GATHER: output voxel v reads input column a.index[v] scaled by 1 / a.b0[index[v]]
+// (plain loads into an FP32 tile: columns are not contiguous).
+template <typename Tin, typename Tout, bool GATHER>
 __global__ void __launch_bounds__(32 * (kTfMaxOut / kTfOpt)) transform_staged_kernel(const __grid_constant__ TransformArgs a,
                                                                                      int n_groups, int og_count,
                                                                                      int max_in) {
+  using Ts = typename std::conditional<GATHER, float, Tin>::type;  // type of the staged input tile
   extern __shared__ float4 tf_smem4[];
   float* Tt = reinterpret_cast<float*>(tf_smem4);                 // [max_in][12 * og_count]
-  Tin* Xs = reinterpret_cast<Tin*>(Tt + max_in * kTfOpt * og_count);  // [max_in][128]
+  Ts* Xs = reinterpret_cast<Ts*>(Tt + max_in * kTfOpt * og_count);  // [max_in][128]
+  int64_t* sidx = reinterpret_cast<int64_t*>(Xs + max_in * kTfVox);  // GATHER: source column per voxel
+  float* sinv = reinterpret_cast<float*>(sidx + kTfVox);            // GATHER: 1 / b0 per voxel
   const int ldt = kTfOpt * og_count;
   const int tid = threadIdx.x, q = tid % 32, og = tid / 32;
   const int64_t vt_count = (a.n_vox + kTfVox - 1) / kTfVox;
@@ -139,16 +145,46 @@ __global__ void __launch_bounds__(32 * (kTfMaxOut / kTfOpt)) transform_staged_ke
     const int64_t v0 = (r % vt_count) * kTfVox;
     const TransformGroup& G = a.g[g];
     __syncthreads();  // the previous tile's reads of Xs (and Tt) are done
-    // input rows of this tile: all copies in flight at once, zero past n_vox
-    const Tin* X = reinterpret_cast<const Tin*>(a.X) + (G.x_row0 + (int64_t)c * G.x_cstride) * a.ldx + v0;
-    const uint32_t xs_base = (uint32_t)__cvta_generic_to_shared(Xs);
-    for (int i = tid; i < G.n_in * kChunksPerRow; i += blockDim.x) {
-      const int j = i / kChunksPerRow, ch = i % kChunksPerRow;
-      const int64_t vv = v0 + (int64_t)ch * kChunkElems;
-      const int64_t left = a.n_vox - vv;
-      const int bytes = left >= kChunkElems ? 16 : (left > 0 ? (int)left * (int)sizeof(Tin) : 0);
-      const Tin* src = X + (int64_t)j * a.ldx + (int64_t)ch * kChunkElems;
-      cp_async16(xs_base + (uint32_t)((j * kTfVox + ch * kChunkElems) * sizeof(Tin)), bytes > 0 ? src : X, bytes);
+    if (GATHER) {
+      // source columns and b0 factors of this tile's voxels, then every input row
+      for (int vv = tid; vv < kTfVox; vv += blockDim.x) {  // the block may have fewer than 128 threads
+        const int64_t v = v0 + vv;
+        int64_t src = -1;
+        float inv = 0.f;
+        if (v < a.n_vox) {
+          src = a.index[v];
+          if (src < 0 || src >= a.n_src) {
+            if (a.err) atomicCAS(a.err, 0, kErrGatherIndex);
+            src = -1;
+          } else if (a.b0) {
+            const float b = a.b0[src];
+            inv = b > 0.f ? 1.f / b : 0.f;
+          } else {
+            inv = 1.f;
+          }
+        }
+        sidx[vv] = src;
+        sinv[vv] = inv;
+      }
+      __syncthreads();
+      const Tin* Xg = reinterpret_cast<const Tin*>(a.X) + (G.x_row0 + (int64_t)c * G.x_cstride) * a.ldx;
+      for (int i = tid; i < G.n_in * kTfVox; i += blockDim.x) {
+        const int j = i / kTfVox, vv = i % kTfVox;
+        const int64_t src = sidx[vv];
+        reinterpret_cast<float*>(Xs)[i] = src >= 0 ? ldf(Xg + (int64_t)j * a.ldx + src) * sinv[vv] : 0.f;
+      }
+    } else {
+      // input rows of this tile: all copies in flight at once, zero past n_vox
+      const Tin* X = reinterpret_cast<const Tin*>(a.X) + (G.x_row0 + (int64_t)c * G.x_cstride) * a.ldx + v0;
+      const uint32_t xs_base = (uint32_t)__cvta_generic_to_shared(Xs);
+      for (int i = tid; i < G.n_in * kChunksPerRow; i += blockDim.x) {
+        const int j = i / kChunksPerRow, ch = i % kChunksPerRow;
+        const int64_t vv = v0 + (int64_t)ch * kChunkElems;
+        const int64_t left = a.n_vox - vv;
+        const int bytes = left >= kChunkElems ? 16 : (left > 0 ? (int)left * (int)sizeof(Tin) : 0);
+        const Tin* src = X + (int64_t)j * a.ldx + (int64_t)ch * kChunkElems;
+        cp_async16(xs_base + (uint32_t)((j * kTfVox + ch * kChunkElems) * sizeof(Tin)), bytes > 0 ? src : X, bytes);
+      }
     }
     if (g != cur_g) {  // the group's operator, transposed: Tt[j][o] = T[o][j], zero past n_out
       for (int i = tid; i < G.n_in * ldt; i += blockDim.x) {
@@ -166,7 +202,7 @@ __global__ void __launch_bounds__(32 * (kTfMaxOut / kTfOpt)) transform_staged_ke
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[o][v] = 0.f;
       const float* tcol = Tt + og * kTfOpt;
-      const Tin* xq = Xs + 4 * q;
+      const Ts* xq = Xs + 4 * q;
 #pragma unroll 2
       for (int j = 0; j < G.n_in; ++j) {
         const float4 x = ld_x4(xq + j * kTfVox);
@@ -201,15 +237,18 @@ __global__ void __launch_bounds__(32 * (kTfMaxOut / kTfOpt)) transform_staged_ke
   }
 }
 
-template <typename Tin, typename Tout>
+template <typename Tin, typename Tout, bool GATHER = false>
 static cudaError_t transform_dispatch(const TransformArgs& a, int n_groups, int max_out, cudaStream_t st) {
   int max_in = 0;
   for (int g = 0; g < n_groups; ++g) max_in = std::max(max_in, a.g[g].n_in);
+  if (GATHER && (max_out > kTfMaxOut || max_in > 128)) return cudaErrorInvalidValue;
   if (max_out <= kTfMaxOut && max_in <= 128) {
     const int og_count = (max_out + kTfOpt - 1) / kTfOpt;
     const int threads = 32 * og_count;
-    const size_t smem = (size_t)max_in * kTfOpt * og_count * sizeof(float) + (size_t)max_in * kTfVox * sizeof(Tin);
-    auto kern = transform_staged_kernel<Tin, Tout>;
+    const size_t smem = (size_t)max_in * kTfOpt * og_count * sizeof(float) +
+                        (size_t)max_in * kTfVox * (GATHER ? sizeof(float) : sizeof(Tin)) +
+                        (GATHER ? (size_t)kTfVox * (sizeof(int64_t) + sizeof(float)) : 0);
+    auto kern = transform_staged_kernel<Tin, Tout, GATHER>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
@@ -234,6 +273,16 @@ static cudaError_t transform_dispatch(const TransformArgs& a, int n_groups, int 
     { transform_simt_kernel<Tin, Tout, 48, VPT><<<grid, 128, 0, st>>>(a, och); count_launch(); }
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_transform_gather(const TransformArgs& a, int n_groups, int max_out, int in_t, int out_t,
+                                    cudaStream_t st) {
+  TraceScope trace("signal2sh_gather", st);
+  if (a.n_vox == 0) return cudaSuccess;
+  if (in_t == 0 && out_t == 0) return transform_dispatch<float, float, true>(a, n_groups, max_out, st);
+  if (in_t == 1 && out_t == 0) return transform_dispatch<__nv_bfloat16, float, true>(a, n_groups, max_out, st);
+  if (in_t == 0 && out_t == 1) return transform_dispatch<float, __nv_bfloat16, true>(a, n_groups, max_out, st);
+  return transform_dispatch<__nv_bfloat16, __nv_bfloat16, true>(a, n_groups, max_out, st);
 }
 
 cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_out, int in_t, int out_t,

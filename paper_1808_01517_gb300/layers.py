@@ -82,6 +82,26 @@ def transform(kind: str, basis: L.SHBasis, x: torch.Tensor, channels: int, out_d
     return out
 
 
+def signal2sh_gather(basis: L.SHBasis, dwi: torch.Tensor, index: torch.Tensor, n: int | None = None,
+                     b0: torch.Tensor | None = None, channels: int = 1, out_dtype=None) -> torch.Tensor:
+    """Signal2SH of the voxels ``index`` (int64, device) of the volume ``dwi``
+    [channels x directions, n_src], divided by ``b0`` [n_src] (float32) first when
+    given; returns SH rows [S*channels*N, n]."""
+    if dwi.dim() != 2 or dwi.stride(1) != 1:
+        raise ValueError("dwi is 2-D [rows, voxels] with unit voxel stride")
+    n = int(index.numel()) if n is None else int(n)
+    out = empty_act(basis.n_shells * channels * basis.n_coef, max(n, 1), out_dtype or dwi.dtype, dwi.device)[:, :n]
+    b0p = None
+    if b0 is not None:
+        b0 = b0.contiguous().float()
+        b0p = b0.data_ptr()
+    index = index.contiguous()
+    L.check(L.get().delimit_signal2sh_gather(basis.handle, dwi.data_ptr(), dwi.stride(0), dwi.shape[1], b0p,
+                                             index.data_ptr(), n, out.data_ptr(), out.stride(0), channels,
+                                             _code(dwi), _DT[out.dtype], _stream()), "delimit_signal2sh_gather")
+    return out
+
+
 def lsc_workspace(geom: L.LSCGeometry, n_vox: int, c_in: int, c_out: int, dtype, backward: bool, device="cuda"):
     """(keep-alive tensor, 256-byte aligned pointer, bytes) of an LSC workspace."""
     ws_n = geom.workspace_size(n_vox, c_in, c_out, _DT[dtype], backward)

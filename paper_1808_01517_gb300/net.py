@@ -92,7 +92,11 @@ class SphericalNet(torch.nn.Module):
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
         """x [n_in_dirs, V] (b0-normalised) -> [270, V] in the target table's row order."""
-        h = self.s2sh(x.to(self.dtype))
+        return self.forward_sh(self.s2sh(x.to(self.dtype)))
+
+    def forward_sh(self, h: torch.Tensor) -> torch.Tensor:
+        """From the input's SH coefficients (the Signal2SH output, e.g. of a gathered,
+        b0-normalised load) to the [270, V] prediction."""
         for i, lsc in enumerate(self.lscs):
             h = lsc(h)
             if i < len(self.lscs) - 1:

@@ -6,10 +6,13 @@ gradient table: the base 3 x 90 table rotated by a seeded rotation of at most
 5 deg plus per-direction jitter of at most 2 deg (the distorted gradient
 directions the paper names as the reason for a uniform SH representation,
 Sec. 1).  Every subject gets its own FP64 pseudo-inverses and LSC geometries;
-the trained network's weights are shared.  For all subjects, in one launch
-sequence: mask compaction (table T5), gather of the masked voxels, the network
-forward in BF16, scatter of the dense 270-direction prediction into the output
-volume.
+the trained network's weights are shared.  The acquisition is stored raw: the
+normalised signal times a smooth S0 field (b = 0 image, with noise), so the
+normalisation the paper asks for before fitting (Sec. 2.2) happens on the device.
+For all subjects, in one launch sequence: mask compaction (table T5), Signal2SH
+of the masked voxels with the division by b0 fused into its load (no separate
+gather or normalisation pass), the rest of the network in BF16, scatter of the
+dense 270-direction prediction into the output volume.
 """
 from __future__ import annotations
 
@@ -39,15 +42,27 @@ class Subject:
         self.net.load_state_dict(state)
         self.table_seconds = time.perf_counter() - t0
         self.net.eval()
-        # the acquisition: noisy 30-direction signal inside the mask, zero outside
+        # the acquisition: noisy 30-direction signal inside the mask, zero outside, times S0
         n_mask = int(self.mask.sum())
         sig = synth.fibre_signal_torch(self.dirs[sel], np.full(len(sel), 1000.0), n_mask, seed=seed + 7, sub=idx,
                                        max_fibres=3, snr=(15.0, 40.0))
+        midx = torch.from_numpy(np.flatnonzero(self.mask.reshape(-1))).cuda()
+        self.b0 = self.s0_field(shape, seed, idx)  # float32 [n]
         self.volume = layers.empty_act(len(sel), self.n, torch.bfloat16)
         self.volume.zero_()
-        midx = torch.from_numpy(np.flatnonzero(self.mask.reshape(-1))).cuda()
-        self.volume[:, midx] = sig.to(torch.bfloat16)
+        self.volume[:, midx] = (sig * self.b0[midx]).to(torch.bfloat16)
         self.mask_dev = torch.from_numpy(self.mask.reshape(-1).astype(np.uint8)).cuda()
+
+    @staticmethod
+    def s0_field(shape, seed, sub):
+        """A smooth positive S0 (b = 0) image with 1 % noise, float32 on the device."""
+        g = torch.Generator(device="cuda")
+        g.manual_seed(seed * 1000 + sub)
+        axes = [torch.linspace(-1.0, 1.0, n, device="cuda") for n in shape]
+        zz, yy, xx = torch.meshgrid(*axes, indexing="ij")
+        field = 1000.0 * (1.0 + 0.3 * torch.cos(2.0 * zz) * torch.cos(1.5 * yy) - 0.2 * xx * xx)
+        noise = 1.0 + 0.01 * torch.randn(field.shape, generator=g, device="cuda")
+        return (field * noise).reshape(-1).float().contiguous()
 
 
 def run(subjects, chunk: int = 1 << 18):
@@ -79,11 +94,10 @@ def run(subjects, chunk: int = 1 << 18):
             total += k
             for v0 in range(0, k, chunk):
                 m = min(chunk, k - v0)
-                x = layers.empty_act(len(sb.sel), m, torch.bfloat16)
-                L.check(lib.delimit_gather_voxels(sb.volume.data_ptr(), sb.volume.stride(0), sb.n, len(sb.sel),
-                                                  idx[v0:].data_ptr(), m, x.data_ptr(), x.stride(0), L.BF16, st),
-                        "delimit_gather_voxels")
-                y = sb.net(x)
+                # Signal2SH of the chunk's masked voxels, divided by b0 in the load
+                h = layers.signal2sh_gather(sb.net.s2sh.basis, sb.volume, idx[v0:], m, b0=sb.b0, channels=1,
+                                            out_dtype=torch.bfloat16)
+                y = sb.net.forward_sh(h)
                 L.check(lib.delimit_scatter_voxels(y.data_ptr(), y.stride(0), n_dirs, idx[v0:].data_ptr(), m,
                                                    out.data_ptr(), out.stride(0), sb.n, L.BF16, st),
                         "delimit_scatter_voxels")
@@ -96,12 +110,22 @@ def main():
     import argparse
     import json
     ap = argparse.ArgumentParser(description="Whole-volume inference with per-subject gradient tables")
-    ap.add_argument("--model", required=True, help="state saved by paper_1808_01517_gb300.net --save")
+    ap.add_argument("--model", help="state saved by paper_1808_01517_gb300.net --save")
+    ap.add_argument("--random-init", action="store_true",
+                    help="seeded untrained weights (throughput only; the prediction is meaningless)")
     ap.add_argument("--subjects", type=int, default=16)
     ap.add_argument("--mask-voxels", type=int, default=900_000)
     args = ap.parse_args()
-    ck = torch.load(args.model, map_location="cuda")
-    cfg = NetConfig(**{k: (tuple(v) if isinstance(v, list) else v) for k, v in ck["cfg"].items()})
+    if args.random_init:
+        from .net import tables
+        cfg = NetConfig()
+        d, b, sel = tables(cfg)
+        ck = {"state": SphericalNet(cfg, d[sel], d, b).state_dict()}
+    elif args.model:
+        ck = torch.load(args.model, map_location="cuda")
+        cfg = NetConfig(**{k: (tuple(v) if isinstance(v, list) else v) for k, v in ck["cfg"].items()})
+    else:
+        ap.error("give --model or --random-init")
     t0 = time.perf_counter()
     subs = [Subject(i, cfg, ck["state"], mask_voxels=args.mask_voxels) for i in range(args.subjects)]
     setup = time.perf_counter() - t0
@@ -110,6 +134,7 @@ def main():
     o = outs[0].float()
     m = torch.from_numpy(subs[0].mask.reshape(-1)).cuda()
     res = {"subjects": len(subs), "voxels": vox, "seconds": secs, "voxels_per_s": vox / secs,
+           "weights": "random-init" if args.random_init else args.model,
            "table_seconds_total": sum(s.table_seconds for s in subs), "setup_seconds": setup,
            "finite": bool(torch.isfinite(o[:, m]).all()), "outside_zero": bool((o[:, ~m] == 0).all()),
            "mean_b1000_inside": float(o[:90, m].mean())}

@@ -74,3 +74,29 @@ def test_leaky_relu_pair():
     xn, gn = x.cpu().numpy(), g.cpu().numpy()
     np.testing.assert_array_equal(y.cpu().numpy(), np.where(xn > 0, xn, np.float32(0.1) * xn))
     np.testing.assert_allclose(xa.grad.cpu().numpy(), np.where(xn > 0, gn, 0.1 * gn), rtol=1e-7)
+
+
+def test_volume_run_fused_normalisation_matches_unfused_network():
+    """volume.run (mask compaction -> Signal2SH with the b0 division fused into its
+    gathered load -> network -> scatter) against the plain network on the same
+    voxels normalised outside the library."""
+    from paper_1808_01517_gb300 import volume
+    from paper_1808_01517_gb300.net import NetConfig, SphericalNet, tables
+    cfg = NetConfig(hidden=8)
+    dirs, bvals, sel = tables(cfg)
+    net = SphericalNet(cfg, dirs[sel], dirs, bvals).cuda()
+    state = net.state_dict()
+    shape = (18, 21, 17)
+    subs = [volume.Subject(i, cfg, state, shape=shape, mask_voxels=2500) for i in range(2)]
+    outs, secs, vox = volume.run(subs, chunk=1000)
+    assert vox == sum(int(s.mask.sum()) for s in subs)
+    for sb, out in zip(subs, outs):
+        m = torch.from_numpy(sb.mask.reshape(-1)).cuda()
+        midx = torch.nonzero(m).flatten()
+        x = (sb.volume[:, midx].float() / sb.b0[midx]).to(torch.bfloat16)  # normalised outside the library
+        with torch.no_grad():
+            ref = sb.net(x).float()
+        got = out[:, midx].float()
+        assert torch.isfinite(got).all()
+        assert float((got - ref).norm() / ref.norm()) < 2e-2
+        assert bool((out[:, ~m] == 0).all())
