@@ -188,6 +188,25 @@ delimit_status delimit_lsc_geometry_tables(const delimit_lsc_geometry* geom, int
                                            double* M, double* q, int64_t* nb_indptr, int64_t* nb_indices,
                                            int64_t* row_index, unsigned char* window);
 
+/* Ring-tied (isotropic) kernels: one weight for the origin and one per ring,
+ * shared by the ring's points, the circularly symmetric form of the cyclic
+ * kernel (Sec. 2.3):
+ *   w[co,s,ci,s',k] = w_ring[co,s,ci,s',ring(k)],  ring(0) = 0,
+ *   ring(k) = 1 + (k - 1) / sectors for k >= 1 (kernel point order: origin, ring 1, ...).
+ * delimit_lsc_ring_expand writes the per-point weights w [c_out, S_out, c_in,
+ * S_in, K] that delimit_lsc_forward / _backward take from w_ring [c_out, S_out,
+ * c_in, S_in, rings + 1]; delimit_lsc_ring_reduce is its adjoint (dw_ring[r] =
+ * sum of dw over ring r's points, fixed order), turning the weight gradient of
+ * delimit_lsc_backward into the ring weights' gradient.  Device float32 arrays;
+ * asynchronous on `stream`.  With more sectors than the input SH order the layer
+ * then acts on each SH band l of every channel pair as the multiplier
+ * w0 + sectors * sum_r w_r P_l(cos(r alpha / rings)) followed by the output
+ * projection, independent of the tangent frames. */
+delimit_status delimit_lsc_ring_expand(const delimit_lsc_geometry* geom, const float* w_ring, float* w, int c_in,
+                                       int c_out, void* stream);
+delimit_status delimit_lsc_ring_reduce(const delimit_lsc_geometry* geom, const float* dw, float* dw_ring, int c_in,
+                                       int c_out, void* stream);
+
 /* LSC call flags.  DELIMIT_LSC_OPERATOR_READY: `workspace` already holds the
  * collapsed operator (and, for a forward, the bias vector) built by an earlier
  * forward or backward call with the same geometry, sizes, dtype, w and b; the

@@ -30,6 +30,8 @@ Readings where the paper is silent or garbled (all also used by the library):
   of the output gradient table.
 * Weights are independent per kernel point (no tying across sectors); layout
   [C_out, S_out, C_in, S_in, K]; entries outside the shell window are unused.
+  The ring-tied variant (``ring_expand``) shares one weight per ring; with more
+  sectors than the input order it acts per SH band (``ring_band_multipliers``).
 * Shell windows: 'same' (s' = s), 'adjacent' (|s - s'| <= 1), 'all'.
 * Neighbour table T3 of direction i: {j : |g_i . g_j| >= cos(alpha)} (antipodal
   aware, i itself included, ascending j, FP64 comparison, equality inside).
@@ -70,6 +72,36 @@ def kernel_points(dirs: np.ndarray, radius: float, rings: int, sectors: int) -> 
                 out[i, 1 + (r - 1) * sectors + q] = (np.cos(th) * g
                                                      + np.sin(th) * (np.cos(ph) * e1 + np.sin(ph) * e2))
     return out
+
+
+def ring_expand(w_ring: np.ndarray, rings: int, sectors: int) -> np.ndarray:
+    """Ring-tied kernel weights [.., rings + 1] (origin, then one weight per ring,
+    shared by the ring's points) as the per-point vector [.., 1 + rings * sectors]
+    in the kernel order [origin, ring 1, ring 2, ...]."""
+    w_ring = np.asarray(w_ring, np.float64)
+    assert w_ring.shape[-1] == rings + 1
+    return np.concatenate([w_ring[..., :1]] + [np.repeat(w_ring[..., r:r + 1], sectors, axis=-1)
+                                               for r in range(1, rings + 1)], axis=-1)
+
+
+def ring_reduce(dw: np.ndarray, rings: int, sectors: int) -> np.ndarray:
+    """Adjoint of ring_expand: the gradient of the ring weights (sum over each ring's points)."""
+    dw = np.asarray(dw, np.float64)
+    return np.concatenate([dw[..., :1]] + [dw[..., 1 + r * sectors:1 + (r + 1) * sectors].sum(-1, keepdims=True)
+                                           for r in range(rings)], axis=-1)
+
+
+def ring_band_multipliers(w_ring: np.ndarray, order: int, radius: float, rings: int, sectors: int) -> np.ndarray:
+    """mu[.., j] = w_0 + sectors * sum_r w_r P_l(j)(cos(r radius / rings)): by the
+    Funk-Hecke theorem, each ring's sum of the interpolant of band l around g
+    equals sectors * P_l(cos theta_r) times its value at g when sectors > l."""
+    from scipy.special import eval_legendre  # a library routine for P_l
+    w_ring = np.asarray(w_ring, np.float64)
+    lvals = np.array([l for l in range(0, order + 1, 2) for _ in range(2 * l + 1)])
+    mu = np.repeat(w_ring[..., :1], len(lvals), axis=-1).copy()
+    for r in range(1, rings + 1):
+        mu += sectors * w_ring[..., r:r + 1] * eval_legendre(lvals, np.cos(r * radius / rings))
+    return mu
 
 
 def kernel_row_index(m_per_shell, K: int):

@@ -51,6 +51,8 @@ SIGNATURES = {
     "delimit_sh_basis_shell": (C.c_int, [_vp, C.c_int, _ip, _ip, _dp]),
     "delimit_sh_basis_tables": (C.c_int, [_vp, C.c_int, _dp, _dp, _ip]),
     "delimit_signal2sh": (C.c_int, [_vp, _vp, _vp, _i64, C.c_int, _i64, _i64, C.c_int, C.c_int, _vp]),
+    "delimit_lsc_ring_expand": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
+    "delimit_lsc_ring_reduce": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "delimit_signal2sh_gather": (C.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _i64, C.c_int, C.c_int, C.c_int,
                                            _vp]),
     "delimit_sh2signal": (C.c_int, [_vp, _vp, _vp, _i64, C.c_int, _i64, _i64, C.c_int, C.c_int, _vp]),

@@ -475,6 +475,31 @@ delimit_status delimit_lsc_geometry_destroy(delimit_lsc_geometry* g) {
   return DELIMIT_OK;
 }
 
+static delimit_status ring_weights(const delimit_lsc_geometry* g, const float* src, float* dst, int c_in, int c_out,
+                                   void* stream, bool expand) {
+  if (!g) return fail(DELIMIT_ERR_INVALID_ARG, "geometry is NULL");
+  if (c_in < 1 || c_out < 1) return fail(DELIMIT_ERR_INVALID_ARG, "need c_in, c_out >= 1");
+  if (!src || !dst) return fail(DELIMIT_ERR_INVALID_ARG, "weight pointers must not be NULL");
+  if (!g->on_device) return fail(DELIMIT_ERR_INVALID_ARG, "geometry was created with DELIMIT_HOST_ONLY");
+  delimit_status st = check_device(g->device);
+  if (st != DELIMIT_OK) return st;
+  const int64_t n_e = int64_t(c_out) * g->h.s_out * c_in * g->h.s_in;
+  cudaError_t e = launch_ring_weights(src, dst, n_e, g->h.K, g->h.rings, g->h.sectors, expand,
+                                      reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "ring weight launch");
+  return DELIMIT_OK;
+}
+
+delimit_status delimit_lsc_ring_expand(const delimit_lsc_geometry* g, const float* w_ring, float* w, int c_in, int c_out,
+                                       void* stream) {
+  return ring_weights(g, w_ring, w, c_in, c_out, stream, true);
+}
+
+delimit_status delimit_lsc_ring_reduce(const delimit_lsc_geometry* g, const float* dw, float* dw_ring, int c_in,
+                                       int c_out, void* stream) {
+  return ring_weights(g, dw, dw_ring, c_in, c_out, stream, false);
+}
+
 delimit_status delimit_lsc_geometry_info(const delimit_lsc_geometry* g, int* K, int* n_in, int* n_out, int* s_in,
                                          int* s_out, int64_t* n_nb) {
   if (!g) return fail(DELIMIT_ERR_INVALID_ARG, "geometry is NULL");

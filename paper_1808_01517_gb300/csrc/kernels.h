@@ -34,6 +34,10 @@ struct TransformArgs {
   int* err = nullptr;
 };
 
+// ring-tied weights: expand [n_e][rings+1] -> [n_e][K], or the adjoint (reduce)
+cudaError_t launch_ring_weights(const float* src, float* dst, int64_t n_e, int K, int rings, int sectors, bool expand,
+                                cudaStream_t st);
+
 // dtype codes as in the C ABI: 0 = F32, 1 = BF16
 cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_out, int in_t, int out_t,
                                   cudaStream_t st);

@@ -296,6 +296,54 @@ cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_
 }
 
 // ---------------------------------------------------------------------------
+// Ring-tied kernel weights: one weight for the origin and one per ring, shared by
+// the ring's points (kernel point order: origin, ring 1 sectors, ring 2, ...).
+//   expand: w[e][k] = w_ring[e][ring(k)],  ring(0) = 0, ring(k) = 1 + (k-1)/sectors
+//   reduce: dw_ring[e][r] = sum over the ring's points of dw[e][k]  (the adjoint)
+// e runs over the n_e = c_out * S_out * c_in * S_in weight entries.
+// ---------------------------------------------------------------------------
+__global__ void ring_expand_kernel(const float* __restrict__ w_ring, float* __restrict__ w, int64_t n_e, int K,
+                                   int rings, int sectors) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_e * K) return;
+  const int64_t e = i / K;
+  const int k = (int)(i % K);
+  const int r = k == 0 ? 0 : 1 + (k - 1) / sectors;
+  w[i] = w_ring[e * (rings + 1) + r];
+}
+
+__global__ void ring_reduce_kernel(const float* __restrict__ dw, float* __restrict__ dw_ring, int64_t n_e, int K,
+                                   int rings, int sectors) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_e * (rings + 1)) return;
+  const int64_t e = i / (rings + 1);
+  const int r = (int)(i % (rings + 1));
+  const float* src = dw + e * K;
+  float acc = 0.f;
+  if (r == 0) {
+    acc = src[0];
+  } else {
+    for (int q = 0; q < sectors; ++q) acc += src[1 + (r - 1) * sectors + q];  // fixed order
+  }
+  dw_ring[i] = acc;
+}
+
+cudaError_t launch_ring_weights(const float* src, float* dst, int64_t n_e, int K, int rings, int sectors, bool expand,
+                                cudaStream_t st) {
+  TraceScope trace(expand ? "lsc_ring_expand" : "lsc_ring_reduce", st);
+  const int64_t n = n_e * (expand ? K : rings + 1);
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (expand) {
+    ring_expand_kernel<<<grid, 256, 0, st>>>(src, dst, n_e, K, rings, sectors);
+  } else {
+    ring_reduce_kernel<<<grid, 256, 0, st>>>(src, dst, n_e, K, rings, sectors);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Collapsed LSC operator.  For every shell pair (s, s') in the window
 //   W[(s,co,a)][(s',ci,b)] = sum_k w[co,s,ci,s',k] M_s[k][a][b]
 // One block: 8 channel pairs (co, ci) of one shell pair and up to 2048 (a, b)

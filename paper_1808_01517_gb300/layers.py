@@ -271,6 +271,33 @@ class SH2Signal(torch.nn.Module):
         return restore(_TransformFn.apply(x, self.basis, "sh2signal", self.channels, self.out_dtype))
 
 
+class _RingExpandFn(torch.autograd.Function):
+    """w_ring [.., rings + 1] -> per-point w [.., K] (ring-tied kernel); backward folds dw."""
+
+    @staticmethod
+    def forward(ctx, w_ring, geom, c_in, c_out):
+        ctx.geom, ctx.c_in, ctx.c_out = geom, c_in, c_out
+        w_ring = w_ring.detach().contiguous().float()
+        w = torch.empty(w_ring.shape[:-1] + (geom.K,), dtype=torch.float32, device=w_ring.device)
+        L.check(L.get().delimit_lsc_ring_expand(geom.handle, w_ring.data_ptr(), w.data_ptr(), c_in, c_out, _stream()),
+                "delimit_lsc_ring_expand")
+        return w
+
+    @staticmethod
+    def backward(ctx, dw):
+        dw = dw.contiguous().float()
+        g = ctx.geom
+        dr = torch.empty(dw.shape[:-1] + (g.rings + 1,), dtype=torch.float32, device=dw.device)
+        L.check(L.get().delimit_lsc_ring_reduce(g.handle, dw.data_ptr(), dr.data_ptr(), ctx.c_in, ctx.c_out,
+                                                 _stream()), "delimit_lsc_ring_reduce")
+        return dr, None, None, None
+
+
+def ring_expand(geom: L.LSCGeometry, w_ring: torch.Tensor, c_in: int, c_out: int) -> torch.Tensor:
+    """Per-point weights of a ring-tied kernel (differentiable)."""
+    return _RingExpandFn.apply(w_ring, geom, c_in, c_out)
+
+
 class LocalSphericalConvolution(torch.nn.Module):
     """Local spherical convolution (Sec. 2.3) with the paper's parameters.
 
@@ -278,12 +305,15 @@ class LocalSphericalConvolution(torch.nn.Module):
     rings are spread evenly out to ``angular_distance``.  ``window`` selects
     which input shells feed each output shell.  Weights: ``weight``
     [channels_out, shells_out, channels_in, shells_in, K] and ``bias``
-    [channels_out, shells_out], FP32 masters.
+    [channels_out, shells_out], FP32 masters.  ``ring_tied``: one weight for the
+    origin and one per ring ([.., rings + 1]), shared by the ring's points (the
+    isotropic kernel; frame-independent when sectors exceed the input order).
     """
 
     def __init__(self, shells_in: int, shells_out: int, sampled_gradients, sh_order_in: int, sh_order_out: int,
                  kernel_sizes, lb_lambda: float = 0.0, angular_distance: float = math.pi / 5, bvals=None,
-                 channels_in: int = 1, channels_out: int = 1, window: str | None = None, bias: bool = True):
+                 channels_in: int = 1, channels_out: int = 1, window: str | None = None, bias: bool = True,
+                 ring_tied: bool = False):
         super().__init__()
         ks = list(kernel_sizes)
         if len(set(ks)) != 1:
@@ -297,10 +327,15 @@ class LocalSphericalConvolution(torch.nn.Module):
             window = "same" if shells_in == shells_out else "all"
         self.geom = L.LSCGeometry(self.out_basis, sh_order_in, shells_in, angular_distance, len(ks), ks[0], window)
         self.c_in, self.c_out = channels_in, channels_out
-        K = self.geom.K
+        self.ring_tied = bool(ring_tied)
+        K = len(ks) + 1 if self.ring_tied else self.geom.K
         self.weight = torch.nn.Parameter(torch.zeros(channels_out, shells_out, channels_in, shells_in, K))
         self.bias = torch.nn.Parameter(torch.zeros(channels_out, shells_out)) if bias else None
 
+    def point_weights(self) -> torch.Tensor:
+        """Per-point kernel weights [.., K] (the ring weights expanded when ring-tied)."""
+        return ring_expand(self.geom, self.weight, self.c_in, self.c_out) if self.ring_tied else self.weight
+
     def forward(self, sh):
         x, restore = _to_rows(sh)
-        return restore(_LSCFn.apply(x, self.weight, self.bias, self.geom, self.c_in, self.c_out))
+        return restore(_LSCFn.apply(x, self.point_weights(), self.bias, self.geom, self.c_in, self.c_out))

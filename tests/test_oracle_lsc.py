@@ -221,3 +221,31 @@ def test_backward_matches_finite_differences_and_adjoint():
     assert abs(lin - float(np.sum(c * dc))) < 1e-10 * max(1.0, abs(lin))
     # outside-window weight gradients are exactly zero
     assert np.all(dw[:, 0, :, 2] == 0) and np.all(dw[:, 2, :, 0] == 0)
+
+
+@pytest.mark.parametrize("R,Sec,alpha,L", [(2, 9, np.deg2rad(30), 8), (4, 12, np.deg2rad(25), 8),
+                                           (1, 5, np.pi / 5, 4)])
+def test_ring_tied_kernel_is_band_scaling(R, Sec, alpha, L):
+    """Ring-tied weights (origin + one per ring) through the literal LSC equal the band
+    multipliers w0 + Sec sum_r w_r P_l(cos theta_r) at lambda = 0 when Sec > L, for
+    several channels and a random table: the layer does not see the tangent frames."""
+    ob = _single_shell(90, L, 0.0, 35)
+    lsc = olsc.LSCOracle(ob, L, 1, alpha, R, Sec)
+    w_ring = synth.gaussian((2, 1, 3, 1, R + 1), 0.2, seed=11)
+    w = olsc.ring_expand(w_ring, R, Sec)
+    assert w.shape[-1] == lsc.K
+    c = synth.gaussian((5, 3, 1, osh.n_coef(L)), 1.0, seed=12, tag="coeffs")
+    mu = olsc.ring_band_multipliers(w_ring, L, alpha, R, Sec)  # [co, s, ci, s', j]
+    ref = np.einsum("oscpj,vcpj->vosj", mu, c)
+    np.testing.assert_allclose(lsc.forward(c, w, np.zeros((2, 1))), ref, atol=1e-10)
+
+
+def test_ring_expand_reduce_adjoint():
+    w_ring = synth.gaussian((3, 2, 4, 2, 5), 1.0, seed=13)
+    dw = synth.gaussian((3, 2, 4, 2, 1 + 4 * 7), 1.0, seed=14)
+    lhs = np.sum(olsc.ring_expand(w_ring, 4, 7) * dw)
+    rhs = np.sum(w_ring * olsc.ring_reduce(dw, 4, 7))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+    # each ring's points carry the ring's weight
+    w = olsc.ring_expand(w_ring, 4, 7)
+    assert np.all(w[..., 0] == w_ring[..., 0]) and np.all(w[..., 1 + 7 * 2: 1 + 7 * 3] == w_ring[..., 3:4])
