@@ -47,6 +47,40 @@ struct TfParams {
   int* err;
 };
 
+// Tile t = (g * C + c) * M + mt walked with a stride of gridDim.x: the stride is
+// split into (dg, dc, dmt) once, so each step costs a few adds and compares
+// instead of the 64-bit divisions a fresh decode takes (per tile, on the single
+// threads that issue the copies and the MMAs).
+struct TileIter {
+  uint32_t g, c, mt, dg, dc, dmt, C, M;
+  __device__ __forceinline__ void init(uint32_t t0, uint32_t step, uint32_t C_, uint32_t M_) {
+    C = C_;
+    M = M_;
+    const uint32_t pg = C * M;
+    g = t0 / pg;
+    uint32_t r = t0 - g * pg;
+    c = r / M;
+    mt = r - c * M;
+    dg = step / pg;
+    r = step - dg * pg;
+    dc = r / M;
+    dmt = r - dc * M;
+  }
+  __device__ __forceinline__ void next() {
+    mt += dmt;
+    c += dc;
+    g += dg;
+    if (mt >= M) {
+      mt -= M;
+      ++c;
+    }
+    if (c >= C) {
+      c -= C;
+      ++g;
+    }
+  }
+};
+
 template <bool OUT_F32>
 __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_constant__ TfParams p) {
   using namespace ptx;
@@ -98,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int64_t per_group = (int64_t)p.channels * p.m_tiles;
+  const uint32_t total = (uint32_t)p.total_tiles;  // < 2^31 (checked on the host)
 
   if (warp == 0 && lane == 0) {
     // resident B images (all groups), then the A ring
@@ -112,10 +146,10 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
     uint32_t phase = 0;
     int pend[8];
     for (int s = 0; s < 8; ++s) pend[s] = -1;
-    for (int64_t t = blockIdx.x; t < p.total_tiles && !*abort_flag; t += gridDim.x) {
-      const int g = (int)(t / per_group);
-      const int64_t r = t % per_group;
-      const int c = (int)(r / p.m_tiles), mt = (int)(r % p.m_tiles);
+    TileIter ti;
+    ti.init(blockIdx.x, gridDim.x, (uint32_t)p.channels, (uint32_t)p.m_tiles);
+    for (uint32_t t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ti.next()) {
+      const int g = (int)ti.g, c = (int)ti.c, mt = (int)ti.mt;
       if (!wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, p.err, kErrEmpty)) break;
       const uint32_t dst = a_base + stage * p.stage_bytes;
       const int kp = p.g[g].kpad;
@@ -137,8 +171,10 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
     int acc = 0;
     uint32_t acc_phase = 0;
     bool bready = wait_bounded(bload_bar, 0, abort_flag, p.err, kErrFull);
-    for (int64_t t = blockIdx.x; bready && t < p.total_tiles && !*abort_flag; t += gridDim.x) {
-      const int g = (int)(t / per_group);
+    TileIter ti;
+    ti.init(blockIdx.x, gridDim.x, (uint32_t)p.channels, (uint32_t)p.m_tiles);
+    for (uint32_t t = blockIdx.x; bready && t < total && !*abort_flag; t += gridDim.x, ti.next()) {
+      const int g = (int)ti.g;
       const TfGroup& G = p.g[g];
       if (!wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.err, kErrTEmpty)) break;
       tc_fence_after();
@@ -173,10 +209,10 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
     int acc = 0;
     uint32_t acc_phase = 0;
     int it = 0;
-    for (int64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x, ++it) {
-      const int g = (int)(t / per_group);
-      const int64_t r = t % per_group;
-      const int c = (int)(r / p.m_tiles), mt = (int)(r % p.m_tiles);
+    TileIter ti;
+    ti.init(blockIdx.x, gridDim.x, (uint32_t)p.channels, (uint32_t)p.m_tiles);
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++it, ti.next()) {
+      const int g = (int)ti.g, c = (int)ti.c, mt = (int)ti.mt;
       const TfGroup& G = p.g[g];
       const int buf = it & 1;
       const uint32_t use_par = (uint32_t)((it >> 1) & 1);
@@ -447,6 +483,7 @@ cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X,
   stages = std::max(2, std::min(8, stages));
   p.stages = stages;
   p.total_tiles = (int64_t)t.n_shells * C * p.m_tiles;
+  if (p.total_tiles >= (int64_t(1) << 31)) return cudaErrorInvalidValue;  // the kernel walks tiles in 32 bits
   p.n_vox = n_vox;
   p.ldy = ldy;
   p.Y = Y;
