@@ -193,15 +193,20 @@ class LSCOracle:
         q = [P.sum(axis=1) for P in self.Pout]
         return M, q
 
+    def pair_mats(self, s: int, p: int) -> np.ndarray:
+        """The collapse matrices [K, N_out, N_in] acting on input shell p for output shell s
+        (in the resampled form they do not depend on p)."""
+        return self.collapse_mats()[0][s]
+
     def forward_collapsed(self, c_in, w, b) -> np.ndarray:
-        M, q = self.collapse_mats()
+        _, q = self.collapse_mats()
         V, Co = c_in.shape[0], w.shape[0]
         out = np.zeros((V, Co, self.s_out, self.n_out))
         for s in range(self.s_out):
             for p in range(self.s_in):
                 if not self.win[s, p]:
                     continue
-                Weff = np.einsum("ack,kxy->axcy", w[:, s, :, p, :], M[s])  # [co, a, ci, b]
+                Weff = np.einsum("ack,kxy->axcy", w[:, s, :, p, :], self.pair_mats(s, p))  # [co, a, ci, b]
                 out[:, :, s, :] += np.einsum("axcy,vcy->vax", Weff, c_in[:, :, p, :])
             out[:, :, s, :] += b[None, :, s, None] * q[s][None, None, :]
         return out
@@ -219,5 +224,107 @@ class LSCOracle:
             mask = self.win[s].astype(np.float64)
             dw[:, s] = np.einsum("vai,vcpik->acpk", dy, U, optimize=True) * mask[None, None, :, None]
             dU = np.einsum("acpk,vai->vcpik", w[:, s] * mask[None, None, :, None], dy, optimize=True)
-            dc_in += np.einsum("ikj,vcpik->vcpj", self.BK[s], dU, optimize=True)
+            dc_in += self.resample_adjoint(dU, s)
         return dc_in, dw, db
+
+    def resample_adjoint(self, dU: np.ndarray, s: int) -> np.ndarray:
+        """Adjoint of ``resample``: dc[v, ci, s', j] = sum_{i,k} B^K_s[i,k,j] dU[v,ci,s',i,k]."""
+        return np.einsum("ikj,vcpik->vcpj", self.BK[s], dU, optimize=True)
+
+
+def neighbour_bins(g_i: np.ndarray, kpts_i: np.ndarray, dirs_in: np.ndarray, radius: float):
+    """Acquired neighbours of one output direction g_i among the directions ``dirs_in`` of
+    an input shell, and the kernel point each one is binned to (resampling-free form).
+
+    Neighbour: |g_i . g_j| >= cos(radius) (antipodal aware, equality inside, ascending j).
+    The neighbour's oriented direction u = g_j, or -g_j when g_i . g_j < 0 (the signal is
+    antipodally symmetric), goes to the kernel point of g_i nearest to it on the sphere:
+    the largest p_{i,k} . u, the lowest k on ties.  Returns (indices, bins), int64."""
+    c = np.cos(radius)
+    idx, bins = [], []
+    for j in range(dirs_in.shape[0]):
+        d = float(np.dot(g_i, dirs_in[j]))
+        if abs(d) >= c:
+            u = dirs_in[j] if d >= 0.0 else -dirs_in[j]
+            idx.append(j)
+            bins.append(int(np.argmax(kpts_i @ u)))  # argmax returns the first maximum
+    return np.array(idx, np.int64), np.array(bins, np.int64)
+
+
+class LSCNeighbourOracle(LSCOracle):
+    """The LSC without resampling (the alternative Sec. 2.3 argues against): the kernel
+    acts on the *acquired* neighbours of every direction instead of on interpolated
+    kernel points.
+
+    Readings (the paper describes this alternative only by what it lacks):
+
+    * Input shell s' is sampled on the gradient table's shell-s' directions (the
+      output basis' table), so it needs as many input as output shells; its values
+      there are the input SH of order ``order_in`` evaluated at those directions.
+    * Each acquired neighbour j of output direction i (shell s) in input shell s'
+      (``neighbour_bins``) is assigned to the nearest kernel point of i; a kernel
+      point takes the mean of the values assigned to it, 0 when none is.  The
+      resulting m x (n + 1) neighbourhood matrix then meets the kernel exactly as in
+      the resampled form (point-wise product, sum, bias, projection onto SH).
+
+    Linearity again collapses the layer: M_{s,s',k} = P_out,s A^{s,s'}_k B_in,s', with
+    A^{s,s'}_k[i, j] = 1 / (number of neighbours in bin (i, k)) for j in that bin."""
+
+    def __init__(self, out_basis: SHBasisOracle, order_in: int, shells_in: int, radius: float,
+                 rings: int, sectors: int, window: str = "same"):
+        super().__init__(out_basis, order_in, shells_in, radius, rings, sectors, window)
+        if shells_in != self.s_out:
+            raise ValueError("the resampling-free LSC samples input shell s' on the table's shell s'")
+        # input basis of order_in at every acquired direction of every shell
+        self.B_in = [real_sh(order_in, d) for d in self.dirs]
+        # neighbour tables per (output shell s, input shell s'): CSR + bin of each entry
+        self.nb = {}
+        self.A = {}
+        for s in range(self.s_out):
+            for p in range(self.s_in):
+                m_o, m_i = self.dirs[s].shape[0], self.dirs[p].shape[0]
+                indptr, indices, bins = [0], [], []
+                A = np.zeros((m_o, self.K, m_i))
+                for i in range(m_o):
+                    ix, bx = neighbour_bins(self.dirs[s][i], self.kpts[s][i], self.dirs[p], self.radius)
+                    indices.extend(ix.tolist())
+                    bins.extend(bx.tolist())
+                    indptr.append(len(indices))
+                    for k in range(self.K):
+                        sel = ix[bx == k]
+                        if sel.size:
+                            A[i, k, sel] = 1.0 / sel.size
+                self.nb[s, p] = (np.array(indptr, np.int64), np.array(indices, np.int64),
+                                 np.array(bins, np.int64))
+                self.A[s, p] = A
+
+    def acquired(self, c_in: np.ndarray, p: int) -> np.ndarray:
+        """x[v, ci, j]: input shell p's SH evaluated at that shell's acquired directions."""
+        return c_in[:, :, p, :] @ self.B_in[p].T
+
+    def resample(self, c_in: np.ndarray, s: int) -> np.ndarray:
+        """U[v, ci, s', i, k]: mean of input shell s' over the neighbours of output
+        direction i binned to kernel point k (0 for an empty bin)."""
+        V, Ci = c_in.shape[0], c_in.shape[1]
+        m = self.dirs[s].shape[0]
+        U = np.zeros((V, Ci, self.s_in, m, self.K))
+        for p in range(self.s_in):
+            U[:, :, p] = np.einsum("ikj,vcj->vcik", self.A[s, p], self.acquired(c_in, p), optimize=True)
+        return U
+
+    def resample_adjoint(self, dU: np.ndarray, s: int) -> np.ndarray:
+        out = np.zeros(dU.shape[:3] + (self.n_in,))
+        for p in range(self.s_in):
+            dx = np.einsum("ikj,vcik->vcj", self.A[s, p], dU[:, :, p], optimize=True)  # [v, ci, j]
+            out[:, :, p, :] = dx @ self.B_in[p]
+        return out
+
+    def collapse_mats(self):
+        """M[s][s'] = P_out,s A^{s,s'}_k B_in,s' ([K, N_out, N_in]) and q[s] = P_out,s 1."""
+        M = [[np.einsum("ai,ikj,jb->kab", self.Pout[s], self.A[s, p], self.B_in[p], optimize=True)
+              for p in range(self.s_in)] for s in range(self.s_out)]
+        q = [P.sum(axis=1) for P in self.Pout]
+        return M, q
+
+    def pair_mats(self, s: int, p: int) -> np.ndarray:
+        return np.einsum("ai,ikj,jb->kab", self.Pout[s], self.A[s, p], self.B_in[p], optimize=True)
