@@ -31,16 +31,16 @@ METRIC = "voxels/s, Signal2SH->LSC->SH2Signal fwd+bwd, BF16 vs FP32 at stated er
 UNIT = "voxels/s"
 
 # DRAM traffic (read + write) of one launch at the 65,536-voxel workload, from the
-# single-pass ncu capture summarised in profiles/lsc_kernels_16384vox_ncu.md (the
-# `dram__bytes_*` metrics, the bench command itself); valid only while the kernel's
-# sources hash to the value recorded with the capture.
+# single-pass ncu capture of the bench command summarised in
+# profiles/chain_65536vox_launch_list.md (the `dram__bytes_*` metrics); valid only
+# while the kernel's sources hash to the value recorded with the capture.
 _GEMM = ("csrc/tc_gemm.cu", "csrc/tc_ptx.cuh"), "3054bf3a20325923"
-_TF = ("csrc/tc_transform.cu", "csrc/tc_ptx.cuh"), "13967c03ccaf50b5"
+_TF = ("csrc/tc_transform.cu", "csrc/tc_ptx.cuh"), "baa7f0e78928ced7"
 NCU_TRAFFIC = {
-    "lsc_fwd_gemm": {"bytes": 1.600e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
-    "lsc_dgrad_gemm": {"bytes": 2.359e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
-    "lsc_wgrad_gemm": {"bytes": 4.069e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
-    "signal2sh_tc": {"bytes": 0.8136e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
+    "lsc_fwd_gemm": {"bytes": 1.631e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "lsc_dgrad_gemm": {"bytes": 2.344e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "lsc_wgrad_gemm": {"bytes": 3.377e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "signal2sh_tc": {"bytes": 0.8132e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
     "sh2signal_tc": {"bytes": 3.333e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
     "sh2signal_bwd_tc": {"bytes": 3.358e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
     "signal2sh_bwd_tc": {"bytes": 0.7845e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
@@ -99,8 +99,9 @@ class OracleChain:
         self.cfg = cfg
         self.ob = osh.SHBasisOracle(dirs, bvals, cfg.order, cfg.lam)
         self.ob_in = self.ob if cfg.l_in == cfg.order else osh.SHBasisOracle(dirs, bvals, cfg.l_in, cfg.lam)
-        self.og = olsc.LSCOracle(self.ob, cfg.l_in, self.ob.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings,
-                                 cfg.sectors, cfg.window)
+        cls = olsc.LSCOracle if cfg.resample else olsc.LSCNeighbourOracle
+        self.og = cls(self.ob, cfg.l_in, self.ob.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings, cfg.sectors,
+                      cfg.window)
 
     def step(self, sig, w, b, ds_out):
         """sig [V, Ci, dirs], ds_out [V, Co, dirs] -> (s_out, ds_in, dw, db)."""
@@ -427,6 +428,7 @@ def main():
         # ---- mixed SH orders (4 -> 8) with every input shell mixed into every output shell ----
         from dataclasses import replace
         extras["mixed_orders_all_shells"] = run_chain_leg(replace(cfg, order_in=4, window="all"), dirs, bvals)
+        extras["resampling_free"] = run_chain_leg(replace(cfg, resample=False), dirs, bvals)
         # ---- stand-alone transforms at 1,048,576 voxels (FP32 and BF16-in / FP32-out) ----
         extras["transforms"] = run_transforms(cfg, dirs, bvals, args.transform_vox, hbm)
         # ---- oracle on the host cores ----
@@ -449,6 +451,7 @@ def main():
         line["err_vs_oracle_bf16"] = extras.get("err_vs_oracle_bf16")
         line["transforms"] = extras.get("transforms")
         line["mixed_orders_all_shells"] = extras.get("mixed_orders_all_shells")
+        line["resampling_free"] = extras.get("resampling_free")
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

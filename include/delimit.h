@@ -71,6 +71,10 @@ typedef enum {
                                 Sec. 2.2 takes only sh_order and gradients. */
 
 /* LSC shell windows (which input shells s' feed output shell s) */
+/* Geometry flag: the LSC without resampling (the alternative that Sec. 2.3 argues
+ * against), see delimit_lsc_geometry_create. */
+#define DELIMIT_LSC_NEIGHBOURS 4u
+
 #define DELIMIT_WINDOW_SAME 0      /* s' = s (needs as many input as output shells) */
 #define DELIMIT_WINDOW_ADJACENT 1  /* |s - s'| <= 1 (same) */
 #define DELIMIT_WINDOW_ALL (-1)    /* every input shell: the paper's shells-as-channels form */
@@ -164,8 +168,20 @@ delimit_status delimit_sh2signal_backward(const delimit_sh_basis* basis, const v
  * ties), e2 = g x e1.  Built in FP64: kernel points, the input basis at every
  * kernel point, M_{s,k} = P_out,s B^K_{s,k} (N_out x N_in), q_s = P_out,s 1,
  * the window table and the neighbour table {j : |g_i.g_j| >= cos(radius)}.
+ *
+ * flags: DELIMIT_HOST_ONLY (host tables only), DELIMIT_LSC_NEIGHBOURS (the
+ * resampling-free form): input shell s' is sampled on out_basis' shell-s'
+ * directions (shells_in must equal its shell count); each acquired neighbour j
+ * of output direction i in shell s' (|g_i.g_j| >= cos(radius)), oriented onto
+ * g_i's hemisphere, is binned to the kernel point of i nearest to it (largest
+ * dot product, lowest k on ties); a kernel point takes the mean of its
+ * neighbours' values (0 when it has none) and meets the kernel weights as in the
+ * resampled form.  The collapse is then per shell pair,
+ * M_{s,s',k} = P_out,s A^{s,s'}_k B_in,s' (A_k the bin means), and the forward,
+ * backward and workspace calls are unchanged.
  * Errors: INVALID_ARG (radius outside (0, pi/2], rings/sectors < 1, window not
- * matching the shell counts, bad order), OOM/CUDA on upload. */
+ * matching the shell counts, bad order, unknown flags, resampling-free tables
+ * over 256 MiB), OOM/CUDA on upload. */
 delimit_status delimit_lsc_geometry_create(const delimit_sh_basis* out_basis, int order_in, int shells_in,
                                            double radius, int rings, int sectors, int window,
                                            unsigned flags, delimit_lsc_geometry** out);
@@ -179,7 +195,8 @@ delimit_status delimit_lsc_geometry_info(const delimit_lsc_geometry* geom, int* 
 
 /* Host copies of output shell s's tables; NULL skips an output.
  *   kpts       m_s x K x 3 doubles (kernel points)
- *   M          K x N_out x N_in doubles (M_{s,k})
+ *   M          K x N_out x N_in doubles (M_{s,k}); resampling-free geometries:
+ *              shells_in x K x N_out x N_in (M_{s,s',k})
  *   q          N_out doubles
  *   nb_indptr  m_s + 1 int64, nb_indices nb_indptr[m_s] int64 (ascending)
  *   row_index  m_s x K int64: row (dir_off[s] + i) * K + k of kernel point (i, k)
@@ -187,6 +204,15 @@ delimit_status delimit_lsc_geometry_info(const delimit_lsc_geometry* geom, int* 
 delimit_status delimit_lsc_geometry_tables(const delimit_lsc_geometry* geom, int shell, double* kpts,
                                            double* M, double* q, int64_t* nb_indptr, int64_t* nb_indices,
                                            int64_t* row_index, unsigned char* window);
+
+/* Resampling-free geometries only: the acquired neighbours of every direction of
+ * output shell `shell` among the directions of input shell `shell_in` (host
+ * arrays; NULL skips one): indptr m_s + 1 int64, indices indptr[m_s] int64
+ * (ascending within a direction), bins indptr[m_s] int32, the kernel point
+ * 0..K-1 each neighbour is binned to.  INVALID_ARG for another geometry or a
+ * shell out of range. */
+delimit_status delimit_lsc_neighbour_table(const delimit_lsc_geometry* geom, int shell, int shell_in,
+                                           int64_t* indptr, int64_t* indices, int32_t* bins);
 
 /* Ring-tied (isotropic) kernels: one weight for the origin and one per ring,
  * shared by the ring's points, the circularly symmetric form of the cyclic

@@ -33,6 +33,7 @@ F32 = 0
 BF16 = 1
 OPERATOR_READY = 1
 HOST_ONLY = 1
+LSC_NEIGHBOURS = 4
 EVAL_ONLY = 2
 WINDOW_SAME, WINDOW_ADJACENT, WINDOW_ALL = 0, 1, -1
 WINDOWS = {"same": WINDOW_SAME, "adjacent": WINDOW_ADJACENT, "all": WINDOW_ALL}
@@ -63,6 +64,7 @@ SIGNATURES = {
     "delimit_lsc_geometry_destroy": (C.c_int, [_vp]),
     "delimit_lsc_geometry_info": (C.c_int, [_vp, _ip, _ip, _ip, _ip, _ip, _i64p]),
     "delimit_lsc_geometry_tables": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _i64p, _i64p, _i64p, C.POINTER(C.c_ubyte)]),
+    "delimit_lsc_neighbour_table": (C.c_int, [_vp, C.c_int, C.c_int, _i64p, _i64p, C.POINTER(C.c_int32)]),
     "delimit_lsc_workspace_size": (C.c_size_t, [_vp, _i64, C.c_int, C.c_int, C.c_int, C.c_int]),
     "delimit_lsc_forward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64, C.c_int, C.c_uint,
                                       _vp, C.c_size_t, _vp]),
@@ -168,14 +170,16 @@ class LSCGeometry:
     """Handle of ``delimit_lsc_geometry`` (kernel points, collapse matrices, tables)."""
 
     def __init__(self, out_basis: SHBasis, order_in: int, shells_in: int, radius: float, rings: int, sectors: int,
-                 window="same", host_only: bool = False):
+                 window="same", host_only: bool = False, neighbours: bool = False):
         lib = get()
         self.out_basis = out_basis  # keep alive
         win = WINDOWS[window] if isinstance(window, str) else int(window)
         h = _vp()
+        flags = (HOST_ONLY if host_only else 0) | (LSC_NEIGHBOURS if neighbours else 0)
         check(lib.delimit_lsc_geometry_create(out_basis.handle, int(order_in), int(shells_in), float(radius),
-                                              int(rings), int(sectors), win, HOST_ONLY if host_only else 0,
-                                              C.byref(h)), "delimit_lsc_geometry_create")
+                                              int(rings), int(sectors), win, flags, C.byref(h)),
+              "delimit_lsc_geometry_create")
+        self.neighbours = bool(neighbours)
         self.handle = h
         K, ni, no, si, so, nn = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int64()
         check(lib.delimit_lsc_geometry_info(h, C.byref(K), C.byref(ni), C.byref(no), C.byref(si), C.byref(so),
@@ -188,7 +192,7 @@ class LSCGeometry:
         ob = self.out_basis
         m = ob.m[s]
         kp = np.empty((m, self.K, 3))
-        M = np.empty((self.K, self.n_out, self.n_in))
+        M = np.empty(((self.s_in,) if self.neighbours else ()) + (self.K, self.n_out, self.n_in))
         q = np.empty(self.n_out)
         ip = np.empty(m + 1, np.int64)
         lib = get()
@@ -203,6 +207,18 @@ class LSCGeometry:
               "delimit_lsc_geometry_tables")
         return {"kpts": kp, "M": M, "q": q, "nb_indptr": ip, "nb_indices": ix[:ip[-1]], "row_index": ri,
                 "window": win.astype(bool)}
+
+    def neighbour_table(self, s: int, s_in: int):
+        """(indptr, indices, bins) of the resampling-free form for shell pair (s, s_in)."""
+        lib = get()
+        ip = np.empty(self.out_basis.m[s] + 1, np.int64)
+        check(lib.delimit_lsc_neighbour_table(self.handle, s, s_in, ip.ctypes.data_as(_i64p), None, None),
+              "delimit_lsc_neighbour_table")
+        ix = np.empty(max(1, ip[-1]), np.int64)
+        bx = np.empty(max(1, ip[-1]), np.int32)
+        check(lib.delimit_lsc_neighbour_table(self.handle, s, s_in, ip.ctypes.data_as(_i64p), ix.ctypes.data_as(_i64p),
+                                              bx.ctypes.data_as(C.POINTER(C.c_int32))), "delimit_lsc_neighbour_table")
+        return ip, ix[:ip[-1]], bx[:ip[-1]]
 
     def workspace_size(self, n_vox: int, c_in: int, c_out: int, dtype: int, backward: bool) -> int:
         return int(get().delimit_lsc_workspace_size(self.handle, int(n_vox), int(c_in), int(c_out), int(dtype),

@@ -33,6 +33,7 @@ class ChainConfig:
     window: str = "adjacent"
     seed: int = 1808
     order_in: int | None = None  # SH order of the LSC input (Signal2SH); None = order
+    resample: bool = True  # False: the LSC over acquired neighbours (no SH resampling)
 
     @property
     def l_in(self) -> int:
@@ -42,7 +43,7 @@ class ChainConfig:
         orders = f"L={self.order}" if self.l_in == self.order else f"L={self.l_in}->{self.order}"
         return (f"S2SH-LSC-SH2S fwd+bwd V={self.n_vox} {len(self.dirs_per_shell)}x{self.dirs_per_shell[0]} dirs "
                 f"{orders} {self.c_in}->{self.c_out} ch {self.window} {self.radius_deg:g}deg "
-                f"{self.rings}x{self.sectors}")
+                f"{self.rings}x{self.sectors}" + ("" if self.resample else " resampling-free"))
 
 
 class Chain:
@@ -56,7 +57,7 @@ class Chain:
         self.basis = L.SHBasis(dirs, bvals, cfg.order, cfg.lam)  # output side (LSC projection, SH2Signal)
         self.basis_in = self.basis if cfg.l_in == cfg.order else L.SHBasis(dirs, bvals, cfg.l_in, cfg.lam)
         self.geom = L.LSCGeometry(self.basis, cfg.l_in, self.basis.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings,
-                                  cfg.sectors, cfg.window)
+                                  cfg.sectors, cfg.window, neighbours=not cfg.resample)
         V, S, nd = cfg.n_vox, self.basis.n_shells, self.basis.n_dirs
         N, N_in = self.basis.n_coef, self.basis_in.n_coef
         ci, co = cfg.c_in, cfg.c_out

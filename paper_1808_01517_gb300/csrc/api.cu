@@ -92,7 +92,7 @@ struct delimit_lsc_geometry {
   bool on_device = false;
   int device = -1;
   float* d_mem = nullptr;
-  const float* d_M = nullptr;  // [S_out][K][N_out][N_in]
+  const float* d_M = nullptr;  // [S_out][K][N_out][N_in]; resampling-free form [S_out][S_in][K][N_out][N_in]
   const float* d_q = nullptr;  // [S_out][N_out]
   int* err_word = nullptr;
   LscDims dims_template;  // without channel counts
@@ -390,7 +390,12 @@ delimit_status delimit_lsc_geometry_create(const delimit_sh_basis* ob, int order
   delimit_lsc_geometry* g = new (std::nothrow) delimit_lsc_geometry();
   if (!g) return fail(DELIMIT_ERR_OOM, "host allocation failed");
   std::string err;
-  if (build_lsc(ob->h, order_in, shells_in, radius, rings, sectors, window, g->h, err)) {
+  if (flags & ~(DELIMIT_HOST_ONLY | DELIMIT_LSC_NEIGHBOURS)) {
+    delete g;
+    return fail(DELIMIT_ERR_INVALID_ARG, "unknown geometry flags");
+  }
+  if (build_lsc(ob->h, order_in, shells_in, radius, rings, sectors, window, (flags & DELIMIT_LSC_NEIGHBOURS) != 0,
+                g->h, err)) {
     delete g;
     return fail(DELIMIT_ERR_INVALID_ARG, err);
   }
@@ -406,6 +411,10 @@ delimit_status delimit_lsc_geometry_create(const delimit_sh_basis* ob, int order
   d.n_in = g->h.n_in;
   d.n_out = g->h.n_out;
   d.K = g->h.K;
+  // collapse matrices of shell pair (s, s') start at s * m_stride_s + s' * m_stride_sp
+  const int64_t nkab = int64_t(d.K) * d.n_out * d.n_in;
+  d.m_stride_s = g->h.neighbours ? nkab * d.s_in : nkab;
+  d.m_stride_sp = g->h.neighbours ? nkab : 0;
   for (int s = 0; s < d.s_out; ++s) {
     int lo = -1, hi = -1;
     for (int p = 0; p < d.s_in; ++p)
@@ -522,7 +531,7 @@ delimit_status delimit_lsc_geometry_tables(const delimit_lsc_geometry* g, int sh
   if (!g || shell < 0 || shell >= g->h.s_out) return fail(DELIMIT_ERR_INVALID_ARG, "bad geometry or shell");
   const LscShellHost& s = g->h.shells[shell];
   if (kpts) std::memcpy(kpts, s.kpts.data(), s.kpts.size() * sizeof(double));
-  if (M) std::memcpy(M, s.M.data(), s.M.size() * sizeof(double));
+  if (M) std::memcpy(M, s.M.data(), s.M.size() * sizeof(double));  // [S_in] x K x N_out x N_in when resampling-free
   if (q) std::memcpy(q, s.q.data(), s.q.size() * sizeof(double));
   for (size_t i = 0; nb_indptr && i < s.nb_indptr.size(); ++i) nb_indptr[i] = s.nb_indptr[i];
   for (size_t i = 0; nb_indices && i < s.nb_indices.size(); ++i) nb_indices[i] = s.nb_indices[i];
@@ -532,6 +541,21 @@ delimit_status delimit_lsc_geometry_tables(const delimit_lsc_geometry* g, int sh
       for (int k = 0; k < g->h.K; ++k) row_index[size_t(i) * g->h.K + k] = int64_t(bs.dir_off + i) * g->h.K + k;
   }
   if (window) std::memcpy(window, s.window.data(), s.window.size());
+  return DELIMIT_OK;
+}
+
+delimit_status delimit_lsc_neighbour_table(const delimit_lsc_geometry* g, int shell, int shell_in, int64_t* indptr,
+                                           int64_t* indices, int32_t* bins) {
+  if (!g || shell < 0 || shell >= g->h.s_out || shell_in < 0 || shell_in >= g->h.s_in)
+    return fail(DELIMIT_ERR_INVALID_ARG, "bad geometry or shell");
+  if (!g->h.neighbours) return fail(DELIMIT_ERR_INVALID_ARG, "geometry was not created with DELIMIT_LSC_NEIGHBOURS");
+  const LscShellHost& s = g->h.shells[shell];
+  const auto& ip = s.pair_indptr[shell_in];
+  const auto& ix = s.pair_indices[shell_in];
+  const auto& bx = s.pair_bins[shell_in];
+  for (size_t i = 0; indptr && i < ip.size(); ++i) indptr[i] = ip[i];
+  for (size_t i = 0; indices && i < ix.size(); ++i) indices[i] = ix[i];
+  for (size_t i = 0; bins && i < bx.size(); ++i) bins[i] = bx[i];
   return DELIMIT_OK;
 }
 

@@ -184,8 +184,68 @@ int build_basis(const double* dirs, const double* bvals, int n, int order, doubl
   return 0;
 }
 
+// Resampling-free form for output shell s (tables already hold its kernel points):
+// for every input shell s', the acquired neighbours j of each direction i
+// (|g_i.g_j| >= cos(radius), ascending j), each oriented onto g_i's hemisphere and
+// binned to the kernel point with the largest p_{i,k}.u (lowest k on ties); then
+//   M_{s,s',k}[a][b] = sum_i P_out[a][i] * mean_{j in bin (i,k)} Y_b(g_j).
+static void build_neighbour_form(const BasisHost& ob, int s, int order_in, int n_in, double cos_r, LscShellHost& L) {
+  const ShellHost& sh = ob.shells[s];
+  const int S = int(ob.shells.size()), m = sh.m, No = ob.N;
+  const int K = int(L.kpts.size() / (size_t(m) * 3));
+  L.M.assign(size_t(S) * K * No * n_in, 0.0);
+  L.pair_indptr.assign(S, {});
+  L.pair_indices.assign(S, {});
+  L.pair_bins.assign(S, {});
+  std::vector<double> mean(size_t(K) * n_in), y(n_in);
+  std::vector<int> count(K);
+  for (int p = 0; p < S; ++p) {
+    const ShellHost& sp = ob.shells[p];
+    auto& indptr = L.pair_indptr[p];
+    auto& indices = L.pair_indices[p];
+    auto& bins = L.pair_bins[p];
+    indptr.assign(1, 0);
+    double* Mp = &L.M[size_t(p) * K * No * n_in];
+    for (int i = 0; i < m; ++i) {
+      const double* gi = &sh.dirs[3 * i];
+      const double* kp = &L.kpts[size_t(i) * K * 3];
+      std::fill(mean.begin(), mean.end(), 0.0);
+      std::fill(count.begin(), count.end(), 0);
+      for (int j = 0; j < sp.m; ++j) {
+        const double* gj = &sp.dirs[3 * j];
+        const double d = gi[0] * gj[0] + gi[1] * gj[1] + gi[2] * gj[2];
+        if (!(std::fabs(d) >= cos_r)) continue;
+        const double sg = d >= 0.0 ? 1.0 : -1.0;
+        const double u[3] = {sg * gj[0], sg * gj[1], sg * gj[2]};
+        int best = 0;
+        double best_c = kp[0] * u[0] + kp[1] * u[1] + kp[2] * u[2];
+        for (int k = 1; k < K; ++k) {
+          const double c = kp[3 * k] * u[0] + kp[3 * k + 1] * u[1] + kp[3 * k + 2] * u[2];
+          if (c > best_c) best_c = c, best = k;
+        }
+        indices.push_back(j);
+        bins.push_back(best);
+        sh_eval(order_in, gj, y.data());  // even order: Y(-g) = Y(g)
+        for (int b = 0; b < n_in; ++b) mean[size_t(best) * n_in + b] += y[b];
+        ++count[best];
+      }
+      indptr.push_back((long long)indices.size());
+      for (int k = 0; k < K; ++k) {
+        if (!count[k]) continue;
+        const double inv = 1.0 / count[k];
+        const double* mk = &mean[size_t(k) * n_in];
+        for (int a = 0; a < No; ++a) {
+          const double pa = sh.P[size_t(a) * m + i] * inv;
+          double* row = &Mp[(size_t(k) * No + a) * n_in];
+          for (int b = 0; b < n_in; ++b) row[b] += pa * mk[b];
+        }
+      }
+    }
+  }
+}
+
 int build_lsc(const BasisHost& ob, int order_in, int shells_in, double radius, int rings, int sectors, int window,
-              LscHost& out, std::string& err) {
+              bool neighbours, LscHost& out, std::string& err) {
   const int n_in = sh_ncoef(order_in);
   if (n_in < 0 || order_in > 16) {
     err = "order_in must be even and in [0, 16]";
@@ -208,7 +268,16 @@ int build_lsc(const BasisHost& ob, int order_in, int shells_in, double radius, i
     err = "same/adjacent windows need shells_in equal to the output basis' shell count";
     return 1;
   }
+  if (neighbours && shells_in != s_out) {
+    err = "the resampling-free LSC samples input shell s' on the table's shell s': shells_in must equal its shell count";
+    return 1;
+  }
+  if (neighbours && double(s_out) * s_out * (1 + rings * sectors) * ob.N * n_in * 8.0 > double(1 << 28)) {
+    err = "resampling-free LSC: the per-shell-pair collapse matrices would exceed 256 MiB";
+    return 1;
+  }
   out = LscHost();
+  out.neighbours = neighbours;
   out.order_in = order_in;
   out.n_in = n_in;
   out.n_out = ob.N;
@@ -257,7 +326,7 @@ int build_lsc(const BasisHost& ob, int order_in, int shells_in, double radius, i
     }
     // M_{s,k}[a][b] = sum_i P_out[a][i] * BK[i][k][b]
     L.M.assign(size_t(K) * No * n_in, 0.0);
-    for (int k = 0; k < K; ++k)
+    for (int k = 0; !neighbours && k < K; ++k)
       for (int a = 0; a < No; ++a) {
         double* row = &L.M[(size_t(k) * No + a) * n_in];
         for (int i = 0; i < m; ++i) {
@@ -284,6 +353,7 @@ int build_lsc(const BasisHost& ob, int order_in, int shells_in, double radius, i
     L.window.assign(shells_in, 0);
     for (int p = 0; p < shells_in; ++p)
       L.window[p] = (window == -1) ? 1 : (window == 0 ? (p == s) : (std::abs(p - s) <= 1));
+    if (neighbours) build_neighbour_form(ob, s, order_in, n_in, cos_r, L);
     out.shells.push_back(std::move(L));
   }
   return 0;

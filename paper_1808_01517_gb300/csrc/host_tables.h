@@ -35,19 +35,29 @@ int build_basis(const double* dirs, const double* bvals, int n, int order, doubl
 
 struct LscShellHost {
   std::vector<double> kpts;       // m x K x 3
-  std::vector<double> M;          // K x Nout x Nin
+  std::vector<double> M;          // K x Nout x Nin; resampling-free form: S_in x K x Nout x Nin
   std::vector<double> q;          // Nout
   std::vector<long long> nb_indptr, nb_indices;  // neighbour CSR
   std::vector<unsigned char> window;             // S_in
+  // resampling-free form, per input shell s': acquired neighbours of every direction
+  // of this shell among shell s' (CSR, ascending) and the kernel point of each
+  std::vector<std::vector<long long>> pair_indptr, pair_indices;
+  std::vector<std::vector<int>> pair_bins;
 };
 
 struct LscHost {
   int order_in = 0, n_in = 0, n_out = 0, s_in = 0, s_out = 0, K = 0, rings = 0, sectors = 0, window = 0;
   double radius = 0;
+  bool neighbours = false;  // resampling-free form (acquired neighbours binned to kernel points)
   std::vector<LscShellHost> shells;
 };
 
+// neighbours = false: the resampled LSC of Sec. 2.3, M_{s,k} = P_out,s B^K_{s,k}.
+// neighbours = true: the resampling-free form over acquired neighbours, input shell s'
+// sampled on the table's shell s' (shells_in must equal the table's shell count),
+// M_{s,s',k} = P_out,s A^{s,s'}_k B_in,s' with A_k the mean over the neighbours binned
+// to kernel point k.
 int build_lsc(const BasisHost& out_basis, int order_in, int shells_in, double radius, int rings, int sectors,
-              int window, LscHost& out, std::string& err);
+              int window, bool neighbours, LscHost& out, std::string& err);
 
 }  // namespace delimit

@@ -55,11 +55,12 @@ struct LscDims {
   //   W [rows_out][ldW],  W[(s,co,a)][s'*in_blk + ci*n_in + b]
   //   Wt[rows_in][ldWt], Wt[(s',ci,b)][s*out_blk + co*n_out + a]
   int64_t in_blk, out_blk, ldW, ldWt;
+  int64_t m_stride_s, m_stride_sp;  // M of shell pair (s, s'): M + s * m_stride_s + s' * m_stride_sp ([K][N_out][N_in])
   int win_lo[kMaxGroups], win_hi[kMaxGroups];      // input shells [lo, hi) feeding output shell s
   int rwin_lo[kMaxGroups], rwin_hi[kMaxGroups];    // output shells [lo, hi) fed by input shell s'
 };
 
-// W[(s,co,a),(s',ci,b)] = sum_k w[co,s,ci,s',k] M[s][k][a][b] (0 outside the window and in
+// W[(s,co,a),(s',ci,b)] = sum_k w[co,s,ci,s',k] M_{s,s'}[k][a][b] (0 outside the window and in
 // the padding), Wt = W^T (padded layouts above), bias_vec[(s,co,a)] = b[co,s] q[s][a] (0 when b == NULL).
 cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, const float* M, const float* q,
                            void* W, void* Wt, float* bias_vec, int w_t, cudaStream_t st);

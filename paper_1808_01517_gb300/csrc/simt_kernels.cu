@@ -345,9 +345,9 @@ cudaError_t launch_ring_weights(const float* src, float* dst, int64_t n_e, int K
 
 // ---------------------------------------------------------------------------
 // Collapsed LSC operator.  For every shell pair (s, s') in the window
-//   W[(s,co,a)][(s',ci,b)] = sum_k w[co,s,ci,s',k] M_s[k][a][b]
+//   W[(s,co,a)][(s',ci,b)] = sum_k w[co,s,ci,s',k] M_{s,s'}[k][a][b] (M_{s,s'} = M_s in the resampled form)
 // One block: 8 channel pairs (co, ci) of one shell pair and up to 2048 (a, b)
-// entries.  Chunks of 8 kernel points of M_s (8 x 2048 floats) and of w are
+// entries.  Chunks of 8 kernel points of M_{s,s'} (8 x 2048 floats) and of w are
 // staged in shared memory with coalesced loads; each thread then accumulates
 // 8 pairs x 8 consecutive (a, b) entries (64 FMAs per 4 vector shared loads).
 // The finished block goes back through shared memory and is written to W
@@ -378,11 +378,11 @@ __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ Ls
 #pragma unroll
     for (int e = 0; e < 8; ++e) acc[p][e] = 0.f;
   if (in_win) {
-    const float* Ms = M + (int64_t)s * d.K * nab + ab0 + tid;
+    const float* Ms = M + s * d.m_stride_s + sp * d.m_stride_sp + ab0 + tid;
     for (int k0 = 0; k0 < d.K; k0 += kBwKC) {
       const int nk = min(kBwKC, d.K - k0);
       __syncthreads();
-      // stage M_s[k0 .. k0+7][ab0 .. ab0+2047]: element tid + 256 e of each row (zero past the range)
+      // stage M_{s,s'}[k0 .. k0+7][ab0 .. ab0+2047]: element tid + 256 e of each row (zero past the range)
       for (int kk = 0; kk < kBwKC; ++kk) {
         const float* row = Ms + (int64_t)(k0 + kk) * nab;
         float* dst = blk + kk * kBwChunk + tid;
@@ -668,7 +668,7 @@ cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int m
 
 // ---------------------------------------------------------------------------
 // dW -> dw (kernel-point weights) and db.  For a windowed shell pair,
-//   dw[co,s,ci,s',k] = sum_{a,b} M_s[k][a][b] G[(s,co,a)][(s',ci,b)],  G = sum_split P;
+//   dw[co,s,ci,s',k] = sum_{a,b} M_{s,s'}[k][a][b] G[(s,co,a)][(s',ci,b)],  G = sum_split P;
 // a block owns 32 channel pairs x all K and walks (a,b) in chunks of 128.
 // ---------------------------------------------------------------------------
 constexpr int kDwAbPart = 256;  // (a,b) entries per partial sum
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ 
       }
       for (int idx = threadIdx.x; idx < KT * AB; idx += 256) {
         const int t = idx % AB, kk = idx / AB, ab = ab0 + t, k = k0 + kk;
-        ms_[t][kk] = (ab < ab_end && k < d.K) ? M[((int64_t)s * d.K + k) * nab + ab] : 0.f;
+        ms_[t][kk] = (ab < ab_end && k < d.K) ? M[s * d.m_stride_s + sp * d.m_stride_sp + (int64_t)k * nab + ab] : 0.f;
       }
       __syncthreads();
       const int nt = min(AB, ab_end - ab0);

@@ -308,12 +308,16 @@ class LocalSphericalConvolution(torch.nn.Module):
     [channels_out, shells_out], FP32 masters.  ``ring_tied``: one weight for the
     origin and one per ring ([.., rings + 1]), shared by the ring's points (the
     isotropic kernel; frame-independent when sectors exceed the input order).
+    ``resample=False``: the kernel meets the acquired neighbours of every direction
+    (each binned to its nearest kernel point, a point taking the mean of its
+    neighbours) instead of the SH-resampled neighbourhood; input shell s' is then
+    the sampled table's shell s'.
     """
 
     def __init__(self, shells_in: int, shells_out: int, sampled_gradients, sh_order_in: int, sh_order_out: int,
                  kernel_sizes, lb_lambda: float = 0.0, angular_distance: float = math.pi / 5, bvals=None,
                  channels_in: int = 1, channels_out: int = 1, window: str | None = None, bias: bool = True,
-                 ring_tied: bool = False):
+                 ring_tied: bool = False, resample: bool = True):
         super().__init__()
         ks = list(kernel_sizes)
         if len(set(ks)) != 1:
@@ -325,7 +329,8 @@ class LocalSphericalConvolution(torch.nn.Module):
             raise ValueError(f"sampled gradients have {self.out_basis.n_shells} shells, shells_out={shells_out}")
         if window is None:
             window = "same" if shells_in == shells_out else "all"
-        self.geom = L.LSCGeometry(self.out_basis, sh_order_in, shells_in, angular_distance, len(ks), ks[0], window)
+        self.geom = L.LSCGeometry(self.out_basis, sh_order_in, shells_in, angular_distance, len(ks), ks[0], window,
+                                  neighbours=not resample)
         self.c_in, self.c_out = channels_in, channels_out
         self.ring_tied = bool(ring_tied)
         K = len(ks) + 1 if self.ring_tied else self.geom.K

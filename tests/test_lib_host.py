@@ -110,6 +110,37 @@ def test_lsc_tables_match_oracle(table3):
             np.testing.assert_array_equal(t["row_index"], T4[lb.dir_off[s]:lb.dir_off[s] + lb.m[s]])
 
 
+def test_resampling_free_tables_match_oracle(table3):
+    """Neighbour tables and bins of the resampling-free form are bit-exact against the
+    oracle; the per-shell-pair collapse matrices agree to 1e-12."""
+    dirs, bvals = table3
+    lb = L.SHBasis(dirs, bvals, 8, 0.006, host_only=True)
+    ob = osh.SHBasisOracle(dirs, bvals, 8, 0.006)
+    for order_in, window, R, Sec, rad in ((8, "adjacent", 4, 12, np.deg2rad(25)), (4, "all", 1, 5, np.pi / 5),
+                                          (6, "same", 3, 8, np.deg2rad(30))):
+        lg = L.LSCGeometry(lb, order_in, 3, rad, R, Sec, window, host_only=True, neighbours=True)
+        og = olsc.LSCNeighbourOracle(ob, order_in, 3, rad, R, Sec, window)
+        M, q = og.collapse_mats()
+        n_entries = 0
+        for s in range(3):
+            t = lg.tables(s)
+            np.testing.assert_allclose(t["M"], np.stack(M[s]), rtol=0, atol=1e-12)
+            np.testing.assert_allclose(t["q"], q[s], rtol=0, atol=1e-12)
+            for p in range(3):
+                ip, ix, bx = lg.neighbour_table(s, p)
+                oip, oix, obx = og.nb[s, p]
+                np.testing.assert_array_equal(ip, oip)
+                np.testing.assert_array_equal(ix, oix)
+                np.testing.assert_array_equal(bx, obx)
+                n_entries += len(ix)
+        assert n_entries > 0
+    # the resampled geometry has no neighbour-bin table; shell counts must match
+    lg = L.LSCGeometry(lb, 4, 3, 0.4, 2, 6, "same", host_only=True)
+    assert L.get().delimit_lsc_neighbour_table(lg.handle, 0, 0, None, None, None) == L.ERR_INVALID_ARG
+    with pytest.raises(L.DelimitError):
+        L.LSCGeometry(lb, 4, 2, 0.4, 2, 6, "all", host_only=True, neighbours=True)
+
+
 def test_lsc_argument_errors(table3):
     dirs, bvals = table3
     lb = L.SHBasis(dirs, bvals, 4, 0.006, host_only=True)
