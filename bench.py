@@ -172,6 +172,43 @@ def chain_inputs(cfg, dirs, bvals, dtype, rank=0):
     return s_in, ds_out, w, b
 
 
+def run_fp32_leg(ch, cfg, dirs, bvals, idx, steps, tensor_cores):
+    """The chain with FP32 activations on the inputs of the BF16 chain `ch`: voxels/s,
+    per-call times and error on sampled voxels against the FP64 oracle.  tensor_cores:
+    the LSC GEMMs as three-part BF16 splits on the tensor cores, else CUDA-core FP32."""
+    import torch
+    from paper_1808_01517_gb300 import _lib as L
+    from paper_1808_01517_gb300.chain import Chain
+    L.set_tensor_cores(tensor_cores)
+    try:
+        ch32 = Chain(cfg, dirs, bvals, torch.float32)
+        ch32.s_in.copy_(ch.s_in.float())
+        ch32.ds_out.copy_(ch.ds_out.float())
+        ch32.w.copy_(ch.w)
+        ch32.b.copy_(ch.b)
+        ch32.step()
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(steps)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(steps):
+            ch32.step(events=ev[k])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        per_call = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(steps)]))
+                    for i, name in enumerate(Chain.CALLS)}
+        out = {"value": cfg.n_vox / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+               "gemms": "tensor cores, three-part BF16 splits, six part products, FP32 accumulation" if tensor_cores
+               else "CUDA cores, FP32 FMA", "per_call_ms": per_call,
+               "err_vs_oracle": sampled_errors(ch32, cfg, dirs, bvals, idx)}
+        del ch32
+    finally:
+        L.set_tensor_cores(True)
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_chain_leg(cfg, dirs, bvals, steps=10, warm=3):
     """Another chain configuration at full size (BF16): voxels/s, per-call times and
     error on sampled voxels against the FP64 oracle."""
@@ -404,25 +441,9 @@ def main():
         # ---- accuracy on sampled voxels vs the FP64 oracle ----
         idx = synth.voxel_subset(V, 32, seed=cfg.seed + 99)
         extras["err_vs_oracle_bf16"] = sampled_errors(ch, cfg, dirs, bvals, idx)
-        # ---- FP32 path (CUDA cores, accurate) ----
-        ch32 = Chain(cfg, dirs, bvals, torch.float32)
-        ch32.s_in.copy_(ch.s_in.float())
-        ch32.ds_out.copy_(ch.ds_out.float())
-        ch32.w.copy_(ch.w)
-        ch32.b.copy_(ch.b)
-        ch32.step()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.fp32_steps):
-            ch32.step()
-        e1.record()
-        torch.cuda.synchronize()
-        ms32 = e0.elapsed_time(e1) / args.fp32_steps
-        extras["fp32"] = {"value": V / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32, "steps": args.fp32_steps,
-                          "err_vs_oracle": sampled_errors(ch32, cfg, dirs, bvals, idx)}
-        del ch32
-        torch.cuda.empty_cache()
+        # ---- FP32 path: tensor cores through three-part BF16 splits (default), CUDA cores ----
+        extras["fp32"] = run_fp32_leg(ch, cfg, dirs, bvals, idx, max(3, args.fp32_steps), True)
+        extras["fp32_cuda_cores"] = run_fp32_leg(ch, cfg, dirs, bvals, idx, args.fp32_steps, False)
         # ---- end to end through host buffers ----
         extras["e2e"] = run_e2e(ch, args.e2e_steps)
         # ---- mixed SH orders (4 -> 8) with every input shell mixed into every output shell ----
@@ -448,6 +469,7 @@ def main():
                 "gpu_launches": int(launches)}
         line.update({k: v for k, v in extras.items() if k in ("e2e", "cpu_baseline")})
         line["fp32"] = extras.get("fp32")
+        line["fp32_cuda_cores"] = extras.get("fp32_cuda_cores")
         line["err_vs_oracle_bf16"] = extras.get("err_vs_oracle_bf16")
         line["transforms"] = extras.get("transforms")
         line["mixed_orders_all_shells"] = extras.get("mixed_orders_all_shells")

@@ -261,7 +261,15 @@ size_t delimit_lsc_workspace_size(const delimit_lsc_geometry* geom, int64_t n_vo
  *   flags   0 or DELIMIT_LSC_OPERATOR_READY (the workspace already holds this
  *           call's collapsed operator and bias vector; see above)
  *   workspace >= delimit_lsc_workspace_size(..., 0) bytes, 256-byte aligned.
- * BF16 runs on tcgen05 (FP32 accumulation), F32 on CUDA cores. */
+ * BF16 runs on tcgen05 (FP32 accumulation).  F32 runs on tcgen05 too: the
+ * input, the operator and (backward) the upstream gradient are split into
+ * three BF16 parts each (x = x0 + x1 + x2 to 2^-27 |x|), the six part products
+ * down to 2^-18 of the leading one are accumulated in FP32, and K is summed in
+ * chunks of 1,024 whose results are added in FP32 (measured error against
+ * FP64 about 1e-6 at 65,536 voxels, 16 -> 64 channels); with
+ * delimit_set_tensor_cores(0) F32 runs as FP32 FMA on CUDA cores.  The F32
+ * workspace includes the split copies (3 x 2 bytes per element of sh_in, the
+ * operator and, backward, d_out). */
 delimit_status delimit_lsc_forward(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
                                    const float* b, void* sh_out, int64_t n_vox, int c_in, int c_out,
                                    int64_t ld_in, int64_t ld_out, delimit_dtype act_t, unsigned flags,
@@ -342,9 +350,10 @@ delimit_status delimit_lsc_forward_noalloc(const delimit_lsc_geometry* geom, con
  * 0x2100, CUDA if the synchronisation failed, OK otherwise. */
 delimit_status delimit_device_error(void* stream, int* code);
 
-/* Process-wide switch, default 1: BF16 steps run on the tcgen05 tensor-core
- * kernels where their shape rules allow, else on the CUDA-core kernels.  0
- * forces the CUDA-core kernels (same results within BF16 rounding; used to
+/* Process-wide switch, default 1: BF16 steps, and the LSC GEMMs of F32 calls
+ * (as three-part BF16 splits), run on the tcgen05 tensor-core kernels where
+ * their shape rules allow, else on the CUDA-core kernels.  0 forces the
+ * CUDA-core kernels (same results within the dtype's rounding; used to
  * cross-check the two).  Has no counterpart in the paper. */
 delimit_status delimit_set_tensor_cores(int enable);
 

@@ -567,6 +567,11 @@ struct LscPlan {
   LscDims d;
   size_t w_bytes;       // one of W / Wt
   size_t off_W, off_Wt, off_bias, off_P, off_dwp, total_fwd, total_bwd;
+  // FP32 activations on the tensor cores: three-part BF16 splits of the operator (W3,
+  // and Wt3 when the forward reads Wt), of the LSC input (X3) and of dY (dY3); parts of
+  // an activation are ld3-strided rows, ld3 = n_vox rounded up to 8
+  size_t off_W3, off_Wt3, off_X3, off_dY3, off_Psum;
+  int64_t ld3, ldpt;  // ldpt: leading dimension of the transposed weight-gradient partials
   int splits;
   int64_t vox_per_split;
   bool tc;              // tensor-core GEMMs
@@ -628,13 +633,43 @@ bool make_plan(const delimit_lsc_geometry* g, int64_t n_vox, int c_in, int c_out
   p.off_W = 0;
   p.off_Wt = w_bytes;
   p.off_bias = w_bytes + wt_bytes;
-  p.total_fwd = p.off_bias + align_up(size_t(p.d.rows_out) * 4, 256);
+  // the operator (W, Wt, bias and, for FP32, their splits) leads both layouts
+  const bool f32 = t == DELIMIT_F32;
+  p.ld3 = (std::max<int64_t>(n_vox, 1) + 7) / 8 * 8;
+  p.off_W3 = p.off_bias + align_up(size_t(p.d.rows_out) * 4, 256);
+  p.off_Wt3 = p.off_W3 + (f32 ? align_up(3 * size_t(p.d.rows_out) * size_t(p.d.ldW) * 2, 256) : 0);
+  p.off_X3 = p.off_Wt3 +
+             (f32 && !tc_forward_reads_w(p.d) ? align_up(3 * size_t(p.d.rows_in) * size_t(p.d.ldWt) * 2, 256) : 0);
+  p.total_fwd = p.off_X3 + (f32 ? align_up(3 * size_t(p.d.rows_in) * size_t(p.ld3) * 2, 256) : 0);
   p.splits = wgrad_splits(p.d, std::max<int64_t>(n_vox, 1), &p.vox_per_split);
   p.off_P = p.total_fwd;
-  p.off_dwp = p.off_P + align_up(size_t(p.splits) * size_t(p.d.rows_out) * size_t(p.d.rows_in + 1) * 4, 256);
-  p.total_bwd = p.off_dwp + align_up(reduce_dw_scratch_floats(p.d) * 4, 256);
+  // FP32: the partials are written transposed (columns of ldpt floats) and summed into Psum
+  p.ldpt = (p.d.rows_out + 3) / 4 * 4;
+  const size_t p_elems = std::max(size_t(p.d.rows_out) * size_t(p.d.rows_in + 1),
+                                  f32 ? size_t(p.d.rows_in + 1) * size_t(p.ldpt) : size_t(0));
+  p.off_dwp = p.off_P + align_up(size_t(p.splits) * p_elems * 4, 256);
+  p.off_dY3 = p.off_dwp + align_up(reduce_dw_scratch_floats(p.d) * 4, 256);
+  p.off_Psum = p.off_dY3 + (f32 ? align_up(3 * size_t(p.d.rows_out) * size_t(p.ld3) * 2, 256) : 0);
+  p.total_bwd = p.off_Psum + (f32 ? align_up(size_t(p.d.rows_out) * size_t(p.d.rows_in + 1) * 4, 256) : 0);
   p.tc = false;
   return true;
+}
+
+// The collapsed operator of one call: W (and Wt where the forward reads it), the bias
+// vector when b is given, and for FP32 activations on the tensor cores the BF16
+// splits W3 (and Wt3) that the GEMMs read.  The same set whichever call builds it, so
+// that DELIMIT_LSC_OPERATOR_READY holds between a forward and its backward.
+cudaError_t build_operator(const LscDims& d, const delimit_lsc_geometry* g, const LscPlan& p, const float* w,
+                           const float* b, void* W, void* Wt, float* bias, delimit_dtype act_t, bool tc, char* base,
+                           cudaStream_t cs) {
+  const bool wt = needs_wt(d, tc);
+  cudaError_t e = launch_build_w(d, w, b, g->d_M, g->d_q, W, wt ? Wt : nullptr, bias, int(act_t), cs);
+  if (e != cudaSuccess || !(tc && act_t == DELIMIT_F32)) return e;
+  e = split_bf16x3(static_cast<const float*>(W), d.rows_out, d.ldW, d.ldW, base + p.off_W3, d.ldW, d.rows_out * d.ldW,
+                   cs);
+  if (e != cudaSuccess || !wt) return e;
+  return split_bf16x3(static_cast<const float*>(Wt), d.rows_in, d.ldWt, d.ldWt, base + p.off_Wt3, d.ldWt,
+                      d.rows_in * d.ldWt, cs);
 }
 
 }  // namespace
@@ -683,12 +718,26 @@ delimit_status delimit_lsc_forward(const delimit_lsc_geometry* g, const void* sh
   float* bias = reinterpret_cast<float*>(base + p.off_bias);
   cudaError_t e = cudaSuccess;
   const LscDims& d = p.d;
-  const bool tc = act_t == DELIMIT_BF16 && tc_gemm_supported(d, n_vox, ld_in, ld_out);
+  const bool tc = tc_gemm_supported(d, n_vox, ld_in, ld_out);
+  const bool split = tc && act_t == DELIMIT_F32;  // FP32 on the tensor cores through BF16 splits
   if (!(flags & DELIMIT_LSC_OPERATOR_READY)) {
-    e = launch_build_w(d, w, b, g->d_M, g->d_q, W, needs_wt(d, tc) ? Wt : nullptr, bias, int(act_t), cs);
-    if (e != cudaSuccess) return cuda_fail(e, "build_w launch");
+    e = build_operator(d, g, p, w, b, W, Wt, bias, act_t, tc, base, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "LSC operator build launch");
   }
-  if (tc) {
+  if (split) {
+    void* X3 = base + p.off_X3;
+    e = split_bf16x3(static_cast<const float*>(sh_in), d.rows_in, n_vox, ld_in, X3, p.ld3, d.rows_in * p.ld3, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "FP32 operand split launch");
+    const bool km = tc_forward_reads_w(d);
+    TcParts parts;
+    parts.act = d.rows_in * p.ld3;
+    parts.op = km ? d.rows_out * d.ldW : d.rows_in * d.ldWt;
+    e = tc_lsc_forward(d, X3, base + p.off_W3, base + p.off_Wt3, bias, sh_out, n_vox, p.ld3, ld_out, g->err_word, cs,
+                       parts);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core FP32 LSC forward launch");
+    return DELIMIT_OK;
+  }
+  if (tc && act_t == DELIMIT_BF16) {
     e = tc_lsc_forward(d, sh_in, W, Wt, bias, sh_out, n_vox, ld_in, ld_out, g->err_word, cs);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core LSC forward launch");
     return DELIMIT_OK;
@@ -748,17 +797,29 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
   char* base = static_cast<char*>(ws);
   const int per_in = d.c_in * d.n_in, per_out = d.c_out * d.n_out;
   cudaError_t e;
+  const bool tc = tc_gemm_supported(d, n_vox, ld_in, ld_out);
+  const bool split = tc && act_t == DELIMIT_F32;  // FP32 on the tensor cores through BF16 splits
+  void* dY3 = base + p.off_dY3;
+  if (split) {
+    e = split_bf16x3(static_cast<const float*>(d_out), d.rows_out, n_vox, ld_out, dY3, p.ld3, d.rows_out * p.ld3, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "FP32 operand split launch");
+  }
   if (d_in) {
     void* W = base + p.off_W;
     void* Wt = base + p.off_Wt;
     if (!(flags & DELIMIT_LSC_OPERATOR_READY)) {
-      const bool tc = act_t == DELIMIT_BF16 && tc_gemm_supported(d, n_vox, ld_in, ld_out);
-      e = launch_build_w(d, w, nullptr, g->d_M, g->d_q, W, needs_wt(d, tc) ? Wt : nullptr, nullptr, int(act_t), cs);
-      if (e != cudaSuccess) return cuda_fail(e, "build_w launch");
+      e = build_operator(d, g, p, w, nullptr, W, Wt, nullptr, act_t, tc, base, cs);
+      if (e != cudaSuccess) return cuda_fail(e, "LSC operator build launch");
     }
     bool all_fed = true;
     for (int sp = 0; sp < d.s_in; ++sp) all_fed = all_fed && d.rwin_hi[sp] > d.rwin_lo[sp];
-    if (act_t == DELIMIT_BF16 && all_fed && tc_gemm_supported(d, n_vox, ld_in, ld_out)) {
+    if (split && all_fed) {
+      TcParts parts;
+      parts.act = d.rows_out * p.ld3;
+      parts.op = d.rows_out * d.ldW;
+      e = tc_lsc_dgrad(d, dY3, base + p.off_W3, d_in, n_vox, p.ld3, ld_in, g->err_word, cs, parts);
+      if (e != cudaSuccess) return cuda_fail(e, "tensor-core FP32 LSC input-gradient launch");
+    } else if (act_t == DELIMIT_BF16 && all_fed && tc) {
       e = tc_lsc_dgrad(d, d_out, W, d_in, n_vox, ld_out, ld_in, g->err_word, cs);
       if (e != cudaSuccess) return cuda_fail(e, "tensor-core LSC input-gradient launch");
     } else {
@@ -788,8 +849,26 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
   if (dw || db) {
     float* P = reinterpret_cast<float*>(base + p.off_P);
     const int64_t ldp = d.rows_in + 1;
-    const int64_t split_stride = d.rows_out * ldp;
-    if (act_t == DELIMIT_BF16 && tc_gemm_supported(d, n_vox, ld_in, ld_out)) {
+    int64_t split_stride = d.rows_out * ldp;
+    int splits = p.splits;
+    if (split) {
+      void* X3 = base + p.off_X3;
+      e = split_bf16x3(static_cast<const float*>(sh_in), d.rows_in, n_vox, ld_in, X3, p.ld3, d.rows_in * p.ld3, cs);
+      if (e != cudaSuccess) return cuda_fail(e, "FP32 operand split launch");
+      TcParts parts;
+      parts.act = d.rows_out * p.ld3;
+      parts.act2 = d.rows_in * p.ld3;
+      const int64_t ss_t = ldp * p.ldpt;  // transposed partials: rows_in + 1 columns of ldpt floats
+      e = tc_lsc_wgrad(d, dY3, X3, P, p.ldpt, ss_t, p.splits, p.vox_per_split, n_vox, p.ld3, p.ld3, g->err_word, cs,
+                       parts, d_out, ld_out);
+      if (e != cudaSuccess) return cuda_fail(e, "tensor-core FP32 LSC weight-gradient launch");
+      float* Psum = reinterpret_cast<float*>(base + p.off_Psum);
+      e = sum_transposed_partials(P, p.ldpt, ss_t, p.splits, d.rows_out, ldp, Psum, ldp, cs);
+      if (e != cudaSuccess) return cuda_fail(e, "weight-gradient partial sum launch");
+      P = Psum;
+      split_stride = 0;
+      splits = 1;
+    } else if (act_t == DELIMIT_BF16 && tc) {
       e = tc_lsc_wgrad(d, d_out, sh_in, P, ldp, split_stride, p.splits, p.vox_per_split, n_vox, ld_out, ld_in,
                        g->err_word, cs);
       if (e != cudaSuccess) return cuda_fail(e, "tensor-core LSC weight-gradient launch");
@@ -819,7 +898,7 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
       e = launch_wgrad_simt(a, d.s_out, per_out, maxN, p.splits, int(act_t), cs);
       if (e != cudaSuccess) return cuda_fail(e, "LSC weight-gradient launch");
     }
-    e = launch_reduce_dw(d, P, ldp, split_stride, p.splits, g->d_M, g->d_q, dw, db,
+    e = launch_reduce_dw(d, P, ldp, split_stride, splits, g->d_M, g->d_q, dw, db,
                          reinterpret_cast<float*>(base + p.off_dwp), cs);
     if (e != cudaSuccess) return cuda_fail(e, "dw/db reduction launch");
   }

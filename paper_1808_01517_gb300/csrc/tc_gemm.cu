@@ -64,12 +64,38 @@ struct VoxGroup {
   int bn_last;      // width of the group's last operator tile (<= BN, whole 64-column atoms per CTA)
 };
 
+// FP32 operands on the BF16 tensor cores: each operand is stored as three BF16
+// parts (x = x0 + x1 + x2 up to 2^-27 |x|, the parts the z planes of its tensor
+// map) and a tile accumulates the six part products whose magnitude reaches
+// 2^-18 of the leading one; the dropped three stay below 2^-26.  Term t (largest
+// first) multiplies part split_part_a(t) of A with part split_part_b(t) of B; the
+// kernels issue them smallest first, so the corrections are summed while the
+// accumulator is still small.  The TMEM accumulation error grows linearly with the
+// number of MMAs added into a running sum (measured: about 3e-8 of the sum per MMA, a
+// bias rather than a random walk), so the FP32 path also splits K into chunks of
+// chunk_kb blocks: each chunk starts from zero in TMEM and the epilogue adds it to the
+// FP32 output (read, add in FP32, write back by the thread that stored the element).
+constexpr int kSplitTerms = 6;
+// K blocks of 64 per accumulation chunk on the FP32 path.  Measured at 65,536 voxels
+// (16 -> 64 channels): relative errors of the forward / input / weight gradient 1.0e-6 /
+// 1.1e-6 / 9.7e-7 at 16 blocks (5.4e-7 / 5.8e-7 / 3.7e-7 at 4-8, 1.9e-6 / 2.2e-6 / 1.8e-6 at
+// 32); the weight gradient's time 7.18 ms at 16 against 8.16 ms at 4 (more folds).
+constexpr int kSplitChunkKb = 16;
+__host__ __device__ constexpr int split_part_a(int t) { return t == 2 || t == 3 ? 1 : (t == 5 ? 2 : 0); }
+__host__ __device__ constexpr int split_part_b(int t) { return t == 1 || t == 3 ? 1 : (t == 4 ? 2 : 0); }
+// accumulation chunks of a K range of nkb blocks (at least one, as the MMA issuer
+// commits every tile's accumulator even when it is empty)
+__host__ __device__ inline int k_chunks(int nkb, int chunk_kb) { return nkb > 0 ? (nkb + chunk_kb - 1) / chunk_kb : 1; }
+
 struct VoxParams {
   VoxGroup g[kMaxGroups];
   int n_groups, m_tiles, tiles_per_m;
   int b_kmajor;  // operator stored [N rows][K contiguous] (K-major) instead of [K rows][N contiguous]
+  int n_terms;   // 1 (BF16 operands) or kSplitTerms (three-part BF16 splits of FP32 operands)
+  int chunk_kb;  // K blocks per accumulation chunk (> 0; chunks after the first are added in the epilogue)
   int64_t total_tiles, n_vox, ldy;
   __nv_bfloat16* Y;
+  float* Yf;  // FP32 output (direct stores) in place of Y
   const float* bias;
   int* err;
 };
@@ -95,13 +121,17 @@ __device__ __forceinline__ void vox_decode(const VoxParams& p, int64_t t, int& g
 // each CTA's TMEM receives its own 128 voxels x BN accumulator, drained by its
 // own epilogue, which hands the buffer back on the even CTA's barrier.
 // p.total_tiles counts cluster tiles (voxel-tile pairs x operator tiles).
-template <int BN, int STAGES, bool STAGED, int PASSES, int CL>
+template <int BN, int STAGES, bool STAGED, int PASSES, int CL, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     vox_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const __grid_constant__ CUtensorMap mapY, const __grid_constant__ VoxParams p) {
   using namespace ptx;
   static_assert(CL == 1 || CL == 2, "one CTA or a CTA pair");
   static_assert(CL == 1 || (BN / 2) % 64 == 0, "each CTA of a pair holds whole 64-column operator atoms");
+  static_assert(!(SPLIT && STAGED), "FP32 outputs leave through direct stores");
+  // SPLIT: FP32 operands as three BF16 planes (3-D maps), six terms, chunked K, FP32 output
+  const int n_terms = SPLIT ? p.n_terms : 1;
+  const int chunk_kb = SPLIT ? p.chunk_kb : (1 << 24);
   constexpr int A_BYTES = 2 * kBoxBytes;               // 128 voxels x 64 K rows
   constexpr int B_BYTES = (BN / CL / 64) * kBoxBytes;  // this CTA's BN/CL columns x 64 K rows
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -181,38 +211,53 @@ __global__ void __launch_bounds__(kThreads, 1)
       // box of BN / CL rows (a narrow tile loads rows it does not use)
       const int nbox = tile_bn / CL / 64;
       const uint32_t bytes = (uint32_t)(A_BYTES + (p.b_kmajor ? B_BYTES : nbox * kBoxBytes));
+      const int ncol = G.b_n0 + nt * BN + rank * (tile_bn / CL);
       bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
-        if (!wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, p.err, kErrEmpty)) {
-          ok = false;
-          break;
-        }
-        const uint32_t a_dst = sbase + stage * STAGE_BYTES, b_dst = a_dst + A_BYTES;
-        const int krow = G.a_k0 + kb * kBK;
-        const int ncol = G.b_n0 + nt * BN + rank * (tile_bn / CL);
-        if (CL > 1) {
-          // both CTAs' bytes complete on the even CTA's barrier, which that CTA arms
-          const uint32_t fb = mapa_shared(full_bar(stage), 0);
-          if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), CL * bytes);
-          tma_load_2d_pair(&mapA, fb, a_dst, mt * 128, krow);
-          tma_load_2d_pair(&mapA, fb, a_dst + kBoxBytes, mt * 128 + 64, krow);
+      const int nch = SPLIT ? k_chunks(nkb, chunk_kb) : 1;
+      for (int c = 0; c < nch && ok; ++c)
+      for (int ti = 0; ti < n_terms && ok; ++ti) {
+        const int term = n_terms - 1 - ti;  // smallest part products first
+        const int za = split_part_a(term), zb = split_part_b(term);  // operand planes (0 for BF16)
+        for (int kb = c * chunk_kb; kb < min(nkb, (c + 1) * chunk_kb); ++kb) {
+          if (!wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, p.err, kErrEmpty)) {
+            ok = false;
+            break;
+          }
+          const uint32_t a_dst = sbase + stage * STAGE_BYTES, b_dst = a_dst + A_BYTES;
+          const int krow = G.a_k0 + kb * kBK;
+          // operand tiles: plane z of a split operand (3-D map), or the BF16 array (2-D map)
+          auto load = [&](const CUtensorMap* m, uint32_t bar, uint32_t dst, int x, int y, int z) {
+            if constexpr (SPLIT) {
+              if (CL > 1)
+                tma_load_3d_pair(m, bar, dst, x, y, z);
+              else
+                tma_load_3d(m, bar, dst, x, y, z);
+            } else {
+              if (CL > 1)
+                tma_load_2d_pair(m, bar, dst, x, y);
+              else
+                tma_load_2d(m, bar, dst, x, y);
+            }
+          };
+          uint32_t fb = full_bar(stage);
+          if (CL > 1) {
+            // both CTAs' bytes complete on the even CTA's barrier, which that CTA arms
+            fb = mapa_shared(full_bar(stage), 0);
+            if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), CL * bytes);
+          } else {
+            mbar_arrive_expect_tx(full_bar(stage), bytes);
+          }
+          load(&mapA, fb, a_dst, mt * 128, krow, za);
+          load(&mapA, fb, a_dst + kBoxBytes, mt * 128 + 64, krow, za);
           if (p.b_kmajor)
-            tma_load_2d_pair(&mapB, fb, b_dst, krow, ncol);
+            load(&mapB, fb, b_dst, krow, ncol, zb);
           else
-            for (int j = 0; j < nbox; ++j) tma_load_2d_pair(&mapB, fb, b_dst + j * kBoxBytes, ncol + j * 64, krow);
-        } else {
-          mbar_arrive_expect_tx(full_bar(stage), bytes);
-          tma_load_2d(&mapA, full_bar(stage), a_dst, mt * 128, krow);
-          tma_load_2d(&mapA, full_bar(stage), a_dst + kBoxBytes, mt * 128 + 64, krow);
-          if (p.b_kmajor)
-            tma_load_2d(&mapB, full_bar(stage), b_dst, krow, ncol);
-          else
-            for (int j = 0; j < nbox; ++j) tma_load_2d(&mapB, full_bar(stage), b_dst + j * kBoxBytes, ncol + j * 64, krow);
-        }
-        pend[stage] = (int)phase;
-        if (++stage == STAGES) {
-          stage = 0;
-          phase ^= 1u;
+            for (int j = 0; j < nbox; ++j) load(&mapB, fb, b_dst + j * kBoxBytes, ncol + j * 64, krow, zb);
+          pend[stage] = (int)phase;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
         }
       }
       if (!ok) break;
@@ -228,52 +273,60 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int64_t t = t_first; t < p.total_tiles && !*abort_flag; t += t_step) {
+    bool ok = true;
+    for (int64_t t = t_first; ok && t < p.total_tiles && !*abort_flag; t += t_step) {
       int g, mt, nt;
       vox_decode(p, t, g, mt, nt);
       const int nkb = (p.g[g].K + kBK - 1) / kBK;
       const bool bk = p.b_kmajor != 0;
       const uint32_t idesc = idesc_bf16(128 * CL, nt == p.g[g].n_tiles - 1 ? p.g[g].bn_last : BN, true, !bk);
-      if (!wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.err, kErrTmemEmpty)) break;
-      tc_fence_after();
-      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-      bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
-        if (!wait_bounded(full_bar(stage), phase, abort_flag, p.err, kErrFull)) {
+      const int nch = SPLIT ? k_chunks(nkb, chunk_kb) : 1;
+      for (int c = 0; c < nch; ++c) {
+        if (!wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.err, kErrTmemEmpty)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t a_src = sbase + stage * STAGE_BYTES, b_src = a_src + A_BYTES;
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        // this chunk's K blocks of every term, in the producer's order
+        const int nk = SPLIT ? max(0, min(chunk_kb, nkb - c * chunk_kb)) * n_terms : nkb;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!wait_bounded(full_bar(stage), phase, abort_flag, p.err, kErrFull)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_src = sbase + stage * STAGE_BYTES, b_src = a_src + A_BYTES;
 #pragma unroll
-        for (int k = 0; k < kBK / 16; ++k) {
-          // MN-major, 128-byte swizzle: 64-element MN atoms kBoxBytes apart (LBO),
-          // 8-row K groups 1024 B apart (SBO); 16 K rows = 2048 B per MMA.  K-major
-          // operator: rows 128 B apart, 8-row groups 1024 B apart, 16 K = 32 B per MMA.
-          const uint64_t ad = umma_desc(a_src + k * 2048, kBoxBytes, 1024, kSwizzle128B);
-          const uint64_t bd = bk ? umma_desc(b_src + k * 32, 16, 1024, kSwizzle128B)
-                                 : umma_desc(b_src + k * 2048, kBoxBytes, 1024, kSwizzle128B);
+          for (int k = 0; k < kBK / 16; ++k) {
+            // MN-major, 128-byte swizzle: 64-element MN atoms kBoxBytes apart (LBO),
+            // 8-row K groups 1024 B apart (SBO); 16 K rows = 2048 B per MMA.  K-major
+            // operator: rows 128 B apart, 8-row groups 1024 B apart, 16 K = 32 B per MMA.
+            const uint64_t ad = umma_desc(a_src + k * 2048, kBoxBytes, 1024, kSwizzle128B);
+            const uint64_t bd = bk ? umma_desc(b_src + k * 32, 16, 1024, kSwizzle128B)
+                                   : umma_desc(b_src + k * 2048, kBoxBytes, 1024, kSwizzle128B);
+            if (CL > 1)
+              mma_bf16_pair(d_tmem, ad, bd, idesc, (kb | k) != 0);
+            else
+              mma_bf16(d_tmem, ad, bd, idesc, (kb | k) != 0);
+          }
           if (CL > 1)
-            mma_bf16_pair(d_tmem, ad, bd, idesc, (kb | k) != 0);
+            mma_commit_pair_mc(empty_bar(stage), 0x3);  // both CTAs' producers refill this stage
           else
-            mma_bf16(d_tmem, ad, bd, idesc, (kb | k) != 0);
+            mma_commit(empty_bar(stage));
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
         }
+        if (!ok) break;
         if (CL > 1)
-          mma_commit_pair_mc(empty_bar(stage), 0x3);  // both CTAs' producers refill this stage
+          mma_commit_pair_mc(tfull_bar(acc), 0x3);
         else
-          mma_commit(empty_bar(stage));
-        if (++stage == STAGES) {
-          stage = 0;
-          phase ^= 1u;
-        }
+          mma_commit(tfull_bar(acc));
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1u;
       }
-      if (!ok) break;
-      if (CL > 1)
-        mma_commit_pair_mc(tfull_bar(acc), 0x3);
-      else
-        mma_commit(tfull_bar(acc));
-      acc ^= 1;
-      if (acc == 0) acc_phase ^= 1u;
     }
     if (CL > 1)
       mma_commit_pair(drain_bar);
@@ -383,38 +436,79 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!alive) break;
       } else {
-        for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
-          uint32_t rv[4][16];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int c0 = 32 * (k0 + u) + 16 * half;
-            if (c0 < BN && nt * BN + c0 < G.N) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+        // one accumulator per K chunk (one chunk unless the operands are FP32 splits):
+        // the first is stored with the bias, later ones are added to the FP32 output
+        const int nch = SPLIT ? k_chunks((G.K + kBK - 1) / kBK, chunk_kb) : 1;
+        bool alive = true;
+        for (int c = 0; c < nch; ++c) {
+          if (c > 0) {
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
+            const bool okc = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTmemFull);
+            if (!__all_sync(0xffffffffu, okc)) {
+              alive = false;
+              break;
+            }
+            tc_fence_after();
           }
-          tmem_wait_ld();
+          const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+          if (c == 0) {
+            for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
+              uint32_t rv[4][16];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int c0 = 32 * (k0 + u) + 16 * half;
-            const int nbase = nt * BN + c0;
-            if (c0 < BN && nbase < G.N) {
+              for (int u = 0; u < 4; ++u) {
+                const int c0 = 32 * (k0 + u) + 16 * half;
+                if (c0 < BN && nt * BN + c0 < G.N) tmem_ld16_nowait(tb + (uint32_t)c0, rv[u]);
+              }
+              tmem_wait_ld();
 #pragma unroll
-              for (int jj = 0; jj < 16; ++jj) {
-                const int n = nbase + jj;
-                if (n < G.N && vok) {
-                  const float bv = p.bias ? __ldg(p.bias + G.y_row0 + n) : 0.f;
-                  p.Y[(G.y_row0 + n) * p.ldy + vox] = __float2bfloat16_rn(__uint_as_float(rv[u][jj]) + bv);
+              for (int u = 0; u < 4; ++u) {
+                const int c0 = 32 * (k0 + u) + 16 * half;
+                const int nbase = nt * BN + c0;
+                if (c0 < BN && nbase < G.N) {
+#pragma unroll
+                  for (int jj = 0; jj < 16; ++jj) {
+                    const int n = nbase + jj;
+                    if (n < G.N && vok) {
+                      const int64_t o = (G.y_row0 + n) * p.ldy + vox;
+                      const float v = __uint_as_float(rv[u][jj]) + (p.bias ? __ldg(p.bias + G.y_row0 + n) : 0.f);
+                      if constexpr (SPLIT)
+                        p.Yf[o] = v;
+                      else
+                        p.Y[o] = __float2bfloat16_rn(v);
+                    }
+                  }
                 }
               }
             }
+          } else if constexpr (SPLIT) {
+            // later chunks: add to the partial sums this thread stored, their loads all in
+            // flight together (no store between them) under the TMEM loads
+            for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; ++k0) {
+              const int c0 = 32 * k0 + 16 * half, nbase = nt * BN + c0;
+              uint32_t rv[16];
+              float old[16];
+              tmem_ld16_nowait(tb + (uint32_t)c0, rv);
+              float* yc = p.Yf + (G.y_row0 + nbase) * p.ldy + vox;
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) old[jj] = (nbase + jj < G.N && vok) ? yc[jj * p.ldy] : 0.f;
+              tmem_wait_ld();
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj)
+                if (nbase + jj < G.N && vok) yc[jj * p.ldy] = old[jj] + __uint_as_float(rv[jj]);
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            const uint32_t te = CL > 1 ? mapa_shared(tempty_bar(acc), 0) : tempty_bar(acc);
+            if (CL > 1)
+              mbar_arrive_cluster(te);
+            else
+              mbar_arrive(te);
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          if (CL > 1)
-            mbar_arrive_cluster(tempty);
-          else
-            mbar_arrive(tempty);
-        }
+        if (!alive) break;
       }
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
@@ -446,7 +540,13 @@ struct WgGroup {
 struct WgParams {
   WgGroup g[kMaxGroups];
   int n_groups, splits;
+  int n_terms;   // 1 (BF16 operands) or kSplitTerms (three-part splits of FP32 operands)
+  int chunk_kb;  // voxel blocks of 64 per accumulation chunk (> 0)
   int64_t tiles_per_split, total_tiles, vps, n_vox, ldp, split_stride;
+  // element (row r, column c) of a split's partial at r * p_rs + c * p_cs: (ldp, 1), or (1, ldp)
+  // for the transposed partials of the FP32 path, whose read-modify-write per chunk is then
+  // coalesced across a warp's lanes (consecutive rows)
+  int64_t p_rs, p_cs;
   float* P;
   int* err;
 };
@@ -467,13 +567,17 @@ __device__ __forceinline__ void wg_decode(const WgParams& p, int64_t t, int& spl
 // each CTA stages its own 128 output rows of dY and BN/2 of the BN input rows
 // of X; the even CTA arms the stage barriers and issues the MMAs, each CTA
 // drains its own 128 rows.  m_tiles in the groups then counts row-tile pairs.
-template <int BN, int STAGES, int CL>
+template <int BN, int STAGES, int CL, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     wgrad_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                  const __grid_constant__ WgParams p) {
   using namespace ptx;
   static_assert(CL == 1 || CL == 2, "one CTA or a CTA pair");
   static_assert(BN <= 256 && BN % 16 == 0 && (BN / CL) % 8 == 0, "N tile: whole 8-row groups per CTA");
+  // SPLIT: FP32 operands as three BF16 planes (3-D maps), six terms, chunked voxels,
+  // transposed partials
+  const int n_terms = SPLIT ? p.n_terms : 1;
+  const int chunk_kb = SPLIT ? p.chunk_kb : (1 << 24);
   constexpr int A_BYTES = 128 * 128;      // 128 rows x 64 voxels
   constexpr int B_BYTES = BN / CL * 128;  // this CTA's BN/CL rows x 64 voxels
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -539,30 +643,46 @@ __global__ void __launch_bounds__(kThreads, 1)
       const WgGroup& G = p.g[g];
       const int64_t vs = (int64_t)split * p.vps, ve = min(p.n_vox, vs + p.vps);
       const int nkb = (int)((ve - vs + 63) / 64);
+      const int arow = (int)(G.m_row0 + (int64_t)mt * 128);
+      const int brow = (int)(G.x_row0 + (int64_t)nt * BN + rank * (BN / CL));
       bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
-        if (!wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, p.err, kErrEmpty)) {
-          ok = false;
-          break;
-        }
-        const uint32_t a_dst = sbase + stage * STAGE_BYTES, b_dst = a_dst + A_BYTES;
-        const int vx = (int)(vs + (int64_t)kb * 64);
-        const int arow = (int)(G.m_row0 + (int64_t)mt * 128);
-        const int brow = (int)(G.x_row0 + (int64_t)nt * BN + rank * (BN / CL));
-        if (CL > 1) {
-          const uint32_t fb = mapa_shared(full_bar(stage), 0);
-          if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), CL * STAGE_BYTES);
-          tma_load_2d_pair(&mapA, fb, a_dst, vx, arow);
-          tma_load_2d_pair(&mapB, fb, b_dst, vx, brow);
-        } else {
-          mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
-          tma_load_2d(&mapA, full_bar(stage), a_dst, vx, arow);
-          tma_load_2d(&mapB, full_bar(stage), b_dst, vx, brow);
-        }
-        pend[stage] = (int)phase;
-        if (++stage == STAGES) {
-          stage = 0;
-          phase ^= 1u;
+      const int nch = SPLIT ? k_chunks(nkb, chunk_kb) : 1;
+      for (int c = 0; c < nch && ok; ++c)
+      for (int ti = 0; ti < n_terms && ok; ++ti) {
+        const int term = n_terms - 1 - ti;  // smallest part products first
+        const int za = split_part_a(term), zb = split_part_b(term);
+        for (int kb = c * chunk_kb; kb < min(nkb, (c + 1) * chunk_kb); ++kb) {
+          if (!wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, p.err, kErrEmpty)) {
+            ok = false;
+            break;
+          }
+          const uint32_t a_dst = sbase + stage * STAGE_BYTES, b_dst = a_dst + A_BYTES;
+          const int vx = (int)(vs + (int64_t)kb * 64);
+          if (CL > 1) {
+            const uint32_t fb = mapa_shared(full_bar(stage), 0);
+            if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), CL * STAGE_BYTES);
+            if constexpr (SPLIT) {
+              tma_load_3d_pair(&mapA, fb, a_dst, vx, arow, za);
+              tma_load_3d_pair(&mapB, fb, b_dst, vx, brow, zb);
+            } else {
+              tma_load_2d_pair(&mapA, fb, a_dst, vx, arow);
+              tma_load_2d_pair(&mapB, fb, b_dst, vx, brow);
+            }
+          } else {
+            mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
+            if constexpr (SPLIT) {
+              tma_load_3d(&mapA, full_bar(stage), a_dst, vx, arow, za);
+              tma_load_3d(&mapB, full_bar(stage), b_dst, vx, brow, zb);
+            } else {
+              tma_load_2d(&mapA, full_bar(stage), a_dst, vx, arow);
+              tma_load_2d(&mapB, full_bar(stage), b_dst, vx, brow);
+            }
+          }
+          pend[stage] = (int)phase;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
         }
       }
       if (!ok) break;
@@ -575,49 +695,57 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int64_t t = t_first; t < p.total_tiles && !*abort_flag; t += t_step) {
+    bool ok = true;
+    for (int64_t t = t_first; ok && t < p.total_tiles && !*abort_flag; t += t_step) {
       int split, g, mt, nt;
       wg_decode(p, t, split, g, mt, nt);
       const int64_t vs = (int64_t)split * p.vps, ve = min(p.n_vox, vs + p.vps);
       const int nkb = (int)((ve - vs + 63) / 64);
-      if (!wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.err, kErrTmemEmpty)) break;
-      tc_fence_after();
-      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
-      bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
-        if (!wait_bounded(full_bar(stage), phase, abort_flag, p.err, kErrFull)) {
+      const int nch = SPLIT ? k_chunks(nkb, chunk_kb) : 1;
+      for (int c = 0; c < nch; ++c) {
+        if (!wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.err, kErrTmemEmpty)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t a_src = sbase + stage * STAGE_BYTES, b_src = a_src + A_BYTES;
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 256);
+        // this chunk's voxel blocks of every term, in the producer's order
+        const int nk = SPLIT ? max(0, min(chunk_kb, nkb - c * chunk_kb)) * n_terms : nkb;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!wait_bounded(full_bar(stage), phase, abort_flag, p.err, kErrFull)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_src = sbase + stage * STAGE_BYTES, b_src = a_src + A_BYTES;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          // K-major, 128-byte swizzle: rows 128 B apart, 8-row groups 1024 B apart (SBO);
-          // 16 voxels = 32 B per MMA inside the swizzle atom.
-          const uint64_t ad = umma_desc(a_src + k * 32, 16, 1024, kSwizzle128B);
-          const uint64_t bd = umma_desc(b_src + k * 32, 16, 1024, kSwizzle128B);
+          for (int k = 0; k < 4; ++k) {
+            // K-major, 128-byte swizzle: rows 128 B apart, 8-row groups 1024 B apart (SBO);
+            // 16 voxels = 32 B per MMA inside the swizzle atom.
+            const uint64_t ad = umma_desc(a_src + k * 32, 16, 1024, kSwizzle128B);
+            const uint64_t bd = umma_desc(b_src + k * 32, 16, 1024, kSwizzle128B);
+            if (CL > 1)
+              mma_bf16_pair(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+            else
+              mma_bf16(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+          }
           if (CL > 1)
-            mma_bf16_pair(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+            mma_commit_pair_mc(empty_bar(stage), 0x3);
           else
-            mma_bf16(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+            mma_commit(empty_bar(stage));
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
         }
+        if (!ok) break;
         if (CL > 1)
-          mma_commit_pair_mc(empty_bar(stage), 0x3);
+          mma_commit_pair_mc(tfull_bar(acc), 0x3);
         else
-          mma_commit(empty_bar(stage));
-        if (++stage == STAGES) {
-          stage = 0;
-          phase ^= 1u;
-        }
+          mma_commit(tfull_bar(acc));
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1u;
       }
-      if (!ok) break;
-      if (CL > 1)
-        mma_commit_pair_mc(tfull_bar(acc), 0x3);
-      else
-        mma_commit(tfull_bar(acc));
-      acc ^= 1;
-      if (acc == 0) acc_phase ^= 1u;
     }
     if (CL > 1)
       mma_commit_pair(drain_bar);
@@ -634,43 +762,64 @@ __global__ void __launch_bounds__(kThreads, 1)
       wg_decode(p, t, split, g, mt, nt);
       mt = mt * CL + rank;
       const WgGroup& G = p.g[g];
-      bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTmemFull);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
-      tc_fence_after();
       const int m = mt * 128 + q * 32 + lane;
-      float* prow = p.P + (int64_t)split * p.split_stride + (G.m_row0 + m) * p.ldp + G.n_col0;
-      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 256);
-      for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
-        uint32_t rv[4][16];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int c0 = 32 * (k0 + u) + 16 * half;
-          if (c0 < BN && nt * BN + c0 < G.N) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+      const int64_t rs = SPLIT ? p.p_rs : p.ldp, cs = SPLIT ? p.p_cs : 1;
+      float* prow = p.P + (int64_t)split * p.split_stride + (G.m_row0 + m) * rs + G.n_col0 * cs;
+      const int64_t vs = (int64_t)split * p.vps, ve = min(p.n_vox, vs + p.vps);
+      const int nch = SPLIT ? k_chunks((int)((ve - vs + 63) / 64), chunk_kb) : 1;
+      bool alive = true;
+      // one accumulator per voxel chunk: the first is stored, later ones added (FP32)
+      for (int c = 0; c < nch; ++c) {
+        bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTmemFull);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+          alive = false;
+          break;
         }
-        tmem_wait_ld();
-        if (m < G.M) {
+        tc_fence_after();
+        const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 256);
+        for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
+          uint32_t rv[4][16];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int nbase = nt * BN + 32 * (k0 + u) + 16 * half;
-            if (32 * (k0 + u) + 16 * half < BN && nbase < G.N) {
+            const int c0 = 32 * (k0 + u) + 16 * half;
+            if (c0 < BN && nt * BN + c0 < G.N) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+          }
+          tmem_wait_ld();
+          if (m < G.M) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                if (nbase + j < G.N) prow[nbase + j] = __uint_as_float(rv[u][j]);
+            for (int u = 0; u < 4; ++u) {
+              const int nbase = nt * BN + 32 * (k0 + u) + 16 * half;
+              if (32 * (k0 + u) + 16 * half < BN && nbase < G.N) {
+                if (SPLIT && c > 0) {
+                  // later chunks: add to the partial sums this thread stored (loads first)
+                  float old[16];
+#pragma unroll
+                  for (int j = 0; j < 16; ++j) old[j] = nbase + j < G.N ? prow[(nbase + j) * cs] : 0.f;
+#pragma unroll
+                  for (int j = 0; j < 16; ++j)
+                    if (nbase + j < G.N) prow[(nbase + j) * cs] = old[j] + __uint_as_float(rv[u][j]);
+                } else {
+#pragma unroll
+                  for (int j = 0; j < 16; ++j)
+                    if (nbase + j < G.N) prow[(nbase + j) * cs] = __uint_as_float(rv[u][j]);
+                }
+              }
             }
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if (CL > 1)
+            mbar_arrive_cluster(mapa_shared(tempty_bar(acc), 0));
+          else
+            mbar_arrive(tempty_bar(acc));
+        }
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1u;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        if (CL > 1)
-          mbar_arrive_cluster(mapa_shared(tempty_bar(acc), 0));
-        else
-          mbar_arrive(tempty_bar(acc));
-      }
-      acc ^= 1;
-      if (acc == 0) acc_phase ^= 1u;
+      if (!alive) break;
     }
   }
   tc_fence_before();
@@ -690,32 +839,125 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ---------------------------------------------------------------------------
 // host side
 // Row sums of dY per voxel split (the bias-gradient column of the weight gradient).
-__global__ void __launch_bounds__(256) rowsum_kernel(const __nv_bfloat16* __restrict__ dY, int64_t lddy, int64_t rows,
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) rowsum_kernel(const T* __restrict__ dY, int64_t lddy, int64_t rows,
                                                      int64_t n_vox, int64_t vps, int splits, float* __restrict__ P,
-                                                     int64_t ldp, int64_t split_stride, int64_t col) {
+                                                     int64_t rs, int64_t split_stride, int64_t col_off) {
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
   if (wid >= rows * splits) return;
   const int64_t row = wid / splits;
   const int split = (int)(wid % splits);
   const int64_t vs = (int64_t)split * vps, ve = min(n_vox, vs + vps);
-  const __nv_bfloat16* r = dY + row * lddy;
+  const T* r = dY + row * lddy;
   float acc = 0.f;
-  // vs is a multiple of 128 and rows are 16-byte aligned: 8-element vectors up to the last full one
-  const int64_t vend8 = vs + ((ve - vs) / 8) * 8;
-  for (int64_t v = vs + (int64_t)lane * 8; v < vend8; v += 256) {
+  // vs is a multiple of 128 and rows are 16-byte aligned: 16-byte vectors up to the last full one
+  constexpr int VE = 16 / sizeof(T);
+  const int64_t vend = vs + ((ve - vs) / VE) * VE;
+  for (int64_t v = vs + (int64_t)lane * VE; v < vend; v += 32 * VE) {
     const uint4 u = *reinterpret_cast<const uint4*>(r + v);
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+    if constexpr (sizeof(T) == 2) {
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float2 f = __bfloat1622float2(h[i]);
-      acc += f.x + f.y;
+      for (int i = 0; i < 4; ++i) {
+        const float2 f = __bfloat1622float2(h[i]);
+        acc += f.x + f.y;
+      }
+    } else {
+      acc += (__uint_as_float(u.x) + __uint_as_float(u.y)) + (__uint_as_float(u.z) + __uint_as_float(u.w));
     }
   }
-  for (int64_t v = vend8 + lane; v < ve; v += 32) acc += __bfloat162float(r[v]);
+  for (int64_t v = vend + lane; v < ve; v += 32) acc += to_f32(r[v]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) P[(int64_t)split * split_stride + row * ldp + col] = acc;
+  if (lane == 0) P[(int64_t)split * split_stride + row * rs + col_off] = acc;
+}
+
+// Three-part BF16 split of an FP32 array (the operands of the FP32 path): part 0 is
+// the BF16 rounding of x, part 1 that of the remainder x - x0 (exact in FP32), part
+// 2 that of x - x0 - x1.  Each rounding leaves at most 2^-9 of its argument, so
+// |x - x0 - x1 - x2| <= 2^-27 |x| (normal range).  Four columns per thread.
+__global__ void __launch_bounds__(256) split3_kernel(const float* __restrict__ x, int64_t rows, int64_t cols,
+                                                     int64_t ldx, __nv_bfloat16* __restrict__ out, int64_t ldo,
+                                                     int64_t part_stride) {
+  const int64_t c4 = (ldo + 3) / 4;  // 4-column chunks per output row
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows * c4; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / c4, c = (i % c4) * 4;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (c + 4 <= cols) {
+      const float4 f = *reinterpret_cast<const float4*>(x + r * ldx + c);
+      v[0] = f.x, v[1] = f.y, v[2] = f.z, v[3] = f.w;
+    } else {
+      for (int j = 0; j < 4; ++j)
+        if (c + j < cols) v[j] = x[r * ldx + c + j];
+    }
+    __nv_bfloat16 part[3][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float rem = v[j];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        part[q][j] = __float2bfloat16_rn(rem);
+        rem -= __bfloat162float(part[q][j]);
+      }
+    }
+    __nv_bfloat16* o = out + r * ldo + c;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (c + 4 <= ldo) {
+        *reinterpret_cast<uint2*>(o + q * part_stride) = *reinterpret_cast<const uint2*>(part[q]);
+      } else {
+        for (int j = 0; j < 4 && c + j < ldo; ++j) o[q * part_stride + j] = part[q][j];
+      }
+    }
+  }
+}
+
+// P[r * ldp + c] = sum over splits z (in order) of PT[z * split_stride + c * ldpt + r]: the
+// transposed weight-gradient partials of the FP32 path back in the row layout, summed.
+// 32 x 32 tiles through shared memory; reads and writes coalesced.
+__global__ void __launch_bounds__(256) sum_transpose_kernel(const float* __restrict__ PT, int64_t ldpt,
+                                                            int64_t split_stride, int splits, int64_t rows,
+                                                            int64_t cols, float* __restrict__ P, int64_t ldp) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t c = c0 + i, r = r0 + tx;
+    float v = 0.f;
+    if (c < cols && r < rows)
+      for (int z = 0; z < splits; ++z) v += PT[z * split_stride + c * ldpt + r];
+    tile[i][tx] = v;
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r0 + i, c = c0 + tx;
+    if (r < rows && c < cols) P[r * ldp + c] = tile[tx][i];
+  }
+}
+
+cudaError_t sum_transposed_partials(const float* PT, int64_t ldpt, int64_t split_stride, int splits, int64_t rows,
+                                    int64_t cols, float* P, int64_t ldp, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  TraceScope trace("lsc_wgrad_f32_sum", st);
+  const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+  sum_transpose_kernel<<<grid, 256, 0, st>>>(PT, ldpt, split_stride, splits, rows, cols, P, ldp);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t split_bf16x3(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* out, int64_t ldo,
+                         int64_t part_stride, cudaStream_t st) {
+  if (rows <= 0 || ldo <= 0) return cudaSuccess;
+  TraceScope trace("split_bf16x3", st);
+  const int64_t work = rows * ((ldo + 3) / 4);
+  const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, 152 * 16);
+  split3_kernel<<<blocks, 256, 0, st>>>(x, rows, cols, ldx, reinterpret_cast<__nv_bfloat16*>(out), ldo, part_stride);
+  count_launch();
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -753,16 +995,19 @@ DevInfo dev_info() {
   return cache[dev];
 }
 
-// 2-D BF16 map over a [outer][ld] row-major array using `inner` columns, 128-byte swizzle.
+// BF16 map over a [outer][ld] row-major array using `inner` columns, 128-byte swizzle:
+// 2-D, or with part_stride > 0 3-D over the three BF16 parts of a split FP32 operand
+// (part_stride elements apart), which the kernels address with the z coordinate.
 bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t ld_elems, uint32_t box_inner,
-              uint32_t box_outer) {
+              uint32_t box_outer, int64_t part_stride = 0) {
   auto fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {ld_elems * 2};
-  cuuint32_t box[2] = {box_inner, box_outer};
-  cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+  const cuuint32_t rank = part_stride > 0 ? 3 : 2;
+  cuuint64_t dims[3] = {inner, outer, 3};
+  cuuint64_t strides[2] = {ld_elems * 2, (uint64_t)part_stride * 2};
+  cuuint32_t box[3] = {box_inner, box_outer, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -853,13 +1098,13 @@ cudaError_t launch_persistent(void (*kern)(Params...), int64_t tiles, int cl, si
   return e;
 }
 
-template <int BN, bool STAGED, int CL>
+template <int BN, bool STAGED, int CL, bool SPLIT>
 cudaError_t launch_vox(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& my, const VoxParams& p,
                        cudaStream_t st) {
   constexpr int S = vox_stages<BN, STAGED, CL>();
   const size_t smem =
       smem_bytes<BN, S>(2 * kBoxBytes, (BN / CL / 64) * kBoxBytes) + (STAGED ? BN / kFwdPasses * 256 : 0) + 16;
-  auto kern = vox_gemm_kernel<BN, S, STAGED, kFwdPasses, CL>;
+  auto kern = vox_gemm_kernel<BN, S, STAGED, kFwdPasses, CL, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = launch_persistent(kern, p.total_tiles, CL, smem, st, ma, mb, my, p);
@@ -867,17 +1112,17 @@ cudaError_t launch_vox(const CUtensorMap& ma, const CUtensorMap& mb, const CUten
   return cudaGetLastError();
 }
 
-template <int BN, bool STAGED>
+template <int BN, bool STAGED, bool SPLIT = false>
 cudaError_t launch_vox_cl(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& my, VoxParams& p, int cl,
                           cudaStream_t st) {
   if constexpr ((BN / 2) % 64 == 0) {
     if (cl > 1) {
       p.total_tiles = (int64_t)((p.m_tiles + 1) / 2) * p.tiles_per_m;
-      return launch_vox<BN, STAGED, 2>(ma, mb, my, p, st);
+      return launch_vox<BN, STAGED, 2, SPLIT>(ma, mb, my, p, st);
     }
   }
   p.total_tiles = (int64_t)p.m_tiles * p.tiles_per_m;
-  return launch_vox<BN, STAGED, 1>(ma, mb, my, p, st);
+  return launch_vox<BN, STAGED, 1, SPLIT>(ma, mb, my, p, st);
 }
 
 // choose the N tile that wastes the fewest columns over the groups (ties: larger)
@@ -903,6 +1148,7 @@ struct OperatorView {
   const void* ptr;
   uint64_t rows, cols, ld;  // elements
   bool kmajor;
+  int64_t part_stride = 0;  // elements between the BF16 parts of a split FP32 operator (0: BF16)
 };
 
 // cl = 2 runs CTA pairs with 2-SM MMAs; a pair splits its bn operator columns
@@ -912,8 +1158,11 @@ cudaError_t run_vox(const CUtensorMap& ma, const OperatorView& B, VoxParams& p, 
   if (cl > 1 && bn == 192) bn = 256;
   // MN-major: 64-column x 64-K-row boxes; K-major: 64-K x (bn / cl)-row boxes
   CUtensorMap mb;
-  if (!make_map(&mb, B.ptr, B.cols, B.rows, B.ld, 64, B.kmajor ? (uint32_t)(bn / cl) : (uint32_t)kBK))
+  if (!make_map(&mb, B.ptr, B.cols, B.rows, B.ld, 64, B.kmajor ? (uint32_t)(bn / cl) : (uint32_t)kBK, B.part_stride))
     return cudaErrorInvalidValue;
+  if (p.n_terms < 1) p.n_terms = 1;
+  if (p.chunk_kb < 1) p.chunk_kb = 1 << 24;
+  if (p.Yf) staged_ok = false;  // FP32 outputs leave through direct stores
   p.b_kmajor = B.kmajor ? 1 : 0;
   p.tiles_per_m = 0;
   bool same_n = true;
@@ -947,6 +1196,13 @@ cudaError_t run_vox(const CUtensorMap& ma, const OperatorView& B, VoxParams& p, 
       default: return launch_vox_cl<128, true>(ma, mb, my, p, cl, st);
     }
   }
+  if (p.Yf) {
+    switch (bn) {
+      case 256: return launch_vox_cl<256, false, true>(ma, mb, my, p, cl, st);
+      case 192: return launch_vox_cl<192, false, true>(ma, mb, my, p, cl, st);
+      default: return launch_vox_cl<128, false, true>(ma, mb, my, p, cl, st);
+    }
+  }
   switch (bn) {
     case 256: return launch_vox_cl<256, false>(ma, mb, my, p, cl, st);
     case 192: return launch_vox_cl<192, false>(ma, mb, my, p, cl, st);
@@ -970,18 +1226,19 @@ bool tc_gemm_supported(const LscDims& d, int64_t n_vox, int64_t ld_in, int64_t l
 bool tc_forward_reads_w(const LscDims& d) { return d.in_blk == (int64_t)d.c_in * d.n_in; }
 
 cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const void* Wt, const float* bias, void* Y,
-                           int64_t n_vox, int64_t ldx, int64_t ldy, int* err, cudaStream_t st) {
-  TraceScope trace("lsc_fwd_gemm", st);
+                           int64_t n_vox, int64_t ldx, int64_t ldy, int* err, cudaStream_t st, TcParts parts) {
+  TraceScope trace(parts.on() ? "lsc_fwd_gemm_f32" : "lsc_fwd_gemm", st);
   CUtensorMap ma;
-  if (!make_map(&ma, X, (uint64_t)n_vox, (uint64_t)d.rows_in, (uint64_t)ldx, 64, kBK)) return cudaErrorInvalidValue;
+  if (!make_map(&ma, X, (uint64_t)n_vox, (uint64_t)d.rows_in, (uint64_t)ldx, 64, kBK, parts.act))
+    return cudaErrorInvalidValue;
   // Without per-shell column padding the input-feature index of W's columns equals the
   // row index of X, so W serves as the K-major operator and Wt is not needed.
   const bool kmajor = tc_forward_reads_w(d);
   OperatorView B;
   if (kmajor)
-    B = OperatorView{W, (uint64_t)d.rows_out, (uint64_t)d.ldW, (uint64_t)d.ldW, true};
+    B = OperatorView{W, (uint64_t)d.rows_out, (uint64_t)d.ldW, (uint64_t)d.ldW, true, parts.op};
   else
-    B = OperatorView{Wt, (uint64_t)d.rows_in, (uint64_t)d.ldWt, (uint64_t)d.ldWt, false};
+    B = OperatorView{Wt, (uint64_t)d.rows_in, (uint64_t)d.ldWt, (uint64_t)d.ldWt, false, parts.op};
   VoxParams p;
   memset(&p, 0, sizeof p);
   const int per_in = d.c_in * d.n_in, per_out = d.c_out * d.n_out;
@@ -999,7 +1256,12 @@ cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const
   p.m_tiles = (int)((n_vox + 127) / 128);
   p.n_vox = n_vox;
   p.ldy = ldy;
-  p.Y = reinterpret_cast<__nv_bfloat16*>(Y);
+  p.n_terms = parts.on() ? kSplitTerms : 1;
+  p.chunk_kb = parts.on() ? std::max(1, env_int("DELIMIT_F32_CHUNK_KB", kSplitChunkKb)) : (1 << 24);
+  if (parts.on())
+    p.Yf = reinterpret_cast<float*>(Y);
+  else
+    p.Y = reinterpret_cast<__nv_bfloat16*>(Y);
   p.bias = bias;
   p.err = err;
   // forward tiles are short in K and wide in output: stage the epilogue through TMA stores
@@ -1010,11 +1272,12 @@ cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const
 }
 
 cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* dX, int64_t n_vox, int64_t lddy,
-                         int64_t lddx, int* err, cudaStream_t st) {
-  TraceScope trace("lsc_dgrad_gemm", st);
+                         int64_t lddx, int* err, cudaStream_t st, TcParts parts) {
+  TraceScope trace(parts.on() ? "lsc_dgrad_gemm_f32" : "lsc_dgrad_gemm", st);
   CUtensorMap ma;
-  if (!make_map(&ma, dY, (uint64_t)n_vox, (uint64_t)d.rows_out, (uint64_t)lddy, 64, kBK)) return cudaErrorInvalidValue;
-  const OperatorView B{W, (uint64_t)d.rows_out, (uint64_t)d.ldW, (uint64_t)d.ldW, false};
+  if (!make_map(&ma, dY, (uint64_t)n_vox, (uint64_t)d.rows_out, (uint64_t)lddy, 64, kBK, parts.act))
+    return cudaErrorInvalidValue;
+  const OperatorView B{W, (uint64_t)d.rows_out, (uint64_t)d.ldW, (uint64_t)d.ldW, false, parts.op};
   VoxParams p;
   memset(&p, 0, sizeof p);
   const int per_in = d.c_in * d.n_in, per_out = d.c_out * d.n_out;
@@ -1032,17 +1295,22 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* 
   p.m_tiles = (int)((n_vox + 127) / 128);
   p.n_vox = n_vox;
   p.ldy = lddx;
-  p.Y = reinterpret_cast<__nv_bfloat16*>(dX);
+  p.n_terms = parts.on() ? kSplitTerms : 1;
+  p.chunk_kb = parts.on() ? std::max(1, env_int("DELIMIT_F32_CHUNK_KB", kSplitChunkKb)) : (1 << 24);
+  if (parts.on())
+    p.Yf = reinterpret_cast<float*>(dX);
+  else
+    p.Y = reinterpret_cast<__nv_bfloat16*>(dX);
   p.bias = nullptr;
   p.err = err;
   return run_vox(ma, B, p, env_int("DELIMIT_DGRAD_BN", pick_bn(Ns, d.s_in)),
                  env_int("DELIMIT_DGRAD_STAGED", 0) != 0, gemm_cluster(2), dX, lddx, st);
 }
 
-template <int BN, int S, int CL>
+template <int BN, int S, int CL, bool SPLIT>
 cudaError_t launch_wgrad(const CUtensorMap& ma, const CUtensorMap& mb, const WgParams& p, cudaStream_t st) {
   const size_t smem = smem_bytes<BN, S>(128 * 128, BN / CL * 128);
-  auto kern = wgrad_kernel<BN, S, CL>;
+  auto kern = wgrad_kernel<BN, S, CL, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = launch_persistent(kern, p.total_tiles, CL, smem, st, ma, mb, p);
@@ -1051,12 +1319,15 @@ cudaError_t launch_wgrad(const CUtensorMap& ma, const CUtensorMap& mb, const WgP
 }
 
 cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float* P, int64_t ldp, int64_t split_stride,
-                         int splits, int64_t vps, int64_t n_vox, int64_t lddy, int64_t ldx, int* err, cudaStream_t st) {
+                         int splits, int64_t vps, int64_t n_vox, int64_t lddy, int64_t ldx, int* err, cudaStream_t st,
+                         TcParts parts, const void* dY_sum, int64_t lddy_sum) {
   constexpr int BN = kWgradBN;
   const int cl = gemm_cluster(2);
   CUtensorMap ma, mb;
-  if (!make_map(&ma, dY, (uint64_t)n_vox, (uint64_t)d.rows_out, (uint64_t)lddy, 64, 128)) return cudaErrorInvalidValue;
-  if (!make_map(&mb, X, (uint64_t)n_vox, (uint64_t)d.rows_in, (uint64_t)ldx, 64, BN / cl)) return cudaErrorInvalidValue;
+  if (!make_map(&ma, dY, (uint64_t)n_vox, (uint64_t)d.rows_out, (uint64_t)lddy, 64, 128, parts.act))
+    return cudaErrorInvalidValue;
+  if (!make_map(&mb, X, (uint64_t)n_vox, (uint64_t)d.rows_in, (uint64_t)ldx, 64, BN / cl, parts.act2))
+    return cudaErrorInvalidValue;
   if (vps % 64 != 0) return cudaErrorInvalidValue;
   WgParams p;
   memset(&p, 0, sizeof p);
@@ -1074,27 +1345,40 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
     p.tiles_per_split += (int64_t)G.m_tiles * G.n_tiles;
   }
   p.n_groups = d.s_out;
+  p.n_terms = parts.on() ? kSplitTerms : 1;
+  p.chunk_kb = parts.on() ? std::max(1, env_int("DELIMIT_F32_CHUNK_KB", kSplitChunkKb)) : (1 << 24);
   p.splits = splits;
   p.total_tiles = p.tiles_per_split * splits;
   p.vps = vps;
   p.n_vox = n_vox;
   p.ldp = ldp;
   p.split_stride = split_stride;
+  p.p_rs = parts.on() ? 1 : ldp;
+  p.p_cs = parts.on() ? ldp : 1;
   p.P = P;
   p.err = err;
   cudaError_t e = cudaSuccess;
   if (p.total_tiles > 0) {
-    TraceScope trace("lsc_wgrad_gemm", st);
+    TraceScope trace(parts.on() ? "lsc_wgrad_gemm_f32" : "lsc_wgrad_gemm", st);
     // stages: 4 x 46 KiB for one CTA, 7 x 31 KiB per CTA of a pair
-    e = cl > 1 ? launch_wgrad<BN, 7, 2>(ma, mb, p, st) : launch_wgrad<BN, 4, 1>(ma, mb, p, st);
+    if (parts.on())
+      e = cl > 1 ? launch_wgrad<BN, 7, 2, true>(ma, mb, p, st) : launch_wgrad<BN, 4, 1, true>(ma, mb, p, st);
+    else
+      e = cl > 1 ? launch_wgrad<BN, 7, 2, false>(ma, mb, p, st) : launch_wgrad<BN, 4, 1, false>(ma, mb, p, st);
     if (e != cudaSuccess) return e;
   }
   // bias-gradient column: row sums of dY per split (a separate HBM-bound pass; an extra
   // N = 16 MMA per step inside the GEMM measured slower, each MMA re-reads the A tile)
   const int64_t warps = d.rows_out * splits;
   TraceScope trace_rs("lsc_rowsum", st);
-  { rowsum_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
-      reinterpret_cast<const __nv_bfloat16*>(dY), lddy, d.rows_out, n_vox, vps, splits, P, ldp, split_stride, d.rows_in); count_launch(); }
+  const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+  if (parts.on())
+    rowsum_kernel<float><<<blocks, 256, 0, st>>>(reinterpret_cast<const float*>(dY_sum), lddy_sum, d.rows_out, n_vox,
+                                                 vps, splits, P, 1, split_stride, d.rows_in * ldp);
+  else
+    rowsum_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(dY), lddy, d.rows_out,
+                                                         n_vox, vps, splits, P, ldp, split_stride, d.rows_in);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -28,22 +28,43 @@ bool tc_transform_supported(const TcBasisTables& t, int kind, int64_t ldx, int64
 cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X, void* Y, int64_t n_vox, int C,
                                 int64_t ldx, int64_t ldy, int out_t, int* err_word, cudaStream_t st);
 
-// LSC GEMMs (BF16 activations, FP32 accumulation in TMEM)
+// LSC GEMMs (BF16 activations, FP32 accumulation in TMEM).
+// FP32 activations: every operand is passed as three BF16 parts (split_bf16x3), part p
+// at base + p * stride elements (TcParts: stride of the activation operand `act`, of
+// the operator `op`), the GEMM accumulates the six leading part products, and the
+// outputs of the forward and input-gradient GEMMs are FP32.  TcParts{} = BF16 operands.
+struct TcParts {
+  int64_t act = 0, op = 0, act2 = 0;  // act2: the weight gradient's second activation (X)
+  bool on() const { return act != 0; }
+};
 bool tc_gemm_supported(const LscDims& d, int64_t n_vox, int64_t ld_in, int64_t ld_out);
 // Y[(s,co,a), v] = sum_{k in win(s)} Wt[k][s*out_blk + (co,a)] X[k, v] + bias[(s,co,a)]
 // (= sum_k W[(s,co,a)][k] X[k, v]).  When tc_forward_reads_w(d) (no per-shell column
 // padding in W) the kernel reads W as a K-major operator and Wt may be absent.
 bool tc_forward_reads_w(const LscDims& d);
 cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const void* Wt, const float* bias, void* Y,
-                           int64_t n_vox, int64_t ldx, int64_t ldy, int* err_word, cudaStream_t st);
+                           int64_t n_vox, int64_t ldx, int64_t ldy, int* err_word, cudaStream_t st,
+                           TcParts parts = TcParts{});
 // dX[(s',ci,b), v] = sum_{k in rwin(s')} W[k][s'*in_blk + (ci,b)] dY[k, v]
 cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* dX, int64_t n_vox, int64_t lddy,
-                         int64_t lddx, int* err_word, cudaStream_t st);
+                         int64_t lddx, int* err_word, cudaStream_t st, TcParts parts = TcParts{});
 // P[split][(s,co,a)][(s',ci,b)] = sum_{v in split} dY[(s,co,a), v] X[(s',ci,b), v] for s' in win(s),
-// P[split][(s,co,a)][rows_in] = sum_{v in split} dY[(s,co,a), v]
+// P[split][(s,co,a)][rows_in] = sum_{v in split} dY[(s,co,a), v] (from dY_sum: the BF16 dY, or
+// the FP32 dY when the operands are split; lddy_sum its row stride).  With split operands
+// the partials are stored transposed, P[split][col][row] with leading dimension ldp (the
+// row sums in row rows_in); sum_transposed_partials brings them back.
 cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float* P, int64_t ldp, int64_t split_stride,
                          int splits, int64_t vox_per_split, int64_t n_vox, int64_t lddy, int64_t ldx, int* err_word,
-                         cudaStream_t st);
+                         cudaStream_t st, TcParts parts = TcParts{}, const void* dY_sum = nullptr,
+                         int64_t lddy_sum = 0);
+// P[r * ldp + c] = sum_z PT[z * split_stride + c * ldpt + r] for r < rows, c < cols
+cudaError_t sum_transposed_partials(const float* PT, int64_t ldpt, int64_t split_stride, int splits, int64_t rows,
+                                    int64_t cols, float* P, int64_t ldp, cudaStream_t st);
+// out[p * part_stride + r * ldo + c] = part p of x[r * ldx + c] (x = x0 + x1 + x2, each part the
+// BF16 rounding of what the earlier parts leave), for r < rows, c < cols; columns [cols, ldo)
+// of every part row are zeroed.  ldx a multiple of 4, ldo of 8, both pointers 16-byte aligned.
+cudaError_t split_bf16x3(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* out, int64_t ldo,
+                         int64_t part_stride, cudaStream_t st);
 
 // process-wide switch (default on): when off every BF16 step runs on the CUDA-core kernels
 void tc_set_enabled(bool on);

@@ -2,8 +2,9 @@
 
 All calls go through the C ABI.  FP32 path: relative L2 <= 1e-5 per output;
 BF16 path (bf16 activations, fp32 accumulation, fp32 master weights): <= 1e-2.
-Both the tensor-core and the CUDA-core BF16 kernels are checked, the former
-with and without two-CTA clusters (odd voxel-tile and row-tile counts included).
+Both precisions run on the tensor cores (FP32 as three-part BF16 splits with six
+part products) and on the CUDA cores; the tensor-core GEMMs with and without
+two-CTA clusters (odd voxel-tile and row-tile counts included).
 """
 import numpy as np
 import pytest
@@ -74,11 +75,12 @@ def _gpu_lsc(lg, c, w, b, d, ci, co, prec):
             rows_to_sh(din.float().cpu().numpy(), lg.s_in, ci, lg.n_in), dw.cpu().numpy(), db.cpu().numpy())
 
 
-@pytest.mark.parametrize("prec,tc,cluster", [("f32", False, 2), ("bf16", True, 2), ("bf16", True, 1),
-                                             ("bf16", False, 2)])
+@pytest.mark.parametrize("prec,tc,cluster", [("f32", False, 2), ("f32", True, 2), ("f32", True, 1),
+                                             ("bf16", True, 2), ("bf16", True, 1), ("bf16", False, 2)])
 @pytest.mark.parametrize("case", list(CASES))
 def test_lsc_vs_oracle(case, prec, tc, cluster, monkeypatch):
-    # cluster: CTAs per cluster of the tensor-core GEMMs (2 = operator tiles multicast)
+    # cluster: CTAs per cluster of the tensor-core GEMMs (2 = CTA pairs with 2-SM MMAs);
+    # f32 with tc: FP32 activations through three-part BF16 splits on the tensor cores
     monkeypatch.setenv("DELIMIT_GEMM_CLUSTER", str(cluster))
     cfg = CASES[case]
     og, lg = _setup(cfg)
@@ -108,12 +110,14 @@ FULL = {
 }
 
 
-@pytest.mark.parametrize("variant", list(FULL))
-def test_lsc_full_size_sampled(variant):
+@pytest.mark.parametrize("variant,prec", [("adjacent", "bf16"), ("mixed_all", "bf16"), ("adjacent", "f32")])
+def test_lsc_full_size_sampled(variant, prec):
     """65,536 voxels, 3 x 90 directions, 16 -> 64 channels, radius 25 deg, 4 x 12 kernel,
-    BF16 on tensor cores.  Forward and input gradient are checked on 64 sampled voxels
-    against the oracle; the weight and bias gradients through identities that hold at
-    any size and against the oracle on a 512-voxel launch."""
+    on the tensor cores (BF16, or FP32 through split operands).  Forward and input
+    gradient are checked on 64 sampled voxels against the oracle; the weight and bias
+    gradients through identities that hold at any size and against the oracle on a
+    512-voxel launch."""
+    tol = TOL[prec]
     cfg = dict(m=[90, 90, 90], b=[1000, 2000, 3000], order_out=8, lam=0.006, V=65536, ci=16, co=64,
                rad=25, R=4, Sec=12, **FULL[variant])
     og, lg = _setup(cfg, seed=1808)
@@ -122,24 +126,35 @@ def test_lsc_full_size_sampled(variant):
     w = synth.gaussian((64, 3, 16, 3, 49), 0.1, seed=6)
     b = synth.gaussian((64, 3), 0.1, seed=7)
     d = synth.gaussian((V, 64, 3, n_out), 1.0, seed=8, tag="grads").astype(np.float32)
-    y, din, dw, db = _gpu_lsc(lg, c, w, b, d, 16, 64, "bf16")
+    y, din, dw, db = _gpu_lsc(lg, c, w, b, d, 16, 64, prec)
     idx = synth.voxel_subset(V, 64)
     ref_y = og.forward(c[idx].astype(np.float64), w, b)
     ref_din, _, _ = og.backward(c[idx].astype(np.float64), w, d[idx].astype(np.float64))
-    assert rel_l2(y[idx], ref_y) <= TOL_BF16
-    assert rel_l2(din[idx], ref_din) <= TOL_BF16
+    assert rel_l2(y[idx], ref_y) <= tol
+    assert rel_l2(din[idx], ref_din) <= tol
+    # dw of sampled channel pairs over all voxels: the oracle's collapse matrices applied to
+    # G = sum_v d[v, co, s, :] c[v, ci, s', :]^T (FP64), i.e. dw = sum_ab M_{s,s'}[k] * G
+    rng = np.random.default_rng(3)
+    got_s, ref_s = [], []
+    for _ in range(6):
+        co, ci, s = int(rng.integers(64)), int(rng.integers(16)), int(rng.integers(3))
+        sp = int(rng.choice(np.flatnonzero(og.win[s])))
+        G = d[:, co, s, :].astype(np.float64).T @ c[:, ci, sp, :].astype(np.float64)
+        ref_s.append(np.einsum("kab,ab->k", og.pair_mats(s, sp), G))
+        got_s.append(dw[co, s, ci, sp])
+    assert rel_l2(np.array(got_s), np.array(ref_s)) <= tol
     # db = sum over voxels of P_out-weighted upstream gradient, a plain reduction
     q = og.collapse_mats()[1]
     ref_db = np.stack([np.einsum("vcx,x->c", d[:, :, s, :].astype(np.float64), q[s]) for s in range(3)], 1)
-    assert rel_l2(db, ref_db) <= TOL_BF16
+    assert rel_l2(db, ref_db) <= tol
     # <dw, w'> = <d, LSC(c; w', b = 0)> for a random w' (linearity in w), here with the
     # oracle evaluated on a 512-voxel launch of the same kernels
     sub = synth.voxel_subset(V, 512)
     w2 = synth.gaussian(w.shape, 0.1, seed=9) * og.win[None, :, None, :, None]
-    _, _, dw_sub, _ = _gpu_lsc(lg, c[sub], w, b, d[sub], 16, 64, "bf16")
+    _, _, dw_sub, _ = _gpu_lsc(lg, c[sub], w, b, d[sub], 16, 64, prec)
     lhs = float(np.sum(dw_sub * w2))
     rhs = float(np.sum(d[sub].astype(np.float64) * og.forward(c[sub].astype(np.float64), w2, np.zeros_like(b))))
-    assert abs(lhs - rhs) <= TOL_BF16 * np.linalg.norm(dw_sub) * np.linalg.norm(w2) * 4
+    assert abs(lhs - rhs) <= tol * np.linalg.norm(dw_sub) * np.linalg.norm(w2) * 4
     assert np.isfinite(dw).all() and np.linalg.norm(dw) > 0
 
 
@@ -167,20 +182,22 @@ def test_lsc_zero_voxels_and_workspace_errors():
     assert st == L.ERR_ALIGNMENT
 
 
-@pytest.mark.parametrize("tc", [True, False])
-def test_backward_reuses_forward_operator(tc):
+@pytest.mark.parametrize("prec,tc,case", [("bf16", True, "adjacent"), ("bf16", False, "adjacent"),
+                                          ("f32", True, "adjacent"), ("f32", True, "all_mixed")])
+def test_backward_reuses_forward_operator(prec, tc, case):
     """A backward flagged OPERATOR_READY on the forward's workspace gives the same
-    bits as a backward that rebuilds the collapsed operator itself."""
-    cfg = CASES["adjacent"]
+    bits as a backward that rebuilds the collapsed operator itself (for FP32 on the
+    tensor cores including its split parts; all_mixed reads Wt in the forward)."""
+    cfg = CASES[case]
     og, lg = _setup(cfg)
     c, w, b, d = _inputs(og, cfg, seed=5)
     ci, co = cfg["ci"], cfg["co"]
-    x = _dev(sh_to_rows(c), torch.bfloat16)
-    g = _dev(sh_to_rows(d), torch.bfloat16)
+    x = _dev(sh_to_rows(c), DT[prec])
+    g = _dev(sh_to_rows(d), DT[prec])
     wt, bt = torch.from_numpy(w).float().cuda(), torch.from_numpy(b).float().cuda()
     L.set_tensor_cores(tc)
     try:
-        ws = layers.lsc_workspace(lg, x.shape[1], ci, co, torch.bfloat16, True)
+        ws = layers.lsc_workspace(lg, x.shape[1], ci, co, DT[prec], True)
         layers.lsc_forward(lg, x, wt, bt, ci, co, workspace=ws)
         got = layers.lsc_backward(lg, x, wt, g, ci, co, workspace=ws, operator_ready=True)
         ref = layers.lsc_backward(lg, x, wt, g, ci, co)

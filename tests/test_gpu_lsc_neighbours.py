@@ -1,7 +1,7 @@
 """GPU parity of the resampling-free LSC (acquired neighbours binned to kernel points,
 DELIMIT_LSC_NEIGHBOURS) against the FP64 oracle: forward, input gradient, weight and
-bias gradients through the C ABI, on the CUDA-core FP32 path and the BF16 paths
-(tensor cores with and without two-CTA clusters, CUDA cores); the 65,536-voxel
+bias gradients through the C ABI, in FP32 (tensor cores through split operands, CUDA
+cores) and BF16 (tensor cores with and without two-CTA clusters, CUDA cores); the 65,536-voxel
 configuration on sampled voxels; and the layer with ``resample=False``."""
 import numpy as np
 import pytest
@@ -39,8 +39,8 @@ def _setup(cfg, seed=11):
     return og, lg, dirs, bvals
 
 
-@pytest.mark.parametrize("prec,tc,cluster", [("f32", False, 2), ("bf16", True, 2), ("bf16", True, 1),
-                                             ("bf16", False, 2)])
+@pytest.mark.parametrize("prec,tc,cluster", [("f32", False, 2), ("f32", True, 2), ("bf16", True, 2),
+                                             ("bf16", True, 1), ("bf16", False, 2)])
 @pytest.mark.parametrize("case", list(CASES))
 def test_resampling_free_lsc_vs_oracle(case, prec, tc, cluster, monkeypatch):
     monkeypatch.setenv("DELIMIT_GEMM_CLUSTER", str(cluster))
