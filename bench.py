@@ -34,16 +34,16 @@ UNIT = "voxels/s"
 # single-pass ncu capture of the bench command summarised in
 # profiles/chain_65536vox_launch_list.md (the `dram__bytes_*` metrics); valid only
 # while the kernel's sources hash to the value recorded with the capture.
-_GEMM = ("csrc/tc_gemm.cu", "csrc/tc_ptx.cuh"), "3054bf3a20325923"
-_TF = ("csrc/tc_transform.cu", "csrc/tc_ptx.cuh"), "baa7f0e78928ced7"
+_GEMM = ("csrc/tc_gemm.cu", "csrc/tc_ptx.cuh"), "4f0b3c921350fb3e"
+_TF = ("csrc/tc_transform.cu", "csrc/tc_ptx.cuh"), "baafb4dbdc087304"
 NCU_TRAFFIC = {
-    "lsc_fwd_gemm": {"bytes": 1.631e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
-    "lsc_dgrad_gemm": {"bytes": 2.344e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
-    "lsc_wgrad_gemm": {"bytes": 3.377e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
-    "signal2sh_tc": {"bytes": 0.8132e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
+    "lsc_fwd_gemm": {"bytes": 1.608e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "lsc_dgrad_gemm": {"bytes": 2.321e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "lsc_wgrad_gemm": {"bytes": 3.502e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "signal2sh_tc": {"bytes": 0.8134e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
     "sh2signal_tc": {"bytes": 3.333e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
     "sh2signal_bwd_tc": {"bytes": 3.358e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
-    "signal2sh_bwd_tc": {"bytes": 0.7845e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
+    "signal2sh_bwd_tc": {"bytes": 0.7847e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
 }
 
 
@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip fp32 / e2e / cpu / transform legs (profiling runs)")
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "f32"],
+                    help="activations of the timed chain (f32: the split-operand tensor-core path)")
     ap.add_argument("--transform-vox", type=int, default=1 << 20,
                     help="voxels of the stand-alone transform leg (one channel, 3 x 90 directions)")
     return ap.parse_args()
@@ -357,8 +359,9 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
     V = cfg.n_vox
-    ch = Chain(cfg, dirs, bvals, torch.bfloat16)
-    s_in, ds_out, w, b = chain_inputs(cfg, dirs, bvals, torch.bfloat16, rank)
+    act = torch.float32 if args.precision == "f32" else torch.bfloat16
+    ch = Chain(cfg, dirs, bvals, act)
+    s_in, ds_out, w, b = chain_inputs(cfg, dirs, bvals, act, rank)
     ch.set_inputs(s_in, ds_out, w, b)
     del s_in, ds_out
     torch.cuda.synchronize()
@@ -425,8 +428,13 @@ def main():
     for v in kernels.values():
         v["share"] = v["avg_ms"] * v["launches"] / tot
     dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
-    tensor_bound = dom.endswith("_gemm")
-    if tensor_bound:
+    tensor_bound = "_gemm" in dom
+    if tensor_bound and dom.endswith("_f32"):
+        # six BF16 part products per FP32 product: the split path's ceiling is a sixth of BF16's
+        roofline = {"bound": "tensor", "achieved": kernels[dom]["tflops"], "peak": tf_sust / 6, "unit": "TFLOP/s",
+                    "frac": kernels[dom]["tflops"] / (tf_sust / 6),
+                    "peak_source": f"{peak_src} bf16_tflops_sustained / 6 (six BF16 products per FP32 product)"}
+    elif tensor_bound:
         roofline = {"bound": "tensor", "achieved": kernels[dom]["tflops"], "peak": tf_sust, "unit": "TFLOP/s",
                     "frac": kernels[dom]["tflops"] / tf_sust, "peak_source": f"{peak_src} bf16_tflops_sustained"}
     else:
@@ -437,7 +445,7 @@ def main():
     roofline["step_frac_of_tensor_peak"] = roofline["step_tflops"] / tf_sust
 
     extras = {}
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and not args.no_extras and args.precision == "bf16":
         # ---- accuracy on sampled voxels vs the FP64 oracle ----
         idx = synth.voxel_subset(V, 32, seed=cfg.seed + 99)
         extras["err_vs_oracle_bf16"] = sampled_errors(ch, cfg, dirs, bvals, idx)
@@ -461,7 +469,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": cfg.name(), "n_vox": V, "shells": list(cfg.dirs_per_shell),
                            "sh_order": cfg.order, "c_in": cfg.c_in, "c_out": cfg.c_out, "kernel_points": ch.geom.K,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},

@@ -147,7 +147,7 @@ class Chain:
         wbytes = 2.0 * e * r["c_out"] * r["c_in"]
         fl = self.flops()
         by = self.bytes()
-        return {
+        out = {
             "lsc_fwd_gemm": (gemm, e * V * (r["c_in"] + r["c_out"])),
             "lsc_dgrad_gemm": (gemm, e * V * (r["c_out"] + r["c_in"])),
             "lsc_wgrad_gemm": (gemm, e * V * (r["c_out"] + r["c_in"])),
@@ -158,7 +158,13 @@ class Chain:
             "sh2signal_tc": (fl["sh2signal"], by["sh2signal"]),
             "sh2signal_bwd_tc": (fl["sh2signal_backward"], by["sh2signal_backward"]),
             "signal2sh_bwd_tc": (fl["signal2sh_backward"], by["signal2sh_backward"]),
+            "split_bf16x3": (0.0, 0.0),
+            "lsc_wgrad_f32_sum": (0.0, 0.0),
         }
+        # FP32 activations: the same algorithmic work through the split-operand GEMMs
+        for k in ("lsc_fwd_gemm", "lsc_dgrad_gemm", "lsc_wgrad_gemm"):
+            out[k + "_f32"] = out[k]
+        return out
 
     def bytes(self) -> dict:
         """Compulsory HBM bytes per call (activations read + written once)."""
