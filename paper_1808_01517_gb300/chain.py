@@ -159,7 +159,6 @@ class Chain:
             "sh2signal_bwd_tc": (fl["sh2signal_backward"], by["sh2signal_backward"]),
             "signal2sh_bwd_tc": (fl["signal2sh_backward"], by["signal2sh_backward"]),
             "split_bf16x3": (0.0, 0.0),
-            "lsc_wgrad_f32_sum": (0.0, 0.0),
         }
         # FP32 activations: the same algorithmic work through the split-operand GEMMs
         for k in ("lsc_fwd_gemm", "lsc_dgrad_gemm", "lsc_wgrad_gemm"):

@@ -93,6 +93,7 @@ struct delimit_lsc_geometry {
   int device = -1;
   float* d_mem = nullptr;
   const float* d_M = nullptr;  // [S_out][K][N_out][N_in]; resampling-free form [S_out][S_in][K][N_out][N_in]
+  const float* d_Mt = nullptr;  // the same with [N_in][N_out] per kernel point (transposed)
   const float* d_q = nullptr;  // [S_out][N_out]
   int* err_word = nullptr;
   LscDims dims_template;  // without channel counts
@@ -447,11 +448,17 @@ delimit_status delimit_lsc_geometry_create(const delimit_sh_basis* ob, int order
     }
     g->err_word = error_word_for_current_device();
     // M and q of all output shells, packed densely for the kernels
-    std::vector<double> Mall, qall;
+    std::vector<double> Mall, Mtall, qall;
     for (auto& s : g->h.shells) Mall.insert(Mall.end(), s.M.begin(), s.M.end());
     for (auto& s : g->h.shells) qall.insert(qall.end(), s.q.begin(), s.q.end());
+    // Mt: every [N_out][N_in] block of M transposed (the weight-gradient reduction reads it)
+    const size_t blk = size_t(d.n_out) * d.n_in;
+    Mtall.resize(Mall.size());
+    for (size_t o = 0; o < Mall.size(); o += blk)
+      for (int a = 0; a < d.n_out; ++a)
+        for (int b = 0; b < d.n_in; ++b) Mtall[o + size_t(b) * d.n_out + a] = Mall[o + size_t(a) * d.n_in + b];
     Uploader dense;
-    const size_t om = dense.add(Mall), oqq = dense.add(qall);
+    const size_t om = dense.add(Mall), omt = dense.add(Mtall), oqq = dense.add(qall);
     e = cudaMalloc(&g->d_mem, dense.host.size() * sizeof(float));
     if (e != cudaSuccess) {
       delete g;
@@ -464,6 +471,7 @@ delimit_status delimit_lsc_geometry_create(const delimit_sh_basis* ob, int order
       return cuda_fail(e, "cudaMemcpy geometry");
     }
     g->d_M = g->d_mem + om;
+    g->d_Mt = g->d_mem + omt;
     g->d_q = g->d_mem + oqq;
     g->on_device = true;
   }
@@ -570,7 +578,7 @@ struct LscPlan {
   // FP32 activations on the tensor cores: three-part BF16 splits of the operator (W3,
   // and Wt3 when the forward reads Wt), of the LSC input (X3) and of dY (dY3); parts of
   // an activation are ld3-strided rows, ld3 = n_vox rounded up to 8
-  size_t off_W3, off_Wt3, off_X3, off_dY3, off_Psum;
+  size_t off_W3, off_Wt3, off_X3, off_dY3;
   int64_t ld3, ldpt;  // ldpt: leading dimension of the transposed weight-gradient partials
   int splits;
   int64_t vox_per_split;
@@ -643,14 +651,12 @@ bool make_plan(const delimit_lsc_geometry* g, int64_t n_vox, int c_in, int c_out
   p.total_fwd = p.off_X3 + (f32 ? align_up(3 * size_t(p.d.rows_in) * size_t(p.ld3) * 2, 256) : 0);
   p.splits = wgrad_splits(p.d, std::max<int64_t>(n_vox, 1), &p.vox_per_split);
   p.off_P = p.total_fwd;
-  // FP32: the partials are written transposed (columns of ldpt floats) and summed into Psum
+  // tensor-core weight gradient: partials written transposed (columns of ldpt floats)
   p.ldpt = (p.d.rows_out + 3) / 4 * 4;
-  const size_t p_elems = std::max(size_t(p.d.rows_out) * size_t(p.d.rows_in + 1),
-                                  f32 ? size_t(p.d.rows_in + 1) * size_t(p.ldpt) : size_t(0));
+  const size_t p_elems = std::max(size_t(p.d.rows_out) * size_t(p.d.rows_in + 1), size_t(p.d.rows_in + 1) * size_t(p.ldpt));
   p.off_dwp = p.off_P + align_up(size_t(p.splits) * p_elems * 4, 256);
   p.off_dY3 = p.off_dwp + align_up(reduce_dw_scratch_floats(p.d) * 4, 256);
-  p.off_Psum = p.off_dY3 + (f32 ? align_up(3 * size_t(p.d.rows_out) * size_t(p.ld3) * 2, 256) : 0);
-  p.total_bwd = p.off_Psum + (f32 ? align_up(size_t(p.d.rows_out) * size_t(p.d.rows_in + 1) * 4, 256) : 0);
+  p.total_bwd = p.off_dY3 + (f32 ? align_up(3 * size_t(p.d.rows_out) * size_t(p.ld3) * 2, 256) : 0);
   p.tc = false;
   return true;
 }
@@ -850,7 +856,7 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
     float* P = reinterpret_cast<float*>(base + p.off_P);
     const int64_t ldp = d.rows_in + 1;
     int64_t split_stride = d.rows_out * ldp;
-    int splits = p.splits;
+    int64_t p_rs = ldp, p_cs = 1;  // row layout (CUDA-core path); the tensor-core path's is transposed
     if (split) {
       void* X3 = base + p.off_X3;
       e = split_bf16x3(static_cast<const float*>(sh_in), d.rows_in, n_vox, ld_in, X3, p.ld3, d.rows_in * p.ld3, cs);
@@ -862,16 +868,17 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
       e = tc_lsc_wgrad(d, dY3, X3, P, p.ldpt, ss_t, p.splits, p.vox_per_split, n_vox, p.ld3, p.ld3, g->err_word, cs,
                        parts, d_out, ld_out);
       if (e != cudaSuccess) return cuda_fail(e, "tensor-core FP32 LSC weight-gradient launch");
-      float* Psum = reinterpret_cast<float*>(base + p.off_Psum);
-      e = sum_transposed_partials(P, p.ldpt, ss_t, p.splits, d.rows_out, ldp, Psum, ldp, cs);
-      if (e != cudaSuccess) return cuda_fail(e, "weight-gradient partial sum launch");
-      P = Psum;
-      split_stride = 0;
-      splits = 1;
+      p_rs = 1;
+      p_cs = p.ldpt;
+      split_stride = ss_t;
     } else if (act_t == DELIMIT_BF16 && tc) {
-      e = tc_lsc_wgrad(d, d_out, sh_in, P, ldp, split_stride, p.splits, p.vox_per_split, n_vox, ld_out, ld_in,
+      const int64_t ss_t = ldp * p.ldpt;  // transposed partials: rows_in + 1 columns of ldpt floats
+      e = tc_lsc_wgrad(d, d_out, sh_in, P, p.ldpt, ss_t, p.splits, p.vox_per_split, n_vox, ld_out, ld_in,
                        g->err_word, cs);
       if (e != cudaSuccess) return cuda_fail(e, "tensor-core LSC weight-gradient launch");
+      p_rs = 1;
+      p_cs = p.ldpt;
+      split_stride = ss_t;
     } else {
       WgradArgs a;
       std::memset(&a, 0, sizeof a);
@@ -898,7 +905,7 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
       e = launch_wgrad_simt(a, d.s_out, per_out, maxN, p.splits, int(act_t), cs);
       if (e != cudaSuccess) return cuda_fail(e, "LSC weight-gradient launch");
     }
-    e = launch_reduce_dw(d, P, ldp, split_stride, splits, g->d_M, g->d_q, dw, db,
+    e = launch_reduce_dw(d, P, p_rs, p_cs, split_stride, p.splits, g->d_M, g->d_Mt, g->d_q, dw, db,
                          reinterpret_cast<float*>(base + p.off_dwp), cs);
     if (e != cudaSuccess) return cuda_fail(e, "dw/db reduction launch");
   }

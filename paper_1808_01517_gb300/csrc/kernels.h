@@ -101,8 +101,12 @@ cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int m
 // dw[co,s,ci,s',k] = sum_{a,b} M[s][k][a][b] sum_split P[split][(s,co,a)][(s',ci,b)];  db[co,s] = sum_a q[s][a] rowsum
 // scratch: reduce_dw_scratch_floats(d) floats of partial sums
 size_t reduce_dw_scratch_floats(const LscDims& d);
-cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int64_t split_stride, int splits,
-                             const float* M, const float* q, float* dw, float* db, float* scratch, cudaStream_t st);
+// P element (row r, column c) of split z at z * split_stride + r * p_rs + c * p_cs; with
+// p_rs == 1 (transposed partials of the tensor-core weight gradient) the kernel reads Mt,
+// M with a and b swapped per kernel point, so that both streams stay coalesced.
+cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t p_rs, int64_t p_cs, int64_t split_stride,
+                             int splits, const float* M, const float* Mt, const float* q, float* dw, float* db,
+                             float* scratch, cudaStream_t st);
 
 // sets the thread-local message returned by delimit_last_error()
 void set_last_error(const std::string& msg);

@@ -673,8 +673,12 @@ cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int m
 // ---------------------------------------------------------------------------
 constexpr int kDwAbPart = 256;  // (a,b) entries per partial sum
 
+// TRANS: the partials are stored transposed (p_rs = 1): the (a,b) range is walked with a
+// fastest (ab = b * n_out + a, consecutive rows of P, coalesced) and M is read as Mt
+// (per kernel point [b][a]), in the same order.
+template <bool TRANS>
 __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ LscDims d, const float* __restrict__ P,
-                                                        int64_t ldp, int64_t split_stride, int splits,
+                                                        int64_t p_rs, int64_t p_cs, int64_t split_stride, int splits,
                                                         const float* __restrict__ M, float* __restrict__ dwp,
                                                         int64_t part_stride) {
   // block: 64 channel pairs x 64 kernel points x one (a,b) part; thread: 4 pairs x 4 points;
@@ -698,9 +702,10 @@ __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ 
         const int t = idx % AB, pp = idx / AB, pr = p0 + pp, ab = ab0 + t;
         float v = 0.f;
         if (pr < npairs && ab < ab_end) {
-          const int co = pr / d.c_in, ci = pr % d.c_in, aa = ab / d.n_in, bb = ab % d.n_in;
-          const int64_t off =
-              (((int64_t)s * d.c_out + co) * d.n_out + aa) * ldp + ((int64_t)sp * d.c_in + ci) * d.n_in + bb;
+          const int co = pr / d.c_in, ci = pr % d.c_in;
+          const int aa = TRANS ? ab % d.n_out : ab / d.n_in, bb = TRANS ? ab / d.n_out : ab % d.n_in;
+          const int64_t off = (((int64_t)s * d.c_out + co) * d.n_out + aa) * p_rs +
+                              (((int64_t)sp * d.c_in + ci) * d.n_in + bb) * p_cs;
           for (int z = 0; z < splits; ++z) v += P[z * split_stride + off];
         }
         gs[t][pp] = v;
@@ -746,15 +751,15 @@ __global__ void sum_parts_kernel(const float* __restrict__ dwp, int64_t part_str
   }
 }
 
-__global__ void reduce_db_kernel(const __grid_constant__ LscDims d, const float* __restrict__ P, int64_t ldp,
-                                 int64_t split_stride, int splits, int64_t ones_col, const float* __restrict__ q,
-                                 float* __restrict__ db) {
+__global__ void reduce_db_kernel(const __grid_constant__ LscDims d, const float* __restrict__ P, int64_t p_rs,
+                                 int64_t p_cs, int64_t split_stride, int splits, int64_t ones_col,
+                                 const float* __restrict__ q, float* __restrict__ db) {
   const int co = blockIdx.x, s = blockIdx.y;
   const int64_t row0 = ((int64_t)s * d.c_out + co) * d.n_out;
   float acc = 0.f;
   for (int aa = threadIdx.x; aa < d.n_out; aa += 32) {
     float r = 0.f;
-    for (int z = 0; z < splits; ++z) r += P[z * split_stride + (row0 + aa) * ldp + ones_col];
+    for (int z = 0; z < splits; ++z) r += P[z * split_stride + (row0 + aa) * p_rs + ones_col * p_cs];
     acc = fmaf(q[s * d.n_out + aa], r, acc);
   }
 #pragma unroll
@@ -767,15 +772,20 @@ size_t reduce_dw_scratch_floats(const LscDims& d) {
   return (size_t)nparts * d.c_out * d.s_out * d.c_in * d.s_in * d.K;
 }
 
-cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int64_t split_stride, int splits,
-                             const float* M, const float* q, float* dw, float* db, float* scratch, cudaStream_t st) {
+cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t p_rs, int64_t p_cs, int64_t split_stride,
+                             int splits, const float* M, const float* Mt, const float* q, float* dw, float* db,
+                             float* scratch, cudaStream_t st) {
   TraceScope trace("lsc_reduce_dw", st);
   if (dw) {
     const int nparts = (d.n_out * d.n_in + kDwAbPart - 1) / kDwAbPart;
     const int64_t n = (int64_t)d.c_out * d.s_out * d.c_in * d.s_in * d.K;
     dim3 grid((unsigned)((d.K + 63) / 64), (unsigned)((d.c_out * d.c_in + 63) / 64),
               (unsigned)(d.s_out * d.s_in * nparts));
-    { reduce_dw_kernel<<<grid, 256, 0, st>>>(d, P, ldp, split_stride, splits, M, scratch, n); count_launch(); }
+    if (p_rs == 1)
+      reduce_dw_kernel<true><<<grid, 256, 0, st>>>(d, P, p_rs, p_cs, split_stride, splits, Mt, scratch, n);
+    else
+      reduce_dw_kernel<false><<<grid, 256, 0, st>>>(d, P, p_rs, p_cs, split_stride, splits, M, scratch, n);
+    count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned g = (unsigned)std::min<int64_t>(4096, (n + 255) / 256);
@@ -784,7 +794,7 @@ cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t ldp, int6
     if (e != cudaSuccess) return e;
   }
   if (db) {
-    { reduce_db_kernel<<<dim3(d.c_out, d.s_out), 32, 0, st>>>(d, P, ldp, split_stride, splits, d.rows_in, q, db); count_launch(); }
+    { reduce_db_kernel<<<dim3(d.c_out, d.s_out), 32, 0, st>>>(d, P, p_rs, p_cs, split_stride, splits, d.rows_in, q, db); count_launch(); }
     return cudaGetLastError();
   }
   return cudaSuccess;

@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int i = 0; i < BN / 64; ++i) {
         const int w = lane + 32 * i, col = nt * BN + 32 * (w >> 4) + 16 * half + (w & 15);
-        breg[i] = (STAGED && PASSES == 1 && p.bias && col < G.N) ? __ldg(p.bias + G.y_row0 + col) : 0.f;
+        breg[i] = (PASSES == 1 && p.bias && col < G.N) ? __ldg(p.bias + G.y_row0 + col) : 0.f;
       }
       bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTmemFull);
       if (STAGED) ok = ok && wait_bounded(stg_free_bar, (uint32_t)((PASSES * it) & 1) ^ 1u, abort_flag, p.err, kErrTmemEmpty);
@@ -453,7 +453,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
           if (c == 0) {
-            for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
+            // compile-time column loops, so that the bias comes from registers (shuffled)
+#pragma unroll
+            for (int k0 = 0; k0 < BN / 32; k0 += 4) {
+              if (!(32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N)) break;
               uint32_t rv[4][16];
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
@@ -468,10 +471,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (c0 < BN && nbase < G.N) {
 #pragma unroll
                   for (int jj = 0; jj < 16; ++jj) {
+                    const int w = 16 * (k0 + u) + jj;
+                    const float bv = __shfl_sync(0xffffffffu, breg[(w >> 5) < BN / 64 ? (w >> 5) : 0], w & 31);
                     const int n = nbase + jj;
                     if (n < G.N && vok) {
                       const int64_t o = (G.y_row0 + n) * p.ldy + vox;
-                      const float v = __uint_as_float(rv[u][jj]) + (p.bias ? __ldg(p.bias + G.y_row0 + n) : 0.f);
+                      const float v = __uint_as_float(rv[u][jj]) + bv;
                       if constexpr (SPLIT)
                         p.Yf[o] = v;
                       else
@@ -763,7 +768,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mt = mt * CL + rank;
       const WgGroup& G = p.g[g];
       const int m = mt * 128 + q * 32 + lane;
-      const int64_t rs = SPLIT ? p.p_rs : p.ldp, cs = SPLIT ? p.p_cs : 1;
+      const int64_t rs = p.p_rs, cs = p.p_cs;
       float* prow = p.P + (int64_t)split * p.split_stride + (G.m_row0 + m) * rs + G.n_col0 * cs;
       const int64_t vs = (int64_t)split * p.vps, ve = min(p.n_vox, vs + p.vps);
       const int nch = SPLIT ? k_chunks((int)((ve - vs + 63) / 64), chunk_kb) : 1;
@@ -914,39 +919,6 @@ __global__ void __launch_bounds__(256) split3_kernel(const float* __restrict__ x
       }
     }
   }
-}
-
-// P[r * ldp + c] = sum over splits z (in order) of PT[z * split_stride + c * ldpt + r]: the
-// transposed weight-gradient partials of the FP32 path back in the row layout, summed.
-// 32 x 32 tiles through shared memory; reads and writes coalesced.
-__global__ void __launch_bounds__(256) sum_transpose_kernel(const float* __restrict__ PT, int64_t ldpt,
-                                                            int64_t split_stride, int splits, int64_t rows,
-                                                            int64_t cols, float* __restrict__ P, int64_t ldp) {
-  __shared__ float tile[32][33];
-  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  for (int i = ty; i < 32; i += 8) {
-    const int64_t c = c0 + i, r = r0 + tx;
-    float v = 0.f;
-    if (c < cols && r < rows)
-      for (int z = 0; z < splits; ++z) v += PT[z * split_stride + c * ldpt + r];
-    tile[i][tx] = v;
-  }
-  __syncthreads();
-  for (int i = ty; i < 32; i += 8) {
-    const int64_t r = r0 + i, c = c0 + tx;
-    if (r < rows && c < cols) P[r * ldp + c] = tile[tx][i];
-  }
-}
-
-cudaError_t sum_transposed_partials(const float* PT, int64_t ldpt, int64_t split_stride, int splits, int64_t rows,
-                                    int64_t cols, float* P, int64_t ldp, cudaStream_t st) {
-  if (rows <= 0 || cols <= 0) return cudaSuccess;
-  TraceScope trace("lsc_wgrad_f32_sum", st);
-  const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
-  sum_transpose_kernel<<<grid, 256, 0, st>>>(PT, ldpt, split_stride, splits, rows, cols, P, ldp);
-  count_launch();
-  return cudaGetLastError();
 }
 
 cudaError_t split_bf16x3(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* out, int64_t ldo,
@@ -1353,8 +1325,8 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
   p.n_vox = n_vox;
   p.ldp = ldp;
   p.split_stride = split_stride;
-  p.p_rs = parts.on() ? 1 : ldp;
-  p.p_cs = parts.on() ? ldp : 1;
+  p.p_rs = 1;  // transposed partials: a warp's lanes (consecutive rows) store 128 contiguous bytes
+  p.p_cs = ldp;
   p.P = P;
   p.err = err;
   cudaError_t e = cudaSuccess;
@@ -1377,7 +1349,7 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
                                                  vps, splits, P, 1, split_stride, d.rows_in * ldp);
   else
     rowsum_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(dY), lddy, d.rows_out,
-                                                         n_vox, vps, splits, P, ldp, split_stride, d.rows_in);
+                                                         n_vox, vps, splits, P, 1, split_stride, d.rows_in * ldp);
   count_launch();
   return cudaGetLastError();
 }

@@ -50,16 +50,13 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* 
                          int64_t lddx, int* err_word, cudaStream_t st, TcParts parts = TcParts{});
 // P[split][(s,co,a)][(s',ci,b)] = sum_{v in split} dY[(s,co,a), v] X[(s',ci,b), v] for s' in win(s),
 // P[split][(s,co,a)][rows_in] = sum_{v in split} dY[(s,co,a), v] (from dY_sum: the BF16 dY, or
-// the FP32 dY when the operands are split; lddy_sum its row stride).  With split operands
-// the partials are stored transposed, P[split][col][row] with leading dimension ldp (the
-// row sums in row rows_in); sum_transposed_partials brings them back.
+// the FP32 dY when the operands are split; lddy_sum its row stride).  The partials are
+// stored transposed, P[split][col][row] with leading dimension ldp >= rows_out (the row
+// sums in row rows_in), so that the epilogue's stores are coalesced.
 cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float* P, int64_t ldp, int64_t split_stride,
                          int splits, int64_t vox_per_split, int64_t n_vox, int64_t lddy, int64_t ldx, int* err_word,
                          cudaStream_t st, TcParts parts = TcParts{}, const void* dY_sum = nullptr,
                          int64_t lddy_sum = 0);
-// P[r * ldp + c] = sum_z PT[z * split_stride + c * ldpt + r] for r < rows, c < cols
-cudaError_t sum_transposed_partials(const float* PT, int64_t ldpt, int64_t split_stride, int splits, int64_t rows,
-                                    int64_t cols, float* P, int64_t ldp, cudaStream_t st);
 // out[p * part_stride + r * ldo + c] = part p of x[r * ldx + c] (x = x0 + x1 + x2, each part the
 // BF16 rounding of what the earlier parts leave), for r < rows, c < cols; columns [cols, ldo)
 // of every part row are zeroed.  ldx a multiple of 4, ldo of 8, both pointers 16-byte aligned.
