@@ -347,23 +347,32 @@ cudaError_t launch_ring_weights(const float* src, float* dst, int64_t n_e, int K
 // Collapsed LSC operator.  For every shell pair (s, s') in the window
 //   W[(s,co,a)][(s',ci,b)] = sum_k w[co,s,ci,s',k] M_{s,s'}[k][a][b] (M_{s,s'} = M_s in the resampled form)
 // One block: 8 channel pairs (co, ci) of one shell pair and up to 2048 (a, b)
-// entries.  Chunks of 8 kernel points of M_{s,s'} (8 x 2048 floats) and of w are
-// staged in shared memory with coalesced loads; each thread then accumulates
-// 8 pairs x 8 consecutive (a, b) entries (64 FMAs per 4 vector shared loads).
-// The finished block goes back through shared memory and is written to W
-// (runs along b) and Wt (runs along a), one warp per run.  Shell pairs outside
-// the window write zeros.
+// entries.  Chunks of 4 kernel points of M_{s,s'} (4 x 2048 floats) and of w are
+// staged in shared memory by cp.async, two chunks in flight (the next one loads
+// while the current one is used); each thread accumulates 8 pairs x 8 consecutive
+// (a, b) entries (64 FMAs per 4 vector shared loads).  The finished block goes
+// back through shared memory and is written to W (runs along b) and Wt (runs
+// along a), one warp per run.  Shell pairs outside the window write zeros.
 // ---------------------------------------------------------------------------
-constexpr int kBwPairs = 8, kBwChunk = 2048, kBwKC = 8;  // pairs, (a,b) entries, kernel points per stage
-static_assert(kBwKC >= kBwPairs, "the M stage buffer holds the finished block");
+constexpr int kBwPairs = 8, kBwChunk = 2048, kBwKC = 4;  // pairs, (a,b) entries, kernel points per stage
+static_assert(2 * kBwKC >= kBwPairs, "the two M stage buffers hold the finished block");
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 template <typename TW>
 __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
                                                       const float* __restrict__ M, TW* __restrict__ W,
                                                       TW* __restrict__ Wt) {
-  extern __shared__ float4 blk4[];  // [kBwKC][kBwChunk] M stage; later [kBwPairs][kBwChunk] results
+  extern __shared__ float4 blk4[];  // [2][kBwKC][kBwChunk] M stages; later [kBwPairs][kBwChunk] results
   float* blk = reinterpret_cast<float*>(blk4);
-  __shared__ __align__(16) float wk[kBwKC][kBwPairs];
+  __shared__ __align__(16) float wk[2][kBwKC][kBwPairs];
   const int tid = threadIdx.x;
   const int pair = blockIdx.y;  // s * s_in + s'
   const int s = pair / d.s_in, sp = pair % d.s_in;
@@ -379,36 +388,49 @@ __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ Ls
     for (int e = 0; e < 8; ++e) acc[p][e] = 0.f;
   if (in_win) {
     const float* Ms = M + s * d.m_stride_s + sp * d.m_stride_sp + ab0 + tid;
-    for (int k0 = 0; k0 < d.K; k0 += kBwKC) {
-      const int nk = min(kBwKC, d.K - k0);
-      __syncthreads();
-      // stage M_{s,s'}[k0 .. k0+7][ab0 .. ab0+2047]: element tid + 256 e of each row (zero past the range)
+    const uint32_t blk_s = (uint32_t)__cvta_generic_to_shared(blk);
+    const int nst = (d.K + kBwKC - 1) / kBwKC;
+    // stage c: M_{s,s'}[4c .. 4c+3][ab0 .. ab0+2047] (zero past the ranges) and the w values
+    auto issue = [&](int c) {
+      const int buf = c & 1, k0 = c * kBwKC;
+#pragma unroll
       for (int kk = 0; kk < kBwKC; ++kk) {
-        const float* row = Ms + (int64_t)(k0 + kk) * nab;
-        float* dst = blk + kk * kBwChunk + tid;
-        if (kk < nk && nabc == kBwChunk) {
+        const bool krow = k0 + kk < d.K;
+        const float* row = Ms + (int64_t)(krow ? k0 + kk : 0) * nab;
 #pragma unroll
-          for (int e = 0; e < 8; ++e) dst[256 * e] = __ldg(row + 256 * e);
-        } else {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) dst[256 * e] = (kk < nk && tid + 256 * e < nabc) ? __ldg(row + 256 * e) : 0.f;
+        for (int e = 0; e < 8; ++e) {
+          const bool ok = krow && tid + 256 * e < nabc;
+          cp_async4(blk_s + (uint32_t)(((buf * kBwKC + kk) * kBwChunk + tid + 256 * e) * 4), ok ? row + 256 * e : Ms,
+                    ok ? 4 : 0);
         }
       }
+      cp_async_commit();
       if (tid < kBwKC * kBwPairs) {
         const int kk = tid / kBwPairs, pp = tid % kBwPairs, pr = p0 + pp;
         float v = 0.f;
-        if (pp < np && kk < nk) {
+        if (pp < np && k0 + kk < d.K) {
           const int co = pr / d.c_in, ci = pr % d.c_in;
           v = w[((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K + k0 + kk];
         }
-        wk[kk][pp] = v;
+        wk[buf][kk][pp] = v;
       }
-      __syncthreads();
+    };
+    issue(0);
+    for (int c = 0; c < nst; ++c) {
+      const int buf = c & 1;
+      if (c + 1 < nst) {
+        issue(c + 1);  // the buffer it fills was last read in iteration c - 1
+        cp_async_wait_group<1>();
+      } else {
+        cp_async_wait_group<0>();
+      }
+      __syncthreads();  // stage c complete and visible
 #pragma unroll
       for (int kk = 0; kk < kBwKC; ++kk) {
-        const float4 m0 = blk4[kk * (kBwChunk / 4) + 2 * tid], m1 = blk4[kk * (kBwChunk / 4) + 2 * tid + 1];
-        const float4 w0 = *reinterpret_cast<const float4*>(&wk[kk][0]);
-        const float4 w1 = *reinterpret_cast<const float4*>(&wk[kk][4]);
+        const float4 m0 = blk4[(buf * kBwKC + kk) * (kBwChunk / 4) + 2 * tid];
+        const float4 m1 = blk4[(buf * kBwKC + kk) * (kBwChunk / 4) + 2 * tid + 1];
+        const float4 w0 = *reinterpret_cast<const float4*>(&wk[buf][kk][0]);
+        const float4 w1 = *reinterpret_cast<const float4*>(&wk[buf][kk][4]);
         const float mv[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
         const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
@@ -416,6 +438,7 @@ __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ Ls
 #pragma unroll
           for (int e = 0; e < 8; ++e) acc[p][e] = fmaf(wv[p], mv[e], acc[p][e]);
       }
+      __syncthreads();  // everyone is done with buffer buf before it is refilled
     }
   }
   __syncthreads();
@@ -491,7 +514,7 @@ cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, con
   }
   dim3 grid((unsigned)((npairs + kBwPairs - 1) / kBwPairs), (unsigned)(d.s_out * d.s_in),
             (unsigned)((nab + kBwChunk - 1) / kBwChunk));
-  const size_t smem = sizeof(float) * kBwKC * kBwChunk;  // = kBwPairs * kBwChunk for the results
+  const size_t smem = sizeof(float) * 2 * kBwKC * kBwChunk;  // = kBwPairs * kBwChunk for the results
   if (w_t == 0) {
     e = cudaFuncSetAttribute(build_w_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -696,25 +719,52 @@ __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ 
   const int ab_end = min(nab, (part + 1) * kDwAbPart);
   float acc[4][4] = {};
   if (in_win) {
-    for (int ab0 = part * kDwAbPart; ab0 < ab_end; ab0 += AB) {
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < PT * AB; idx += 256) {
-        const int t = idx % AB, pp = idx / AB, pr = p0 + pp, ab = ab0 + t;
-        float v = 0.f;
-        if (pr < npairs && ab < ab_end) {
-          const int co = pr / d.c_in, ci = pr % d.c_in;
-          const int aa = TRANS ? ab % d.n_out : ab / d.n_in, bb = TRANS ? ab / d.n_out : ab % d.n_in;
-          const int64_t off = (((int64_t)s * d.c_out + co) * d.n_out + aa) * p_rs +
-                              (((int64_t)sp * d.c_in + ci) * d.n_in + bb) * p_cs;
-          for (int z = 0; z < splits; ++z) v += P[z * split_stride + off];
+    // software pipeline: the next chunk's loads are issued before this chunk's FMAs and
+    // summed after them (up to four splits held raw in registers)
+    constexpr int kRaw = 4;
+    float raw[8][kRaw], mv_n[8];
+    auto issue = [&](int ab0) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int idx = threadIdx.x + 256 * e;
+        {
+          const int t = idx % AB, pp = idx / AB, pr = p0 + pp, ab = ab0 + t;
+#pragma unroll
+          for (int z = 0; z < kRaw; ++z) raw[e][z] = 0.f;
+          if (pr < npairs && ab < ab_end) {
+            const int co = pr / d.c_in, ci = pr % d.c_in;
+            const int aa = TRANS ? ab % d.n_out : ab / d.n_in, bb = TRANS ? ab / d.n_out : ab % d.n_in;
+            const int64_t off = (((int64_t)s * d.c_out + co) * d.n_out + aa) * p_rs +
+                                (((int64_t)sp * d.c_in + ci) * d.n_in + bb) * p_cs;
+#pragma unroll
+            for (int z = 0; z < kRaw; ++z)
+              if (z < splits) raw[e][z] = P[z * split_stride + off];
+            for (int z = kRaw; z < splits; ++z) raw[e][kRaw - 1] += P[z * split_stride + off];
+          }
         }
-        gs[t][pp] = v;
+        {
+          const int t = idx % AB, kk = idx / AB, ab = ab0 + t, k = k0 + kk;
+          mv_n[e] = (ab < ab_end && k < d.K) ? M[s * d.m_stride_s + sp * d.m_stride_sp + (int64_t)k * nab + ab] : 0.f;
+        }
       }
-      for (int idx = threadIdx.x; idx < KT * AB; idx += 256) {
-        const int t = idx % AB, kk = idx / AB, ab = ab0 + t, k = k0 + kk;
-        ms_[t][kk] = (ab < ab_end && k < d.K) ? M[s * d.m_stride_s + sp * d.m_stride_sp + (int64_t)k * nab + ab] : 0.f;
+    };
+    auto stage = [&]() {  // summed values of the issued chunk into shared memory
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int idx = threadIdx.x + 256 * e;
+        float v = raw[e][0];
+#pragma unroll
+        for (int z = 1; z < kRaw; ++z) v += raw[e][z];
+        gs[idx % AB][idx / AB] = v;
+        ms_[idx % AB][idx / AB] = mv_n[e];
       }
+    };
+    issue(part * kDwAbPart);
+    for (int ab0 = part * kDwAbPart; ab0 < ab_end; ab0 += AB) {
+      __syncthreads();  // the previous chunk's FMAs are done with gs / ms_
+      stage();
       __syncthreads();
+      if (ab0 + AB < ab_end) issue(ab0 + AB);
       const int nt = min(AB, ab_end - ab0);
       for (int t = 0; t < nt; ++t) {
         const float4 g4 = *reinterpret_cast<const float4*>(&gs[t][ty * 4]);
