@@ -548,6 +548,7 @@ struct WgParams {
   int n_terms;   // 1 (BF16 operands) or kSplitTerms (three-part splits of FP32 operands)
   int chunk_kb;  // voxel blocks of 64 per accumulation chunk (> 0)
   int64_t tiles_per_split, total_tiles, vps, n_vox, ldp, split_stride;
+  int64_t ones_col;  // column of the row sums (rows_in)
   // element (row r, column c) of a split's partial at r * p_rs + c * p_cs: (ldp, 1), or (1, ldp)
   // for the transposed partials of the FP32 path, whose read-modify-write per chunk is then
   // coalesced across a warp's lanes (consecutive rows)
@@ -568,6 +569,11 @@ __device__ __forceinline__ void wg_decode(const WgParams& p, int64_t t, int& spl
   nt = (int)(r % p.g[g].n_tiles);
 }
 
+template <int BN, int CL, bool SPLIT>
+constexpr bool wgrad_sums() { return !SPLIT && CL == 2 && BN / CL + 8 <= 128; }
+template <int BN, int CL, bool SPLIT>
+constexpr int wgrad_b_slot_rows() { return wgrad_sums<BN, CL, SPLIT>() ? BN / CL + 8 : BN / CL; }
+
 // CL = 2: a cluster of two CTAs computes a 256-row x BN tile with 2-SM MMAs:
 // each CTA stages its own 128 output rows of dY and BN/2 of the BN input rows
 // of X; the even CTA arms the stage barriers and issues the MMAs, each CTA
@@ -583,11 +589,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   // transposed partials
   const int n_terms = SPLIT ? p.n_terms : 1;
   const int chunk_kb = SPLIT ? p.chunk_kb : (1 << 24);
-  constexpr int A_BYTES = 128 * 128;      // 128 rows x 64 voxels
-  constexpr int B_BYTES = BN / CL * 128;  // this CTA's BN/CL rows x 64 voxels
+  // SUMS: the bias-gradient row sums come out of the GEMM itself.  Each CTA's B slot
+  // holds 8 constant rows of ones after its BN/CL rows of X; the first column tile of
+  // every (split, group, row tile) runs with N = 2 (BN/CL + 8) = 256 instead of BN, and
+  // its columns BN/CL .. BN/CL + 7 are sum_v dY[row][v].  (BF16 operands, CTA pairs.)
+  constexpr bool SUMS = wgrad_sums<BN, CL, SPLIT>();
+  constexpr int B_ROWS = BN / CL;              // rows of X this CTA loads per stage
+  constexpr int B_SLOT_ROWS = wgrad_b_slot_rows<BN, CL, SPLIT>();
+  constexpr int A_BYTES = 128 * 128;           // 128 rows x 64 voxels
+  constexpr int B_BYTES = B_SLOT_ROWS * 128;   // B slot (X rows, then the ones rows)
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  constexpr uint32_t TMEM_COLS = 512;      // two accumulators, 256 columns apart
+  constexpr uint32_t TX_BYTES = A_BYTES + B_ROWS * 128;  // bytes the copies deliver per CTA and stage
+  constexpr uint32_t TMEM_COLS = 512;          // two accumulators, 256 columns apart
   constexpr uint32_t IDESC = idesc_bf16(128 * CL, BN, false, false);
+  constexpr uint32_t IDESC_SUMS = idesc_bf16(128 * CL, 2 * B_SLOT_ROWS, false, false);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -620,6 +635,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_mbar_init();
     prefetch_tmap(&mapA);
     prefetch_tmap(&mapB);
+  }
+  if (SUMS) {
+    // the ones rows of every stage (BF16 1.0 pairs), never overwritten by the copies; made
+    // visible to the tensor core's proxy before the cluster barrier below
+    for (int i = threadIdx.x; i < STAGES * 8 * 32; i += blockDim.x) {
+      const int st = i / 256, w = i % 256;
+      reinterpret_cast<uint32_t*>(smem + st * STAGE_BYTES + A_BYTES + B_ROWS * 128)[w] = 0x3F803F80u;
+    }
+    fence_proxy_async_smem();
   }
   if (CL > 1) cluster_sync();  // the peer's barriers exist before any copy or commit reaches them
   if (warp == 1) {
@@ -665,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int vx = (int)(vs + (int64_t)kb * 64);
           if (CL > 1) {
             const uint32_t fb = mapa_shared(full_bar(stage), 0);
-            if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), CL * STAGE_BYTES);
+            if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), CL * TX_BYTES);
             if constexpr (SPLIT) {
               tma_load_3d_pair(&mapA, fb, a_dst, vx, arow, za);
               tma_load_3d_pair(&mapB, fb, b_dst, vx, brow, zb);
@@ -674,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               tma_load_2d_pair(&mapB, fb, b_dst, vx, brow);
             }
           } else {
-            mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
+            mbar_arrive_expect_tx(full_bar(stage), TX_BYTES);
             if constexpr (SPLIT) {
               tma_load_3d(&mapA, full_bar(stage), a_dst, vx, arow, za);
               tma_load_3d(&mapB, full_bar(stage), b_dst, vx, brow, zb);
@@ -707,6 +731,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t vs = (int64_t)split * p.vps, ve = min(p.n_vox, vs + p.vps);
       const int nkb = (int)((ve - vs + 63) / 64);
       const int nch = SPLIT ? k_chunks(nkb, chunk_kb) : 1;
+      const uint32_t idesc = (SUMS && nt == 0) ? IDESC_SUMS : IDESC;
       for (int c = 0; c < nch; ++c) {
         if (!wait_bounded(tempty_bar(acc), acc_phase ^ 1u, abort_flag, p.err, kErrTmemEmpty)) {
           ok = false;
@@ -730,9 +755,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t ad = umma_desc(a_src + k * 32, 16, 1024, kSwizzle128B);
             const uint64_t bd = umma_desc(b_src + k * 32, 16, 1024, kSwizzle128B);
             if (CL > 1)
-              mma_bf16_pair(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+              mma_bf16_pair(d_tmem, ad, bd, idesc, (kb | k) != 0);
             else
-              mma_bf16(d_tmem, ad, bd, IDESC, (kb | k) != 0);
+              mma_bf16(d_tmem, ad, bd, idesc, (kb | k) != 0);
           }
           if (CL > 1)
             mma_commit_pair_mc(empty_bar(stage), 0x3);
@@ -783,6 +808,38 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 256);
+        if (SUMS && nt == 0) {
+          // N = 256: D column j holds X row j (j < B_ROWS), the row sum (B_ROWS <= j < 128),
+          // X row j - 8 (128 <= j < 128 + B_ROWS) or the row sum again
+          for (int k0 = 0; 32 * k0 + 16 * half < 2 * B_SLOT_ROWS; k0 += 4) {
+            uint32_t rv[4][16];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int c0 = 32 * (k0 + u) + 16 * half;
+              if (c0 < 2 * B_SLOT_ROWS) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+            }
+            tmem_wait_ld();
+            if (m < G.M) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int c0 = 32 * (k0 + u) + 16 * half;
+                if (c0 < 2 * B_SLOT_ROWS) {
+#pragma unroll
+                  for (int j = 0; j < 16; ++j) {
+                    const int jc = c0 + j, in_half = jc % B_SLOT_ROWS;
+                    const int n = (jc / B_SLOT_ROWS) * B_ROWS + in_half;
+                    if (in_half < B_ROWS) {
+                      if (n < G.N) prow[n * cs] = __uint_as_float(rv[u][j]);
+                    } else if (jc == B_ROWS) {
+                      p.P[(int64_t)split * p.split_stride + (G.m_row0 + m) * rs + p.ones_col * cs] =
+                          __uint_as_float(rv[u][j]);
+                    }
+                  }
+                }
+              }
+            }
+          }
+        } else
         for (int k0 = 0; 32 * k0 + 16 * half < BN && nt * BN + 32 * k0 + 16 * half < G.N; k0 += 4) {
           uint32_t rv[4][16];
 #pragma unroll
@@ -1281,7 +1338,7 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* 
 
 template <int BN, int S, int CL, bool SPLIT>
 cudaError_t launch_wgrad(const CUtensorMap& ma, const CUtensorMap& mb, const WgParams& p, cudaStream_t st) {
-  const size_t smem = smem_bytes<BN, S>(128 * 128, BN / CL * 128);
+  const size_t smem = smem_bytes<BN, S>(128 * 128, wgrad_b_slot_rows<BN, CL, SPLIT>() * 128);
   auto kern = wgrad_kernel<BN, S, CL, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1327,6 +1384,7 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
   p.split_stride = split_stride;
   p.p_rs = 1;  // transposed partials: a warp's lanes (consecutive rows) store 128 contiguous bytes
   p.p_cs = ldp;
+  p.ones_col = d.rows_in;
   p.P = P;
   p.err = err;
   cudaError_t e = cudaSuccess;
@@ -1339,8 +1397,14 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
       e = cl > 1 ? launch_wgrad<BN, 7, 2, false>(ma, mb, p, st) : launch_wgrad<BN, 4, 1, false>(ma, mb, p, st);
     if (e != cudaSuccess) return e;
   }
-  // bias-gradient column: row sums of dY per split (a separate HBM-bound pass; an extra
-  // N = 16 MMA per step inside the GEMM measured slower, each MMA re-reads the A tile)
+  // bias-gradient column: row sums of dY per split.  BF16 operands on CTA pairs: made by
+  // the GEMM (ones rows in its operand slots, one 256-wide column tile per row tile);
+  // otherwise a separate HBM-bound pass (a separate N = 16 MMA per step inside the GEMM
+  // measured slower: each MMA streams its whole A tile again)
+  if (!parts.on() && cl > 1) {
+    static_assert(wgrad_sums<BN, 2, false>(), "the BF16 pair kernel makes the row sums");
+    return cudaGetLastError();
+  }
   const int64_t warps = d.rows_out * splits;
   TraceScope trace_rs("lsc_rowsum", st);
   const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
