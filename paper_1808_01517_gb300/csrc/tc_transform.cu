@@ -41,6 +41,7 @@ struct TfParams {
   CUtensorMap mapY[kMaxTcGroups];  // output, 3-D {voxels, rows of one channel, channels}
   TfGroup g[kMaxTcGroups];
   int n_groups, channels, m_tiles, stages, stage_bytes, stg_bytes;
+  int swz;  // launch the SWZ instantiation (wide BF16 outputs)
   uint32_t b_total;
   int64_t total_tiles, n_vox, ldy;
   void* Y;
@@ -81,8 +82,11 @@ struct TileIter {
   }
 };
 
-template <bool OUT_F32>
+// SWZ: BF16 output through stmatrix into 128-byte-swizzled staging halves (a separate
+// instantiation, so that the one-box epilogue keeps its own register allocation)
+template <bool OUT_F32, bool SWZ>
 __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_constant__ TfParams p) {
+  static_assert(!(OUT_F32 && SWZ), "the swizzled epilogue writes BF16");
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -225,6 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
       // staging tile [n_mma rows][128 voxels]: one 256-byte (BF16) run per output row
       uint8_t* stg = stg_ptr + (size_t)buf * p.stg_bytes;
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
+      if constexpr (!SWZ) {
       // this warp's chunks: c0 = 16 * (2k + half); up to four loads in flight per wait
       for (int k0 = 0; 32 * k0 + 16 * half < G.n_mma; k0 += 4) {
         uint32_t rv[4][16];
@@ -254,6 +259,47 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
           }
         }
       }
+      } else {
+      // BF16: staging halves [voxel half][n_mma rows][64 voxels], 128-byte swizzled (16-byte
+      // chunk index XOR row % 8).  16 x 256-bit TMEM loads give each thread two voxels x two
+      // adjacent columns; packed to BF16 pairs they are mma fragments, and stmatrix .trans
+      // writes each 8 voxel x 8 column block as 8 rows of 16 bytes (conflict-free).
+      const uint32_t stg_h = stg_base + (uint32_t)(buf * p.stg_bytes) + (uint32_t)((q >> 1) * G.n_mma * 128);
+      const int vq = (q & 1) * 4;  // this warp's first 8-voxel chunk within its half
+      const int mm = lane >> 3, rr = lane & 7;  // matrix and row whose address this thread gives
+      const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
+      for (int k0 = 0; 32 * k0 + 16 * half < G.n_mma; k0 += 2) {
+        uint32_t rv[2][2][2][4];  // [chunk][16-lane block][8-column half][regs]
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int c0 = 32 * (k0 + u) + 16 * half;
+          if (c0 < G.n_mma) {
+#pragma unroll
+            for (int lb = 0; lb < 2; ++lb)
+#pragma unroll
+              for (int ch = 0; ch < 2; ++ch)
+                tmem_ld_16x256b_nowait(tl + ((uint32_t)(16 * lb) << 16) + (uint32_t)(c0 + 8 * ch), rv[u][lb][ch]);
+          }
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int c0 = 32 * (k0 + u) + 16 * half;
+          if (c0 < G.n_mma) {
+#pragma unroll
+            for (int lb = 0; lb < 2; ++lb) {
+              // matrices: 0 = voxels 0-7 x columns 0-7, 1 = voxels 8-15 x 0-7, 2 = 0-7 x 8-15, 3 = 8-15 x 8-15
+              const uint32_t m0 = pack_bf16x2(rv[u][lb][0][0], rv[u][lb][0][1]);
+              const uint32_t m1 = pack_bf16x2(rv[u][lb][0][2], rv[u][lb][0][3]);
+              const uint32_t m2 = pack_bf16x2(rv[u][lb][1][0], rv[u][lb][1][1]);
+              const uint32_t m3 = pack_bf16x2(rv[u][lb][1][2], rv[u][lb][1][3]);
+              const int c = c0 + ((mm >> 1) << 3) + rr, vc = vq + 2 * lb + (mm & 1);
+              stmatrix_x4_trans(stg_h + (uint32_t)(c * 128 + ((vc ^ (c & 7)) << 4)), m0, m1, m2, m3);
+            }
+          }
+        }
+      }
+      }
       // accumulator drained: hand it back to the MMA warp; staging filled: hand it to the store
       tc_fence_before();
       fence_proxy_async_smem();
@@ -268,7 +314,12 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_kernel(const __grid_
           lead_ok = wait_bounded(stg_ready_bar(buf), use_par, abort_flag, p.err, kErrTFull);
           if (lead_ok) {
             const uint32_t src = stg_base + (uint32_t)(buf * p.stg_bytes);
-            tma_store_3d(&p.mapY[g], src, mt * 128, 0, c);  // box {128 voxels, n_out rows, 1}
+            if (!SWZ) {
+              tma_store_3d(&p.mapY[g], src, mt * 128, 0, c);  // box {128 voxels, n_out rows, 1}
+            } else {  // two swizzled boxes {64 voxels, n_out rows, 1}
+              tma_store_3d(&p.mapY[g], src, mt * 128, 0, c);
+              tma_store_3d(&p.mapY[g], src + (uint32_t)(G.n_mma * 128), mt * 128 + 64, 0, c);
+            }
             bulk_commit();
             // the previous tile's store has finished reading its buffer: release it
             bulk_wait_read<1>();
@@ -455,27 +506,33 @@ cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X,
         return cudaErrorInvalidValue;
     }
   }
-  // output maps
+  // output maps.  BF16 outputs of 64 or more rows (SH2Signal and the Signal2SH adjoint at
+  // order 8) go through the stmatrix epilogue: measured 0.62 -> 0.50 ms and 0.164 ->
+  // 0.135 ms; the 45-row coefficient outputs stay faster with one 128-voxel box
   const int es = out_t == 0 ? 4 : 2;
   int nmax = 0;
+  for (int s = 0; s < t.n_shells; ++s) nmax = std::max(nmax, p.g[s].n_out);
+  p.swz = (out_t != 0 && nmax >= 64) ? 1 : 0;
   for (int s = 0; s < t.n_shells; ++s) {
     const TfGroup& G = p.g[s];
-    nmax = std::max(nmax, G.n_out);
     const char* base = static_cast<const char*>(Y) + G.y_row0 * ldy * es;
     cuuint64_t dims[3] = {(cuuint64_t)n_vox, (cuuint64_t)G.n_out, (cuuint64_t)C};
     cuuint64_t strides[2] = {(cuuint64_t)ldy * es, (cuuint64_t)(G.y_cstride * ldy * es)};
-    cuuint32_t box[3] = {128, (cuuint32_t)G.n_out, 1};
+    // FP32: one box of 128 voxels, staging unswizzled; BF16: boxes of 64 voxels (128-byte rows)
+    // read from the 128-byte-swizzled staging halves
+    cuuint32_t box[3] = {p.swz ? 64u : 128u, (cuuint32_t)G.n_out, 1};
     cuuint32_t esz[3] = {1, 1, 1};
     if (fn(&p.mapY[s], out_t == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
-           const_cast<char*>(base), dims, strides, box, esz, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+           const_cast<char*>(base), dims, strides, box, esz, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           p.swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
   p.n_groups = t.n_shells;
   p.channels = C;
   p.m_tiles = (int)((n_vox + 127) / 128);
   p.stage_bytes = kmax * 256;
-  const int nmma_max = (nmax + 15) / 16 * 16;
+  const int nmma_max = (nmax + 15) / 16 * 16;  // nmax: widest group output (above)
   p.stg_bytes = (2 * nmma_max * 64 * es + 1023) / 1024 * 1024;
   p.b_total = (boff + 1023) / 1024 * 1024;
   const size_t fixed = 1024 + p.b_total + 2 * (size_t)p.stg_bytes + 16 * 8 + 128;
@@ -493,15 +550,11 @@ cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X,
   if (p.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)std::min<int64_t>(p.total_tiles, tf_sms());
   cudaError_t e;
-  if (out_t == 0) {
-    e = cudaFuncSetAttribute(transform_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    transform_tc_kernel<true><<<grid, kThreads, smem, st>>>(p);
-  } else {
-    e = cudaFuncSetAttribute(transform_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    transform_tc_kernel<false><<<grid, kThreads, smem, st>>>(p);
-  }
+  auto kern = out_t == 0 ? transform_tc_kernel<true, false>
+                         : (p.swz ? transform_tc_kernel<false, true> : transform_tc_kernel<false, false>);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, smem, st>>>(p);
   count_launch();
   return cudaGetLastError();
 }
