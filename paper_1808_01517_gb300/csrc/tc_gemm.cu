@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int acc = 0;
     uint32_t acc_phase = 0;
     int it = 0;
-    const int h = q >> 1, xl = (q & 1) * 32 + lane;
+    const int h = q >> 1;
     for (int64_t t = t_first; t < p.total_tiles; t += t_step, ++it) {
       int g, mt, nt;
       vox_decode(p, t, g, mt, nt);
@@ -377,31 +377,51 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           const int cbeg = pass * HB;
+          // 16 x 256-bit TMEM loads: thread t holds voxels t/4 and t/4 + 8 of a 16-lane block
+          // and columns 2(t%4), 2(t%4)+1 (+8); with the bias added and packed to BF16 pairs
+          // they are mma fragments, stored by stmatrix .trans into the staging halves
+          // [voxel half][HB rows][64 voxels], 128-byte swizzled (16-byte chunk ^ row % 8)
+          const uint32_t stg_h = smem_u32(stg_ptr) + (uint32_t)(h * HB * 128);
+          const int vq = (q & 1) * 4, mm = lane >> 3, rr = lane & 7;
 #pragma unroll
-          for (int k0 = 0; k0 < (HB + 31) / 32; k0 += 4) {
-            uint32_t rv[4][16];
+          for (int k0 = 0; k0 < (HB + 31) / 32; k0 += 2) {
+            uint32_t rv[2][2][2][4];  // [chunk][16-lane block][8-column half][regs]
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 2; ++u) {
               const int c0 = cbeg + 32 * (k0 + u) + 16 * half;
-              if (c0 < cbeg + HB) tmem_ld16_nowait(tbase + (uint32_t)c0, rv[u]);
+              if (c0 < cbeg + HB) {
+#pragma unroll
+                for (int lb = 0; lb < 2; ++lb)
+#pragma unroll
+                  for (int ch = 0; ch < 2; ++ch)
+                    tmem_ld_16x256b_nowait(tbase + ((uint32_t)(16 * lb) << 16) + (uint32_t)(c0 + 8 * ch), rv[u][lb][ch]);
+              }
             }
             tmem_wait_ld();
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 2; ++u) {
               const int c0 = cbeg + 32 * (k0 + u) + 16 * half;
-              const int nbase = nt * BN + c0;
               if (c0 < cbeg + HB) {
-                __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(stg_ptr) + (size_t)h * HB * 64 + (c0 - cbeg) * 64 + xl;
+                const int m = k0 + u;  // this warp's chunk number: columns w = 16 m + j of breg's map
+                float b[4];            // columns 2(t%4) + {0, 1, 8, 9} of the chunk
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                  float bv;
-                  if (PASSES == 1) {
-                    const int w = 16 * (k0 + u) + jj;  // compile-time: the loops are unrolled
-                    bv = __shfl_sync(0xffffffffu, breg[(w >> 5) < BN / 64 ? (w >> 5) : 0], w & 31);
-                  } else {
-                    bv = (p.bias && nbase + jj < G.N) ? __ldg(p.bias + G.y_row0 + nbase + jj) : 0.f;
-                  }
-                  dst[jj * 64] = __float2bfloat16_rn(__uint_as_float(rv[u][jj]) + bv);
+                for (int i = 0; i < 4; ++i) {
+                  const int jc = 2 * (lane & 3) + (i & 1) + 8 * (i >> 1);
+                  if (PASSES == 1)
+                    b[i] = __shfl_sync(0xffffffffu, breg[(m >> 1) < BN / 64 ? (m >> 1) : 0], ((m & 1) * 16 + jc) & 31);
+                  else
+                    b[i] = (p.bias && nt * BN + c0 + jc < G.N) ? __ldg(p.bias + G.y_row0 + nt * BN + c0 + jc) : 0.f;
+                }
+#pragma unroll
+                for (int lb = 0; lb < 2; ++lb) {
+                  const uint32_t* r0 = rv[u][lb][0];
+                  const uint32_t* r1 = rv[u][lb][1];
+                  const uint32_t m0 = pack_bf16x2f(__uint_as_float(r0[0]) + b[0], __uint_as_float(r0[1]) + b[1]);
+                  const uint32_t m1 = pack_bf16x2f(__uint_as_float(r0[2]) + b[0], __uint_as_float(r0[3]) + b[1]);
+                  const uint32_t m2 = pack_bf16x2f(__uint_as_float(r1[0]) + b[2], __uint_as_float(r1[1]) + b[3]);
+                  const uint32_t m3 = pack_bf16x2f(__uint_as_float(r1[2]) + b[2], __uint_as_float(r1[3]) + b[3]);
+                  const int c = (c0 - cbeg) + ((mm >> 1) << 3) + rr, vc = vq + 2 * lb + (mm & 1);
+                  stmatrix_x4_trans(stg_h + (uint32_t)(c * 128 + ((vc ^ (c & 7)) << 4)), m0, m1, m2, m3);
                 }
               }
             }
@@ -570,9 +590,9 @@ __device__ __forceinline__ void wg_decode(const WgParams& p, int64_t t, int& spl
 }
 
 template <int BN, int CL, bool SPLIT>
-constexpr bool wgrad_sums() { return !SPLIT && CL == 2 && BN / CL + 8 <= 128; }
+__host__ __device__ constexpr bool wgrad_sums() { return !SPLIT && CL == 2 && BN / CL + 8 <= 128; }
 template <int BN, int CL, bool SPLIT>
-constexpr int wgrad_b_slot_rows() { return wgrad_sums<BN, CL, SPLIT>() ? BN / CL + 8 : BN / CL; }
+__host__ __device__ constexpr int wgrad_b_slot_rows() { return wgrad_sums<BN, CL, SPLIT>() ? BN / CL + 8 : BN / CL; }
 
 // CL = 2: a cluster of two CTAs computes a 256-row x BN tile with 2-SM MMAs:
 // each CTA stages its own 128 output rows of dY and BN/2 of the BN input rows
@@ -1215,7 +1235,7 @@ cudaError_t run_vox(const CUtensorMap& ma, const OperatorView& B, VoxParams& p, 
     cuuint32_t box[3] = {64, (cuuint32_t)(bn / kFwdPasses), 1};
     cuuint32_t es[3] = {1, 1, 1};
     staged = fn(&my, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Y, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   }
   if (staged) {
