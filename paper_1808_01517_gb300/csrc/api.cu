@@ -617,11 +617,14 @@ int wgrad_splits(const LscDims& d, int64_t n_vox, int64_t* vps) {
   return splits;
 }
 
-// Whether the forward reads the transposed operator Wt (the CUDA-core path always
-// does; the tensor-core path only when W's column blocks carry padding).  The same
+// Whether the operator build writes the transposed operator Wt: the CUDA-core forward
+// always reads it, the tensor-core forward when W's column blocks carry padding, and the
+// BF16 tensor-core input gradient when it can read Wt as its K-major operator.  The same
 // answer in a forward and the backward that follows keeps DELIMIT_LSC_OPERATOR_READY
 // valid between them.
-bool needs_wt(const LscDims& d, bool tc) { return !tc || !tc_forward_reads_w(d); }
+bool needs_wt(const LscDims& d, bool tc, delimit_dtype t) {
+  return !tc || !tc_forward_reads_w(d) || (t == DELIMIT_BF16 && tc_dgrad_reads_wt(d));
+}
 
 bool make_plan(const delimit_lsc_geometry* g, int64_t n_vox, int c_in, int c_out, delimit_dtype t, LscPlan& p) {
   if (!g || c_in < 1 || c_out < 1 || n_vox < 0 || c_in > 4096 || c_out > 4096 || !valid_dtype(t)) return false;
@@ -668,7 +671,7 @@ bool make_plan(const delimit_lsc_geometry* g, int64_t n_vox, int c_in, int c_out
 cudaError_t build_operator(const LscDims& d, const delimit_lsc_geometry* g, const LscPlan& p, const float* w,
                            const float* b, void* W, void* Wt, float* bias, delimit_dtype act_t, bool tc, char* base,
                            cudaStream_t cs) {
-  const bool wt = needs_wt(d, tc);
+  const bool wt = needs_wt(d, tc, act_t);
   cudaError_t e = launch_build_w(d, w, b, g->d_M, g->d_q, W, wt ? Wt : nullptr, bias, int(act_t), cs);
   if (e != cudaSuccess || !(tc && act_t == DELIMIT_F32)) return e;
   e = split_bf16x3(static_cast<const float*>(W), d.rows_out, d.ldW, d.ldW, base + p.off_W3, d.ldW, d.rows_out * d.ldW,
@@ -823,10 +826,10 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
       TcParts parts;
       parts.act = d.rows_out * p.ld3;
       parts.op = d.rows_out * d.ldW;
-      e = tc_lsc_dgrad(d, dY3, base + p.off_W3, d_in, n_vox, p.ld3, ld_in, g->err_word, cs, parts);
+      e = tc_lsc_dgrad(d, dY3, base + p.off_W3, nullptr, d_in, n_vox, p.ld3, ld_in, g->err_word, cs, parts);
       if (e != cudaSuccess) return cuda_fail(e, "tensor-core FP32 LSC input-gradient launch");
     } else if (act_t == DELIMIT_BF16 && all_fed && tc) {
-      e = tc_lsc_dgrad(d, d_out, W, d_in, n_vox, ld_out, ld_in, g->err_word, cs);
+      e = tc_lsc_dgrad(d, d_out, W, needs_wt(d, tc, act_t) ? Wt : nullptr, d_in, n_vox, ld_out, ld_in, g->err_word, cs);
       if (e != cudaSuccess) return cuda_fail(e, "tensor-core LSC input-gradient launch");
     } else {
       RowGemmArgs a;

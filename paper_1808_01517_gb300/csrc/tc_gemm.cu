@@ -46,6 +46,7 @@ constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // + TMA warp + MMA warp
 constexpr int kBK = 64;            // K rows (or voxels) per stage
 constexpr int kWgradBN = 240;      // weight-gradient column tile (divides 720-multiples: 1440, 2160)
+constexpr int kDgradBN = 240;      // input-gradient column tile on Wt (K-major), when it divides c_in n_in
 constexpr int kBoxBytes = 64 * 128;  // one 64 x 64 BF16 box, 128-byte rows
 
 }  // namespace
@@ -127,13 +128,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const __grid_constant__ CUtensorMap mapY, const __grid_constant__ VoxParams p) {
   using namespace ptx;
   static_assert(CL == 1 || CL == 2, "one CTA or a CTA pair");
-  static_assert(CL == 1 || (BN / 2) % 64 == 0, "each CTA of a pair holds whole 64-column operator atoms");
+  // MN-major operators need whole 64-column atoms per CTA (checked on the host); K-major ones
+  // only whole 8-row groups (BN = 240 for the input gradient)
+  static_assert((BN / CL) % 8 == 0, "whole 8-row operator groups per CTA");
+  static_assert(!STAGED || BN % 64 == 0, "the staged epilogue's bias map covers 64-column atoms");
   static_assert(!(SPLIT && STAGED), "FP32 outputs leave through direct stores");
   // SPLIT: FP32 operands as three BF16 planes (3-D maps), six terms, chunked K, FP32 output
   const int n_terms = SPLIT ? p.n_terms : 1;
   const int chunk_kb = SPLIT ? p.chunk_kb : (1 << 24);
   constexpr int A_BYTES = 2 * kBoxBytes;               // 128 voxels x 64 K rows
-  constexpr int B_BYTES = (BN / CL / 64) * kBoxBytes;  // this CTA's BN/CL columns x 64 K rows
+  constexpr int B_BYTES = (BN / CL) * 128;  // this CTA's BN/CL operator columns x 64 K (128 bytes each)
+  constexpr int ACC_STRIDE = BN <= 128 ? 128 : 256;  // TMEM columns between the two accumulators
+  constexpr int NBREG = (BN / 2 + 31) / 32;  // bias registers: a warp's BN/2 columns over 32 lanes
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   constexpr int HB = BN / PASSES;                        // columns per staged pass
   constexpr int STG_BYTES = STAGED ? HB * 128 * 2 : 0;  // [HB rows][64 voxels] x 2 voxel halves, BF16
@@ -287,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * ACC_STRIDE);
         // this chunk's K blocks of every term, in the producer's order
         const int nk = SPLIT ? max(0, min(chunk_kb, nkb - c * chunk_kb)) * n_terms : nkb;
         for (int kb = 0; kb < nk; ++kb) {
@@ -349,9 +355,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // bias of this warp's columns, fetched before the accumulator is ready (a load per
       // column inside the drain loop stalled it): lane L holds the warp's columns
       // w = L + 32 i, i.e. chunk w / 16 (tile columns 32 (w / 16) + 16 half + w % 16)
-      float breg[BN / 64 > 0 ? BN / 64 : 1];
+      float breg[NBREG];
 #pragma unroll
-      for (int i = 0; i < BN / 64; ++i) {
+      for (int i = 0; i < NBREG; ++i) {
         const int w = lane + 32 * i, col = nt * BN + 32 * (w >> 4) + 16 * half + (w & 15);
         breg[i] = (PASSES == 1 && p.bias && col < G.N) ? __ldg(p.bias + G.y_row0 + col) : 0.f;
       }
@@ -361,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int64_t vox = (int64_t)mt * 128 + q * 32 + lane;
       const bool vok = vox < p.n_vox;
-      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * ACC_STRIDE);
       // accumulator released to the MMA issuer (the even CTA's barrier for a pair)
       const uint32_t tempty = CL > 1 ? mapa_shared(tempty_bar(acc), 0) : tempty_bar(acc);
       if (STAGED) {
@@ -408,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int i = 0; i < 4; ++i) {
                   const int jc = 2 * (lane & 3) + (i & 1) + 8 * (i >> 1);
                   if (PASSES == 1)
-                    b[i] = __shfl_sync(0xffffffffu, breg[(m >> 1) < BN / 64 ? (m >> 1) : 0], ((m & 1) * 16 + jc) & 31);
+                    b[i] = __shfl_sync(0xffffffffu, breg[(m >> 1) < NBREG ? (m >> 1) : 0], ((m & 1) * 16 + jc) & 31);
                   else
                     b[i] = (p.bias && nt * BN + c0 + jc < G.N) ? __ldg(p.bias + G.y_row0 + nt * BN + c0 + jc) : 0.f;
                 }
@@ -471,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
           }
-          const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+          const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * ACC_STRIDE);
           if (c == 0) {
             // compile-time column loops, so that the bias comes from registers (shuffled)
 #pragma unroll
@@ -492,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                   for (int jj = 0; jj < 16; ++jj) {
                     const int w = 16 * (k0 + u) + jj;
-                    const float bv = __shfl_sync(0xffffffffu, breg[(w >> 5) < BN / 64 ? (w >> 5) : 0], w & 31);
+                    const float bv = __shfl_sync(0xffffffffu, breg[(w >> 5) < NBREG ? (w >> 5) : 0], w & 31);
                     const int n = nbase + jj;
                     if (n < G.N && vok) {
                       const int64_t o = (G.y_row0 + n) * p.ldy + vox;
@@ -1067,7 +1073,7 @@ constexpr int kFwdPasses = 1;
 // operand stages that fit beside the staging tile in the ~226 KiB a CTA may use
 template <int BN, bool STAGED, int CL>
 constexpr int vox_stages() {
-  constexpr int stage = 2 * kBoxBytes + (BN / CL / 64) * kBoxBytes;
+  constexpr int stage = 2 * kBoxBytes + (BN / CL) * 128;
   constexpr int stg = STAGED ? BN / kFwdPasses * 256 : 0;
   constexpr int n = (226 * 1024 - 2048 - stg) / stage;
   return n > 8 ? 8 : n;
@@ -1152,7 +1158,7 @@ cudaError_t launch_vox(const CUtensorMap& ma, const CUtensorMap& mb, const CUten
                        cudaStream_t st) {
   constexpr int S = vox_stages<BN, STAGED, CL>();
   const size_t smem =
-      smem_bytes<BN, S>(2 * kBoxBytes, (BN / CL / 64) * kBoxBytes) + (STAGED ? BN / kFwdPasses * 256 : 0) + 16;
+      smem_bytes<BN, S>(2 * kBoxBytes, (BN / CL) * 128) + (STAGED ? BN / kFwdPasses * 256 : 0) + 16;
   auto kern = vox_gemm_kernel<BN, S, STAGED, kFwdPasses, CL, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1164,8 +1170,9 @@ cudaError_t launch_vox(const CUtensorMap& ma, const CUtensorMap& mb, const CUten
 template <int BN, bool STAGED, bool SPLIT = false>
 cudaError_t launch_vox_cl(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& my, VoxParams& p, int cl,
                           cudaStream_t st) {
-  if constexpr ((BN / 2) % 64 == 0) {
-    if (cl > 1) {
+  if constexpr ((BN / 2) % 8 == 0) {
+    // a pair splits the operator columns: whole 64-column atoms for an MN-major operator
+    if (cl > 1 && (p.b_kmajor || (BN / 2) % 64 == 0)) {
       p.total_tiles = (int64_t)((p.m_tiles + 1) / 2) * p.tiles_per_m;
       return launch_vox<BN, STAGED, 2, SPLIT>(ma, mb, my, p, st);
     }
@@ -1254,6 +1261,7 @@ cudaError_t run_vox(const CUtensorMap& ma, const OperatorView& B, VoxParams& p, 
   }
   switch (bn) {
     case 256: return launch_vox_cl<256, false>(ma, mb, my, p, cl, st);
+    case 240: return launch_vox_cl<240, false>(ma, mb, my, p, cl, st);
     case 192: return launch_vox_cl<192, false>(ma, mb, my, p, cl, st);
     default: return launch_vox_cl<128, false>(ma, mb, my, p, cl, st);
   }
@@ -1273,6 +1281,10 @@ bool tc_gemm_supported(const LscDims& d, int64_t n_vox, int64_t ld_in, int64_t l
 }
 
 bool tc_forward_reads_w(const LscDims& d) { return d.in_blk == (int64_t)d.c_in * d.n_in; }
+
+bool tc_dgrad_reads_wt(const LscDims& d) {
+  return d.out_blk == (int64_t)d.c_out * d.n_out && ((int64_t)d.c_in * d.n_in) % kDgradBN == 0;
+}
 
 cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const void* Wt, const float* bias, void* Y,
                            int64_t n_vox, int64_t ldx, int64_t ldy, int* err, cudaStream_t st, TcParts parts) {
@@ -1320,13 +1332,19 @@ cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const
   return run_vox(ma, B, p, bn, env_int("DELIMIT_FWD_STAGED", 1) != 0, gemm_cluster(2), Y, ldy, st);
 }
 
-cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* dX, int64_t n_vox, int64_t lddy,
-                         int64_t lddx, int* err, cudaStream_t st, TcParts parts) {
+cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, const void* Wt, void* dX, int64_t n_vox,
+                         int64_t lddy, int64_t lddx, int* err, cudaStream_t st, TcParts parts) {
   TraceScope trace(parts.on() ? "lsc_dgrad_gemm_f32" : "lsc_dgrad_gemm", st);
   CUtensorMap ma;
   if (!make_map(&ma, dY, (uint64_t)n_vox, (uint64_t)d.rows_out, (uint64_t)lddy, 64, kBK, parts.act))
     return cudaErrorInvalidValue;
-  const OperatorView B{W, (uint64_t)d.rows_out, (uint64_t)d.ldW, (uint64_t)d.ldW, false, parts.op};
+  // BF16 with Wt available: Wt is the K-major operator (rows = input features, columns = dY
+  // rows when W's output blocks carry no padding) and 240-column tiles cover c_in n_in
+  // exactly; otherwise W as the MN-major operator (64-column atoms, padded last tile)
+  const bool kmajor = !parts.on() && Wt && tc_dgrad_reads_wt(d);
+  const OperatorView B = kmajor ? OperatorView{Wt, (uint64_t)d.rows_in, (uint64_t)d.ldWt, (uint64_t)d.ldWt, true}
+                                : OperatorView{W, (uint64_t)d.rows_out, (uint64_t)d.ldW, (uint64_t)d.ldW, false,
+                                               parts.op};
   VoxParams p;
   memset(&p, 0, sizeof p);
   const int per_in = d.c_in * d.n_in, per_out = d.c_out * d.n_out;
@@ -1335,7 +1353,7 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* 
     VoxGroup& G = p.g[sp];
     G.a_k0 = d.rwin_lo[sp] * per_out;
     G.K = std::max(0, d.rwin_hi[sp] - d.rwin_lo[sp]) * per_out;
-    G.b_n0 = (int)(sp * d.in_blk);
+    G.b_n0 = (int)(kmajor ? (int64_t)sp * per_in : sp * d.in_blk);  // first operator row (K-major) or column
     G.N = per_in;
     G.y_row0 = (int64_t)sp * per_in;
     Ns[sp] = G.N;
@@ -1352,8 +1370,9 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* 
     p.Y = reinterpret_cast<__nv_bfloat16*>(dX);
   p.bias = nullptr;
   p.err = err;
-  return run_vox(ma, B, p, env_int("DELIMIT_DGRAD_BN", pick_bn(Ns, d.s_in)),
-                 env_int("DELIMIT_DGRAD_STAGED", 0) != 0, gemm_cluster(2), dX, lddx, st);
+  const int bn = kmajor ? kDgradBN : pick_bn(Ns, d.s_in);
+  return run_vox(ma, B, p, env_int("DELIMIT_DGRAD_BN", bn), env_int("DELIMIT_DGRAD_STAGED", 0) != 0,
+                 gemm_cluster(2), dX, lddx, st);
 }
 
 template <int BN, int S, int CL, bool SPLIT>

@@ -45,9 +45,11 @@ bool tc_forward_reads_w(const LscDims& d);
 cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const void* Wt, const float* bias, void* Y,
                            int64_t n_vox, int64_t ldx, int64_t ldy, int* err_word, cudaStream_t st,
                            TcParts parts = TcParts{});
-// dX[(s',ci,b), v] = sum_{k in rwin(s')} W[k][s'*in_blk + (ci,b)] dY[k, v]
-cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, void* dX, int64_t n_vox, int64_t lddy,
-                         int64_t lddx, int* err_word, cudaStream_t st, TcParts parts = TcParts{});
+// dX[(s',ci,b), v] = sum_{k in rwin(s')} W[k][s'*in_blk + (ci,b)] dY[k, v].  BF16 reads Wt
+// (K-major) when tc_dgrad_reads_wt(d) and Wt is given, else W.
+bool tc_dgrad_reads_wt(const LscDims& d);
+cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, const void* Wt, void* dX, int64_t n_vox,
+                         int64_t lddy, int64_t lddx, int* err_word, cudaStream_t st, TcParts parts = TcParts{});
 // P[split][(s,co,a)][(s',ci,b)] = sum_{v in split} dY[(s,co,a), v] X[(s',ci,b), v] for s' in win(s),
 // P[split][(s,co,a)][rows_in] = sum_{v in split} dY[(s,co,a), v] (from dY_sum: the BF16 dY, or
 // the FP32 dY when the operands are split; lddy_sum its row stride).  The partials are
