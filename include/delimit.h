@@ -364,7 +364,8 @@ delimit_status delimit_set_tensor_cores(int enable);
  * time}, ...} into buf (truncated to cap - 1 characters); it returns the full
  * length.  Names: signal2sh_tc, sh2signal_tc, signal2sh_bwd_tc,
  * sh2signal_bwd_tc, transform_simt, lsc_build_w, lsc_fwd_gemm, lsc_dgrad_gemm,
- * lsc_wgrad_gemm, lsc_rowsum, lsc_reduce_dw, lsc_gemm_simt, lsc_wgrad_simt.
+ * lsc_wgrad_gemm (the _f32 suffix for split FP32 operands), lsc_rowsum (FP32 and
+ * single-CTA paths), split_bf16x3, lsc_reduce_dw, lsc_gemm_simt, lsc_wgrad_simt.
  * No counterpart in the paper. */
 delimit_status delimit_trace_enable(int enable);
 int64_t delimit_trace_summary(char* buf, size_t cap);

@@ -98,7 +98,8 @@ struct WgradArgs {
 cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int max_N, int splits, int act_t,
                               cudaStream_t st);
 
-// dw[co,s,ci,s',k] = sum_{a,b} M[s][k][a][b] sum_split P[split][(s,co,a)][(s',ci,b)];  db[co,s] = sum_a q[s][a] rowsum
+// dw[co,s,ci,s',k] = sum_{a,b} M_{s,s'}[k][a][b] sum_split P[split][(s,co,a)][(s',ci,b)];
+// db[co,s] = sum_a q[s][a] sum_split P[split][(s,co,a)][rows_in] (the row sums of dY)
 // scratch: reduce_dw_scratch_floats(d) floats of partial sums
 size_t reduce_dw_scratch_floats(const LscDims& d);
 // P element (row r, column c) of split z at z * split_stride + r * p_rs + c * p_cs; with
