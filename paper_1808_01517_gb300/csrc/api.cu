@@ -617,13 +617,14 @@ int wgrad_splits(const LscDims& d, int64_t n_vox, int64_t* vps) {
   return splits;
 }
 
-// Whether the operator build writes the transposed operator Wt: the CUDA-core forward
-// always reads it, the tensor-core forward when W's column blocks carry padding, and the
-// BF16 tensor-core input gradient when it can read Wt as its K-major operator.  The same
-// answer in a forward and the backward that follows keeps DELIMIT_LSC_OPERATOR_READY
-// valid between them.
+// Whether the operator build writes the transposed operator Wt (the CUDA-core forward
+// always reads it; the tensor-core forward only when W's column blocks carry padding).
+// The same answer in a forward and the backward that follows keeps
+// DELIMIT_LSC_OPERATOR_READY valid between them.  (The BF16 tensor-core input gradient
+// transposes W into Wt itself when the build did not write it.)
 bool needs_wt(const LscDims& d, bool tc, delimit_dtype t) {
-  return !tc || !tc_forward_reads_w(d) || (t == DELIMIT_BF16 && tc_dgrad_reads_wt(d));
+  (void)t;
+  return !tc || !tc_forward_reads_w(d);
 }
 
 bool make_plan(const delimit_lsc_geometry* g, int64_t n_vox, int c_in, int c_out, delimit_dtype t, LscPlan& p) {
@@ -829,7 +830,14 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
       e = tc_lsc_dgrad(d, dY3, base + p.off_W3, nullptr, d_in, n_vox, p.ld3, ld_in, g->err_word, cs, parts);
       if (e != cudaSuccess) return cuda_fail(e, "tensor-core FP32 LSC input-gradient launch");
     } else if (act_t == DELIMIT_BF16 && all_fed && tc) {
-      e = tc_lsc_dgrad(d, d_out, W, needs_wt(d, tc, act_t) ? Wt : nullptr, d_in, n_vox, ld_out, ld_in, g->err_word, cs);
+      // the K-major operator of the input gradient: Wt as built, else transposed from W here
+      // (a plain transpose: without block padding W is [rows_out][rows_in], Wt [rows_in][rows_out])
+      const bool wt_k = tc_dgrad_reads_wt(d);
+      if (wt_k && !needs_wt(d, tc, act_t)) {
+        e = transpose_bf16(W, d.rows_out, d.ldW, d.ldW, Wt, d.ldWt, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "operator transpose launch");
+      }
+      e = tc_lsc_dgrad(d, d_out, W, wt_k ? Wt : nullptr, d_in, n_vox, ld_out, ld_in, g->err_word, cs);
       if (e != cudaSuccess) return cuda_fail(e, "tensor-core LSC input-gradient launch");
     } else {
       RowGemmArgs a;

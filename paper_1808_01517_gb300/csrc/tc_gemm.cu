@@ -1004,6 +1004,44 @@ __global__ void __launch_bounds__(256) split3_kernel(const float* __restrict__ x
   }
 }
 
+// out[c * ldo + r] = in[r * ldi + c] for r < rows, c < cols (BF16), through 64 x 64 tiles in
+// shared memory: the input-gradient GEMM's K-major operator Wt from W.
+__global__ void __launch_bounds__(256) transpose_bf16_kernel(const __nv_bfloat16* __restrict__ in, int64_t rows,
+                                                             int64_t cols, int64_t ldi, __nv_bfloat16* __restrict__ out,
+                                                             int64_t ldo) {
+  __shared__ __nv_bfloat16 tile[64][66];
+  const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int i = ty; i < 64; i += 8) {
+    const int64_t r = r0 + i;
+#pragma unroll
+    for (int j = tx; j < 64; j += 32) {
+      const int64_t c = c0 + j;
+      tile[i][j] = (r < rows && c < cols) ? in[r * ldi + c] : __float2bfloat16_rn(0.f);
+    }
+  }
+  __syncthreads();
+  for (int i = ty; i < 64; i += 8) {
+    const int64_t c = c0 + i;
+#pragma unroll
+    for (int j = tx; j < 64; j += 32) {
+      const int64_t r = r0 + j;
+      if (c < cols && r < rows) out[c * ldo + r] = tile[j][i];
+    }
+  }
+}
+
+cudaError_t transpose_bf16(const void* in, int64_t rows, int64_t cols, int64_t ldi, void* out, int64_t ldo,
+                           cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  TraceScope trace("lsc_transpose_w", st);
+  const dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
+  transpose_bf16_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(in), rows, cols, ldi,
+                                              reinterpret_cast<__nv_bfloat16*>(out), ldo);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t split_bf16x3(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* out, int64_t ldo,
                          int64_t part_stride, cudaStream_t st) {
   if (rows <= 0 || ldo <= 0) return cudaSuccess;

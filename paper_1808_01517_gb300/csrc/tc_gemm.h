@@ -59,6 +59,9 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
                          int splits, int64_t vox_per_split, int64_t n_vox, int64_t lddy, int64_t ldx, int* err_word,
                          cudaStream_t st, TcParts parts = TcParts{}, const void* dY_sum = nullptr,
                          int64_t lddy_sum = 0);
+// out[c * ldo + r] = in[r * ldi + c] for r < rows, c < cols (BF16)
+cudaError_t transpose_bf16(const void* in, int64_t rows, int64_t cols, int64_t ldi, void* out, int64_t ldo,
+                           cudaStream_t st);
 // out[p * part_stride + r * ldo + c] = part p of x[r * ldx + c] (x = x0 + x1 + x2, each part the
 // BF16 rounding of what the earlier parts leave), for r < rows, c < cols; columns [cols, ldo)
 // of every part row are zeroed.  ldx a multiple of 4, ldo of 8, both pointers 16-byte aligned.
