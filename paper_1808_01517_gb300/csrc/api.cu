@@ -277,8 +277,7 @@ static delimit_status run_transform(const delimit_sh_basis* b, const void* X, vo
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core transform launch");
     return DELIMIT_OK;
   }
-  TransformArgs a;
-  std::memset(&a, 0, sizeof a);
+  TransformArgs a{};  // every member zero (or its default)
   int max_out = 0;
   for (int s = 0; s < S; ++s) {
     const ShellHost& sh = b->h.shells[s];
@@ -330,8 +329,7 @@ delimit_status delimit_signal2sh_gather(const delimit_sh_basis* b, const void* d
   if (st != DELIMIT_OK) return st;
   if ((st = check_act(sh, ld_sh, n, out_t, "sh")) != DELIMIT_OK) return st;
   const int N = b->h.N, S = int(b->h.shells.size());
-  TransformArgs a;
-  std::memset(&a, 0, sizeof a);
+  TransformArgs a{};  // every member zero (or its default)
   int max_out = 0;
   for (int s = 0; s < S; ++s) {
     const ShellHost& shl = b->h.shells[s];
