@@ -172,6 +172,22 @@ def test_workspace_size_is_monotone(table3):
     assert lg.workspace_size(65536, 0, 64, L.BF16, False) == 0
 
 
+def test_fp32_workspace_holds_the_split_operands(table3):
+    """FP32 activations on the tensor cores keep three BF16 parts of the LSC input (and,
+    backward, of dY) per voxel: the workspace grows with the voxel count by at least
+    3 x 2 bytes per input row (forward) and per input and output row (backward) more
+    than the BF16 workspace does."""
+    dirs, bvals = table3
+    lb = L.SHBasis(dirs, bvals, 8, 0.006, host_only=True)
+    lg = L.LSCGeometry(lb, 8, 3, np.deg2rad(25), 4, 12, "adjacent", host_only=True)
+    rows_in, rows_out = 3 * 16 * 45, 3 * 64 * 45
+    for backward, rows in ((False, rows_in), (True, rows_in + rows_out)):
+        grow = {}
+        for t in (L.BF16, L.F32):
+            grow[t] = lg.workspace_size(2 * 65536, 16, 64, t, backward) - lg.workspace_size(65536, 16, 64, t, backward)
+        assert grow[L.F32] - grow[L.BF16] >= 65536 * rows * 3 * 2
+
+
 def test_eval_only_basis():
     g = synth.hemisphere_directions(30, seed=8)
     b = np.full(30, 1000.0)
