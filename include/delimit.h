@@ -350,6 +350,14 @@ delimit_status delimit_lsc_forward_noalloc(const delimit_lsc_geometry* geom, con
  * 0x2100, CUDA if the synchronisation failed, OK otherwise. */
 delimit_status delimit_device_error(void* stream, int* code);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): launches one
+ * CTA on `stream` whose thread waits, through the same bounded wait the tensor-core
+ * kernels use, on an mbarrier that nothing arrives at.  After the wait limit (2 s) it
+ * records code 0x7F00 in the device error word and returns, so that the next
+ * delimit_device_error reports DEVICE_TIMEOUT and the context stays usable.  Returns
+ * CUDA if the launch fails. */
+delimit_status delimit_selftest_wait_timeout(void* stream);
+
 /* Process-wide switch, default 1: BF16 steps, and the LSC GEMMs of F32 calls
  * (as three-part BF16 splits), run on the tcgen05 tensor-core kernels where
  * their shape rules allow, else on the CUDA-core kernels.  0 forces the

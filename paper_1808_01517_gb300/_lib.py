@@ -65,6 +65,7 @@ SIGNATURES = {
     "delimit_lsc_geometry_info": (C.c_int, [_vp, _ip, _ip, _ip, _ip, _ip, _i64p]),
     "delimit_lsc_geometry_tables": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _i64p, _i64p, _i64p, C.POINTER(C.c_ubyte)]),
     "delimit_lsc_neighbour_table": (C.c_int, [_vp, C.c_int, C.c_int, _i64p, _i64p, C.POINTER(C.c_int32)]),
+    "delimit_selftest_wait_timeout": (C.c_int, [_vp]),
     "delimit_lsc_workspace_size": (C.c_size_t, [_vp, _i64, C.c_int, C.c_int, C.c_int, C.c_int]),
     "delimit_lsc_forward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64, C.c_int, C.c_uint,
                                       _vp, C.c_size_t, _vp]),

@@ -921,6 +921,16 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
   return DELIMIT_OK;
 }
 
+delimit_status delimit_selftest_wait_timeout(void* stream) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(DELIMIT_ERR_CUDA, "no current CUDA device");
+  int* wd = error_word_for_current_device();
+  if (!wd) return fail(DELIMIT_ERR_CUDA, "no device error word");
+  const cudaError_t e = launch_wait_probe(wd, kErrWaitProbe, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wait probe launch");
+  return DELIMIT_OK;
+}
+
 delimit_status delimit_device_error(void* stream, int* code) {
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaStreamSynchronize(cs);

@@ -45,6 +45,7 @@ cudaError_t launch_transform_simt(const TransformArgs& a, int n_groups, int max_
 cudaError_t launch_transform_gather(const TransformArgs& a, int n_groups, int max_out, int in_t, int out_t,
                                     cudaStream_t st);
 constexpr int kErrGatherIndex = 0x2100;  // device error word: a gather index outside [0, n_src)
+constexpr int kErrWaitProbe = 0x7F00;    // device error word: the bounded-wait self-test ran out
 
 // ---- LSC ----
 struct LscDims {

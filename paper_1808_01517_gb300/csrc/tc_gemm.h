@@ -68,6 +68,10 @@ cudaError_t transpose_bf16(const void* in, int64_t rows, int64_t cols, int64_t l
 cudaError_t split_bf16x3(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* out, int64_t ldo,
                          int64_t part_stride, cudaStream_t st);
 
+// one CTA waiting on an mbarrier nothing arrives at, through the kernels' bounded wait:
+// after the limit (2 s) the error word gets `code` and the kernel returns
+cudaError_t launch_wait_probe(int* err, int code, cudaStream_t st);
+
 // process-wide switch (default on): when off every BF16 step runs on the CUDA-core kernels
 void tc_set_enabled(bool on);
 bool tc_enabled();
