@@ -174,6 +174,26 @@ def chain_inputs(cfg, dirs, bvals, dtype, rank=0):
     return s_in, ds_out, w, b
 
 
+def time_tables(cfg, dirs, bvals, repeats=3):
+    """Host FP64 table build (Sec. 2.2, 2.3; built once per gradient table, outside every timed
+    step): the per-shell basis and regularised pseudo-inverse, then the LSC geometry (kernel
+    points, basis at the kernel points, collapse matrices).  Host-only handles, so no device
+    upload is timed; best of `repeats`."""
+    from paper_1808_01517_gb300 import _lib as L
+    best_b = best_g = float("inf")
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        basis = L.SHBasis(dirs, bvals, cfg.order, cfg.lam, host_only=True)
+        t1 = time.perf_counter()
+        geom = L.LSCGeometry(basis, cfg.l_in, basis.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings, cfg.sectors,
+                             cfg.window, host_only=True, neighbours=not cfg.resample)
+        t2 = time.perf_counter()
+        best_b, best_g = min(best_b, t1 - t0), min(best_g, t2 - t1)
+        del geom, basis
+    return {"sh_basis_ms": 1e3 * best_b, "lsc_geometry_ms": 1e3 * best_g, "precision": "f64",
+            "where": "host, one thread, host-only handles", "repeats": repeats}
+
+
 def run_fp32_leg(ch, cfg, dirs, bvals, idx, steps, tensor_cores):
     """The chain with FP32 activations on the inputs of the BF16 chain `ch`: voxels/s,
     per-call times and error on sampled voxels against the FP64 oracle.  tensor_cores:
@@ -460,6 +480,8 @@ def main():
         extras["resampling_free"] = run_chain_leg(replace(cfg, resample=False), dirs, bvals)
         # ---- stand-alone transforms at 1,048,576 voxels (FP32 and BF16-in / FP32-out) ----
         extras["transforms"] = run_transforms(cfg, dirs, bvals, args.transform_vox, hbm)
+        # ---- FP64 table build on the host (once per gradient table) ----
+        extras["tables"] = time_tables(cfg, dirs, bvals)
         # ---- oracle on the host cores ----
         vps, nv, tw = time_oracle(cfg, dirs, bvals, args.cpu_seconds)
         extras["cpu_baseline"] = {"value": vps, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
@@ -482,6 +504,7 @@ def main():
         line["transforms"] = extras.get("transforms")
         line["mixed_orders_all_shells"] = extras.get("mixed_orders_all_shells")
         line["resampling_free"] = extras.get("resampling_free")
+        line["tables"] = extras.get("tables")
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -208,3 +208,14 @@ def test_binding_constants_match_header():
                  "WINDOW_SAME", "WINDOW_ADJACENT", "WINDOW_ALL"]:
         assert vals["DELIMIT_" + name] == getattr(L, name), name
     assert vals["DELIMIT_LSC_OPERATOR_READY"] == L.OPERATOR_READY
+
+
+def test_bench_times_the_host_table_build():
+    """The bench's `tables` entry: the FP64 host build of the basis and the LSC geometry on
+    host-only handles (no device needed), once per gradient table."""
+    import bench
+    from dataclasses import replace
+    cfg = replace(bench.workload_config(256), dirs_per_shell=(30, 30), bvals=(1000.0, 2000.0), rings=2, sectors=6)
+    dirs, bvals = bench.table(cfg)
+    rec = bench.time_tables(cfg, dirs, bvals, repeats=1)
+    assert rec["sh_basis_ms"] > 0 and rec["lsc_geometry_ms"] > 0 and rec["precision"] == "f64"
