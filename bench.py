@@ -122,7 +122,28 @@ def blas_threads():
             return int(max(n))
     except Exception:
         pass
-    return os.cpu_count() or 1
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var, "").strip().isdigit() and int(os.environ[var]) > 0:
+            return int(os.environ[var])
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle_single_thread(steps=3, warm=1, timeout_s=240):
+    """The reference arm (the FP64 oracle on 64-voxel samples) in a child interpreter with
+    every BLAS / OpenMP pool held to one thread: the oracle's single-core rate."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", str(steps),
+           "--warmup", str(warm)]
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=timeout_s)
+        rec = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+        return {"value": rec["value"], "unit": rec["unit"], "cores": 1, "kind": "oracle",
+                "sample": f"{steps} x 64 voxels of the same workload, FP64 numpy oracle, one thread"}
+    except Exception as e:  # reported, not fatal: the GPU legs do not depend on it
+        return {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
 
 
 def oracle_inputs(cfg, dirs, bvals, V, seed):
@@ -487,6 +508,7 @@ def main():
         extras["cpu_baseline"] = {"value": vps, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                                   "sample": f"{nv} voxels of the same workload in 64-voxel chunks, "
                                             f"{tw:.1f} s of FP64 numpy oracle work"}
+        extras["cpu_baseline_single_thread"] = time_oracle_single_thread()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -505,6 +527,7 @@ def main():
         line["mixed_orders_all_shells"] = extras.get("mixed_orders_all_shells")
         line["resampling_free"] = extras.get("resampling_free")
         line["tables"] = extras.get("tables")
+        line["cpu_baseline_single_thread"] = extras.get("cpu_baseline_single_thread")
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -219,3 +219,12 @@ def test_bench_times_the_host_table_build():
     dirs, bvals = bench.table(cfg)
     rec = bench.time_tables(cfg, dirs, bvals, repeats=1)
     assert rec["sh_basis_ms"] > 0 and rec["lsc_geometry_ms"] > 0 and rec["precision"] == "f64"
+
+
+def test_bench_times_the_oracle_on_one_thread():
+    """The bench's single-thread oracle leg: a child interpreter with the BLAS pools held to
+    one thread runs the reference arm and its rate is reported."""
+    import bench
+    rec = bench.time_oracle_single_thread(steps=1, warm=0, timeout_s=120)
+    assert "unavailable" not in rec, rec
+    assert rec["value"] > 0 and rec["cores"] == 1
