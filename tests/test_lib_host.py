@@ -110,6 +110,31 @@ def test_lsc_tables_match_oracle(table3):
             np.testing.assert_array_equal(t["row_index"], T4[lb.dir_off[s]:lb.dir_off[s] + lb.m[s]])
 
 
+@pytest.mark.parametrize("order_out,lam,order_in,R,Sec,rad,win", [
+    (0, 0.0, 0, 2, 6, np.deg2rad(20), "adjacent"),   # one coefficient per shell
+    (8, 0.006, 0, 1, 1, np.deg2rad(20), "all"),      # order-0 input, one-point ring (K = 2)
+    (4, 0.0, 4, 1, 1, np.pi / 2, "same"),            # largest radius: every direction a neighbour
+    (2, 0.006, 2, 3, 7, np.pi / 2, "adjacent")])
+def test_degenerate_lsc_tables_match_oracle(order_out, lam, order_in, R, Sec, rad, win):
+    dirs, bvals = synth.multishell_table([30, 30], [1000, 2000], seed=5)
+    lb = L.SHBasis(dirs, bvals, order_out, lam, host_only=True)
+    ob = osh.SHBasisOracle(dirs, bvals, order_out, lam)
+    lg = L.LSCGeometry(lb, order_in, 2, rad, R, Sec, win, host_only=True)
+    og = olsc.LSCOracle(ob, order_in, 2, rad, R, Sec, win)
+    M, q = og.collapse_mats()
+    assert lg.K == 1 + R * Sec
+    for s in range(2):
+        t = lg.tables(s)
+        np.testing.assert_allclose(t["kpts"], og.kpts[s], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(t["M"], M[s], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(t["q"], q[s], rtol=0, atol=1e-12)
+        ip, ix = olsc.neighbour_csr(og.dirs[s], rad)
+        np.testing.assert_array_equal(t["nb_indptr"], ip)
+        np.testing.assert_array_equal(t["nb_indices"], ix)
+    if rad == np.pi / 2:
+        assert (np.diff(ip) == 30).all()
+
+
 def test_resampling_free_tables_match_oracle(table3):
     """Neighbour tables and bins of the resampling-free form are bit-exact against the
     oracle; the per-shell-pair collapse matrices agree to 1e-12."""

@@ -6,6 +6,7 @@
 * Funk-Hecke: a ring-uniform kernel acts per band as multiplication by
   w_0 + sum_r w_r P_l(cos theta_r) (Legendre polynomials from numpy), which
   includes the paper's moving-average example (n = 5, alpha = pi/5, weights 1/6);
+* order 0: the layer reduces to a kernel sum plus sqrt(4 pi) times the bias, for any lambda;
 * brute force: kernel-point sums of a closed-form band-limited function;
 * the algebraically collapsed route equals the literal route;
 * gradients against central finite differences and the adjoint identity.
@@ -93,6 +94,22 @@ def test_identity_for_centre_only_kernel():
     L2 = olsc.LSCOracle(ob2, 8, 1, np.deg2rad(30), 3, 8)
     np.testing.assert_allclose(L2.forward(c, w, np.zeros((1, 1))), ob2.signal2sh(ob2.sh2signal(c)),
                                atol=1e-11)
+
+
+def test_order_zero_is_a_kernel_sum_for_any_lambda():
+    """Order 0 (one coefficient per shell): the interpolant is the constant c / sqrt(4 pi) at
+    every kernel point, so each output direction carries sum_k w c / sqrt(4 pi) + b, and the
+    projection of a constant recovers it exactly for any lambda (the penalty vanishes on
+    l = 0).  Closed form: c_out = sum_{ci, s' in win(s), k} w c + sqrt(4 pi) b."""
+    dirs, bvals = synth.multishell_table([20, 30], [1000, 2000], seed=7)
+    for lam in (0.0, 0.06):
+        ob = osh.SHBasisOracle(dirs, bvals, 0, lam)
+        lsc = olsc.LSCOracle(ob, 0, 2, np.deg2rad(20), 2, 6, "adjacent")
+        c = synth.gaussian((4, 3, 2, 1), 1.0, seed=3, tag="coeffs")
+        w = synth.gaussian((5, 2, 3, 2, lsc.K), 0.1, seed=4)
+        b = synth.gaussian((5, 2), 0.1, seed=5)
+        want = np.einsum("osipk,vip->vos", w, c[..., 0])[..., None] + np.sqrt(4 * np.pi) * b[None, :, :, None]
+        np.testing.assert_allclose(lsc.forward(c, w, b), want, rtol=0, atol=1e-12)
 
 
 @pytest.mark.parametrize("R,Sec,alpha,L", [(1, 5, np.pi / 5, 4), (3, 9, np.deg2rad(30), 8),
