@@ -131,7 +131,7 @@ def blas_threads():
         return os.cpu_count() or 1
 
 
-def time_oracle_single_thread(steps=3, warm=1, timeout_s=240):
+def time_oracle_single_thread(steps=3, warm=1, timeout_s=120):
     """The reference arm (the FP64 oracle on 64-voxel samples) in a child interpreter with
     every BLAS / OpenMP pool held to one thread: the oracle's single-core rate."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
