@@ -440,6 +440,8 @@ def main():
     value = job_throughput(V, world, ms)
     per_call = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]))
                 for i, name in enumerate(Chain.CALLS)}
+    # each step alone, from the event before its first call to the one after its last
+    step_ms = [ev[k][0].elapsed_time(ev[k][len(Chain.CALLS)]) for k in range(K)]
     st, code = L.device_error(torch.cuda.current_stream().cuda_stream)
     if st != L.OK:
         raise RuntimeError(f"device error word set: {code:#x}")
@@ -512,7 +514,8 @@ def main():
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": max(3, args.warmup), "ms_per_step": ms,
+                "ms_per_step_median": float(np.median(step_ms)), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": cfg.name(), "n_vox": V, "shells": list(cfg.dirs_per_shell),
                            "sh_order": cfg.order, "c_in": cfg.c_in, "c_out": cfg.c_out, "kernel_points": ch.geom.K,
