@@ -50,7 +50,7 @@ typedef enum {
   DELIMIT_OK = 0,
   DELIMIT_ERR_INVALID_ARG = 1,     /* bad size, order, direction, null pointer, ... */
   DELIMIT_ERR_RANK_DEFICIENT = 2,  /* normal equations singular (e.g. lambda = 0, m < N) */
-  DELIMIT_ERR_UNSUPPORTED = 3,     /* valid request outside what this build implements */
+  DELIMIT_ERR_UNSUPPORTED = 3,     /* valid request outside what this library implements */
   DELIMIT_ERR_ALIGNMENT = 4,       /* pointer or row stride violates the 16-byte rule */
   DELIMIT_ERR_CUDA = 5,            /* a CUDA runtime call failed (see delimit_last_error) */
   DELIMIT_ERR_DEVICE_TIMEOUT = 6,  /* a bounded device-side wait ran out */

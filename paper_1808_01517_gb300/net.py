@@ -12,7 +12,7 @@ Architecture (reading of the learned-part configuration):
   LSC(64 -> 1, adjacent shells)                                    -> 3 x 45
   SH2Signal onto each shell's 90 target directions                -> 270 values
 All LSCs use radius 25 deg with 4 rings x 12 sectors.  Activations are BF16,
-master weights FP32 (torch Adam).  The judge is plain SH least-squares
+master weights FP32 (torch Adam).  The comparison is plain SH least-squares
 interpolation: an order-8 fit of the 30 input values (lambda 0.006),
 evaluated on the 90 b=1000 targets and extrapolated to b = 2000, 3000 by
 S_b = S_1000^(b/1000).
@@ -206,7 +206,7 @@ def evaluate(net: SphericalNet, fb: Fallback, data: Data) -> dict:
 def main():
     import argparse
     import json
-    ap = argparse.ArgumentParser(description="Train and judge the LSC network (learned-part configuration)")
+    ap = argparse.ArgumentParser(description="Train the LSC network and compare it with SH least-squares interpolation")
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--train-voxels", type=int, default=10_000_000)
