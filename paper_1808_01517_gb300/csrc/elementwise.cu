@@ -200,13 +200,29 @@ using namespace delimit;
 
 static bool ok_rows(int64_t rows) { return rows >= 1 && rows <= 65535; }
 
+// argument refusal with its reason for delimit_last_error()
+static delimit_status bad_arg(const char* fn, const char* what) {
+  set_last_error(std::string(fn) + ": " + what);
+  return DELIMIT_ERR_INVALID_ARG;
+}
+
+// status of the launches just made, with the CUDA error text on failure
+static delimit_status launch_status(const char* fn) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return DELIMIT_OK;
+  set_last_error(std::string(fn) + ": " + cudaGetErrorString(e));
+  return DELIMIT_ERR_CUDA;
+}
+
+static const char* kActArgs = "need non-NULL pointers, 1 <= rows <= 65535, ld >= n_vox and dtype F32 or BF16";
+
 extern "C" {
 
 delimit_status delimit_leaky_relu(const void* x, void* y, int64_t rows, int64_t n_vox, int64_t ld_x, int64_t ld_y,
                                   float slope, delimit_dtype t, void* stream) {
   if (n_vox == 0) return DELIMIT_OK;
   if (!x || !y || n_vox < 0 || !ok_rows(rows) || ld_x < n_vox || ld_y < n_vox || (t != DELIMIT_F32 && t != DELIMIT_BF16))
-    return DELIMIT_ERR_INVALID_ARG;
+    return bad_arg("delimit_leaky_relu", kActArgs);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   dim3 grid(grid_x(n_vox), (unsigned)rows);
   if (t == DELIMIT_F32) {
@@ -219,7 +235,7 @@ delimit_status delimit_leaky_relu(const void* x, void* y, int64_t rows, int64_t 
                                                       ld_y, slope);
   }
   count_launch();
-  return cudaGetLastError() == cudaSuccess ? DELIMIT_OK : DELIMIT_ERR_CUDA;
+  return launch_status("delimit_leaky_relu");
 }
 
 delimit_status delimit_leaky_relu_backward(const void* y, const void* dy, void* dx, int64_t rows, int64_t n_vox,
@@ -228,7 +244,7 @@ delimit_status delimit_leaky_relu_backward(const void* y, const void* dy, void* 
   if (n_vox == 0) return DELIMIT_OK;
   if (!y || !dy || !dx || n_vox < 0 || !ok_rows(rows) || ld_y < n_vox || ld_dy < n_vox || ld_dx < n_vox ||
       (t != DELIMIT_F32 && t != DELIMIT_BF16))
-    return DELIMIT_ERR_INVALID_ARG;
+    return bad_arg("delimit_leaky_relu_backward", kActArgs);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   dim3 grid(grid_x(n_vox), (unsigned)rows);
   if (t == DELIMIT_F32) {
@@ -243,7 +259,7 @@ delimit_status delimit_leaky_relu_backward(const void* y, const void* dy, void* 
                                                           (__nv_bfloat16*)dx, rows, n_vox, ld_y, ld_dy, ld_dx, slope);
   }
   count_launch();
-  return cudaGetLastError() == cudaSuccess ? DELIMIT_OK : DELIMIT_ERR_CUDA;
+  return launch_status("delimit_leaky_relu_backward");
 }
 
 size_t delimit_mask_compact_workspace_size(int64_t n) {
@@ -254,10 +270,19 @@ size_t delimit_mask_compact_workspace_size(int64_t n) {
 
 delimit_status delimit_mask_compact(const uint8_t* mask, int64_t n, int64_t* index, int64_t* count, void* workspace,
                                     size_t ws_bytes, void* stream) {
-  if (n < 0 || !count || (n > 0 && (!mask || !index))) return DELIMIT_ERR_INVALID_ARG;
+  if (n < 0 || !count || (n > 0 && (!mask || !index)))
+    return bad_arg("delimit_mask_compact", "need n >= 0, count non-NULL, and mask and index non-NULL when n > 0");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (n == 0) return cudaMemsetAsync(count, 0, sizeof(int64_t), st) == cudaSuccess ? DELIMIT_OK : DELIMIT_ERR_CUDA;
-  if (ws_bytes < delimit_mask_compact_workspace_size(n) || !workspace) return DELIMIT_ERR_WORKSPACE;
+  if (n == 0) {
+    const cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int64_t), st);
+    if (e == cudaSuccess) return DELIMIT_OK;
+    set_last_error(std::string("delimit_mask_compact: ") + cudaGetErrorString(e));
+    return DELIMIT_ERR_CUDA;
+  }
+  if (ws_bytes < delimit_mask_compact_workspace_size(n) || !workspace) {
+    set_last_error("delimit_mask_compact: workspace NULL or smaller than delimit_mask_compact_workspace_size(n)");
+    return DELIMIT_ERR_WORKSPACE;
+  }
   const int64_t nb = (n + kCompactBlock * kCompactPer - 1) / (kCompactBlock * kCompactPer);
   int64_t* counts = static_cast<int64_t*>(workspace);
   compact_count_kernel<<<(unsigned)nb, kCompactBlock, 0, st>>>(mask, n, counts);
@@ -266,7 +291,7 @@ delimit_status delimit_mask_compact(const uint8_t* mask, int64_t n, int64_t* ind
   count_launch();
   compact_write_kernel<<<(unsigned)nb, kCompactBlock, 0, st>>>(mask, n, counts, index);
   count_launch();
-  return cudaGetLastError() == cudaSuccess ? DELIMIT_OK : DELIMIT_ERR_CUDA;
+  return launch_status("delimit_mask_compact");
 }
 
 delimit_status delimit_gather_voxels(const void* src, int64_t ld_src, int64_t n_src, int64_t rows, const int64_t* index,
@@ -274,7 +299,8 @@ delimit_status delimit_gather_voxels(const void* src, int64_t ld_src, int64_t n_
   if (n == 0) return DELIMIT_OK;
   if (!src || !dst || !index || n < 0 || n_src < 0 || ld_src < n_src || !ok_rows(rows) || ld_dst < n ||
       (t != DELIMIT_F32 && t != DELIMIT_BF16))
-    return DELIMIT_ERR_INVALID_ARG;
+    return bad_arg("delimit_gather_voxels",
+                   "need non-NULL pointers, n >= 0, 0 <= n_src <= ld_src, n <= ld_dst, 1 <= rows <= 65535, F32 or BF16");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   dim3 grid(grid_x(n), (unsigned)rows);
   if (t == DELIMIT_F32)
@@ -283,7 +309,7 @@ delimit_status delimit_gather_voxels(const void* src, int64_t ld_src, int64_t n_
     gather_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16*)src, ld_src, n_src, index, n,
                                                        (__nv_bfloat16*)dst, ld_dst);
   count_launch();
-  return cudaGetLastError() == cudaSuccess ? DELIMIT_OK : DELIMIT_ERR_CUDA;
+  return launch_status("delimit_gather_voxels");
 }
 
 delimit_status delimit_scatter_voxels(const void* src, int64_t ld_src, int64_t rows, const int64_t* index, int64_t n,
@@ -291,7 +317,8 @@ delimit_status delimit_scatter_voxels(const void* src, int64_t ld_src, int64_t r
   if (n == 0) return DELIMIT_OK;
   if (!src || !dst || !index || n < 0 || n_dst < 0 || ld_dst < n_dst || !ok_rows(rows) || ld_src < n ||
       (t != DELIMIT_F32 && t != DELIMIT_BF16))
-    return DELIMIT_ERR_INVALID_ARG;
+    return bad_arg("delimit_scatter_voxels",
+                   "need non-NULL pointers, n >= 0, 0 <= n_dst <= ld_dst, n <= ld_src, 1 <= rows <= 65535, F32 or BF16");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   dim3 grid(grid_x(n), (unsigned)rows);
   if (t == DELIMIT_F32)
@@ -300,7 +327,7 @@ delimit_status delimit_scatter_voxels(const void* src, int64_t ld_src, int64_t r
     scatter_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16*)src, ld_src, index, n,
                                                         (__nv_bfloat16*)dst, ld_dst, n_dst);
   count_launch();
-  return cudaGetLastError() == cudaSuccess ? DELIMIT_OK : DELIMIT_ERR_CUDA;
+  return launch_status("delimit_scatter_voxels");
 }
 
 }  // extern "C"

@@ -9,6 +9,7 @@ import ctypes as C
 import glob
 import os
 import re
+import threading
 
 import numpy as np
 import pytest
@@ -253,3 +254,35 @@ def test_bench_times_the_oracle_on_one_thread():
     rec = bench.time_oracle_single_thread(steps=1, warm=0, timeout_s=120)
     assert "unavailable" not in rec, rec
     assert rec["value"] > 0 and rec["cores"] == 1
+
+
+def test_every_entry_point_refuses_null_pointers_with_a_reason():
+    """Each compute or table entry point, given NULL pointers (and non-zero sizes), returns
+    INVALID_ARG and leaves a message in delimit_last_error, without touching a device."""
+    lib = L.get()
+    device_calls = {"delimit_device_error", "delimit_selftest_wait_timeout"}
+    no_status = {"delimit_version", "delimit_kernel_launches", "delimit_status_string", "delimit_last_error",
+                 "delimit_trace_enable", "delimit_trace_summary", "delimit_set_tensor_cores",
+                 "delimit_lsc_workspace_size", "delimit_mask_compact_workspace_size",
+                 "delimit_sh_basis_destroy", "delimit_lsc_geometry_destroy"}
+    ints = (C.c_int, C.c_int64, C.c_size_t, C.c_uint32, C.c_uint64, C.c_long, C.c_uint)
+    checked = 0
+    for name, (_, args) in sorted(L.SIGNATURES.items()):
+        if name in device_calls or name in no_status:
+            continue
+        vals = [0.0 if a in (C.c_double, C.c_float) else (64 if a in ints else None) for a in args]
+        out = {}
+
+        def run():  # the message is thread-local: a fresh thread starts without one
+            out["st"] = getattr(lib, name)(*vals)
+            out["msg"] = lib.delimit_last_error()
+        t = threading.Thread(target=run)
+        t.start()
+        t.join()
+        assert out["st"] == L.ERR_INVALID_ARG, (name, out["st"])
+        assert out["msg"], name
+        checked += 1
+    assert checked >= 20
+    # NULL handles are accepted by destroy (no-op) and give a zero workspace size
+    assert lib.delimit_sh_basis_destroy(None) == L.OK and lib.delimit_lsc_geometry_destroy(None) == L.OK
+    assert lib.delimit_lsc_workspace_size(None, 64, 1, 1, L.BF16, 0) == 0
