@@ -503,6 +503,7 @@ def main():
         extras["resampling_free"] = run_chain_leg(replace(cfg, resample=False), dirs, bvals)
         # ---- stand-alone transforms at 1,048,576 voxels (FP32 and BF16-in / FP32-out) ----
         extras["transforms"] = run_transforms(cfg, dirs, bvals, args.transform_vox, hbm)
+        extras["transforms"]["cpu_baseline"] = time_oracle_transforms(cfg, dirs, bvals)
         # ---- FP64 table build on the host (once per gradient table) ----
         extras["tables"] = time_tables(cfg, dirs, bvals)
         # ---- oracle on the host cores ----
@@ -615,6 +616,28 @@ def run_transforms(cfg, dirs, bvals, V, hbm_gbs, steps=20, warm=3, n_check=4096)
     out["config"] = {"n_vox": V, "channels": 1, "shells": list(cfg.dirs_per_shell), "sh_order": cfg.order,
                      "check_voxels": n_check, "timed_steps": steps}
     return out
+
+
+def time_oracle_transforms(cfg, dirs, bvals, n_vox=131072, reps=3):
+    """The FP64 oracle's Signal2SH and SH2Signal (Sec. 2.2) on a bounded host sample of the
+    stand-alone transform workload (one channel, the full direction table): voxels/s, best
+    of ``reps``, on the host's BLAS threads."""
+    from oracle import sh as osh
+    from paper_1808_01517_gb300 import synth
+    ob = osh.SHBasisOracle(dirs, bvals, cfg.order, cfg.lam)
+    sig = synth.gaussian((n_vox, 1, dirs.shape[0]), 1.0, seed=cfg.seed, tag="grads", sub=11)
+    sh = synth.gaussian((n_vox, 1, ob.n_shells, ob.n_coef), 1.0, seed=cfg.seed, tag="coeffs", sub=11)
+    best = {}
+    for name, fn, x in (("signal2sh", ob.signal2sh, sig), ("sh2signal", ob.sh2signal, sh)):
+        dt = float("inf")
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn(x)
+            dt = min(dt, time.perf_counter() - t0)
+        best[f"{name}_voxels_per_s"] = n_vox / dt
+    best.update({"kind": "oracle", "cores": blas_threads(),
+                 "sample": f"{n_vox} voxels, one channel, FP64 numpy oracle, best of {reps}"})
+    return best
 
 
 def run_e2e(ch, steps):

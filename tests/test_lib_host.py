@@ -286,3 +286,12 @@ def test_every_entry_point_refuses_null_pointers_with_a_reason():
     # NULL handles are accepted by destroy (no-op) and give a zero workspace size
     assert lib.delimit_sh_basis_destroy(None) == L.OK and lib.delimit_lsc_geometry_destroy(None) == L.OK
     assert lib.delimit_lsc_workspace_size(None, 64, 1, 1, L.BF16, 0) == 0
+
+
+def test_bench_times_the_oracle_transforms():
+    import bench
+    from dataclasses import replace
+    cfg = replace(bench.workload_config(256), dirs_per_shell=(30, 30), bvals=(1000.0, 2000.0))
+    dirs, bvals = bench.table(cfg)
+    rec = bench.time_oracle_transforms(cfg, dirs, bvals, n_vox=512, reps=1)
+    assert rec["signal2sh_voxels_per_s"] > 0 and rec["sh2signal_voxels_per_s"] > 0 and rec["kind"] == "oracle"
