@@ -295,3 +295,25 @@ def test_bench_times_the_oracle_transforms():
     dirs, bvals = bench.table(cfg)
     rec = bench.time_oracle_transforms(cfg, dirs, bvals, n_vox=512, reps=1)
     assert rec["signal2sh_voxels_per_s"] > 0 and rec["sh2signal_voxels_per_s"] > 0 and rec["kind"] == "oracle"
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: with the shared library absent and its build failing, loading raises,
+    and a layer call on host tensors raises instead of computing anything on the CPU."""
+    from paper_1808_01517_gb300 import build as _build
+    from paper_1808_01517_gb300 import layers
+    import torch
+
+    def no_build(*args, **kwargs):
+        raise RuntimeError("nvcc unavailable")
+    monkeypatch.setattr(L, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "libdelimit.so"))
+    monkeypatch.setattr(_build, "build", no_build)
+    with pytest.raises(RuntimeError, match="nvcc unavailable"):
+        L.get()
+    monkeypatch.undo()
+    dirs, bvals = synth.multishell_table([30], [1000], seed=1)
+    basis = L.SHBasis(dirs, bvals, 4, 0.006, host_only=True)
+    if not torch.cuda.is_available():
+        with pytest.raises(Exception):
+            layers.transform("signal2sh", basis, torch.zeros((30, 64)), 1)
