@@ -1,6 +1,7 @@
 """The C ABI from a plain C program (tests/c_abi/host_only.c): compiled with gcc against
 include/delimit.h, linked to the built library and run without a GPU (host-only
-handles, table queries, error codes)."""
+handles, table queries, error codes); and the host FP64 table code under the address and
+undefined-behaviour sanitizers."""
 import os
 import shutil
 import subprocess
@@ -30,3 +31,26 @@ def test_c_program_uses_the_abi(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "c abi ok" in r.stdout
+
+
+def test_host_tables_under_address_and_undefined_sanitizers(tmp_path):
+    """csrc/host_tables.cpp (the FP64 basis, pseudo-inverse, kernel geometry, collapse and
+    neighbour tables) built with -fsanitize=address,undefined beside a driver
+    (tests/c_abi/host_tables_sanitized.cpp) that runs every table builder over orders
+    0-8, both lambdas, every window, both LSC forms and the refused inputs."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    flags = ["-std=c++17", "-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
+             "-fno-omit-frame-pointer"]
+    probe = tmp_path / "probe.cpp"
+    probe.write_text("int main() { return 0; }\n")
+    if subprocess.run([gxx, *flags, str(probe), "-o", str(tmp_path / "probe")], capture_output=True).returncode:
+        pytest.skip("sanitizer runtimes not available")
+    exe = str(tmp_path / "host_tables_sanitized")
+    csrc = os.path.join(ROOT, "paper_1808_01517_gb300", "csrc")
+    subprocess.run([gxx, *flags, "-Wall", "-Werror", "-I", csrc, os.path.join(HERE, "c_abi", "host_tables_sanitized.cpp"),
+                    os.path.join(csrc, "host_tables.cpp"), "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "host tables ok" in r.stdout
