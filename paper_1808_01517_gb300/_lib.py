@@ -99,14 +99,18 @@ class DelimitError(RuntimeError):
 
 
 def get():
-    """The loaded library (built in-tree on first use if needed)."""
+    """The loaded library (built in-tree on first use if needed).  DELIMIT_LIB names
+    another build of it to load instead (e.g. the sanitized host build); it must exist."""
     global _lib
     if _lib is not None:
         return _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if not os.path.exists(path) or os.environ.get("DELIMIT_REBUILD"):
+            path = os.environ.get("DELIMIT_LIB") or _build.LIB
+            if os.environ.get("DELIMIT_LIB"):
+                if not os.path.exists(path):
+                    raise RuntimeError(f"DELIMIT_LIB={path} does not exist")
+            elif not os.path.exists(path) or os.environ.get("DELIMIT_REBUILD"):
                 path = _build.build()
             lib = C.CDLL(path)
             for name, (res, args) in SIGNATURES.items():

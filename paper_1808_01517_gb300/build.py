@@ -45,16 +45,30 @@ def _digest(paths, extra=""):
     return h.hexdigest()
 
 
-def build(verbose: bool = False, jobs: int = 8) -> str:
-    """Compile every unit (if stale) and link libdelimit.so; returns the library path."""
-    os.makedirs(OUT, exist_ok=True)
+# host code of the sanitized build: address and undefined-behaviour sanitizers (the
+# device code is compiled as in the regular build)
+SANITIZE_OUT = os.path.join(OUT, "sanitize")
+SANITIZE_LIB = os.path.join(SANITIZE_OUT, "libdelimit.so")
+SANITIZE_FLAGS = ["-Xcompiler=-fsanitize=address", "-Xcompiler=-fsanitize=undefined",
+                  "-Xcompiler=-fno-omit-frame-pointer", "-Xcompiler=-fno-sanitize-recover=all"]
+
+
+def build(verbose: bool = False, jobs: int = 8, sanitize: bool = False) -> str:
+    """Compile every unit (if stale) and link libdelimit.so; returns the library path.
+
+    sanitize: a separate build under ``_build/sanitize`` whose host code runs under the
+    address and undefined-behaviour sanitizers (load it with the sanitizer runtimes
+    preloaded), for checking the host side of the library on a machine without a GPU."""
+    out_dir, lib_path = (SANITIZE_OUT, SANITIZE_LIB) if sanitize else (OUT, LIB)
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     hdr = _digest(_headers())
-    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
+    host_opt = ["-Xcompiler", "-O1", "-g"] + SANITIZE_FLAGS if sanitize else ["-Xcompiler", "-O3"]
+    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"] + host_opt + [
              "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")] + ARCH
     objs, jobs_list = [], []
     for src in _sources():
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         stamp = obj + ".sha"
         key = _digest([src], hdr + " ".join(flags))
         objs.append(obj)
@@ -80,15 +94,15 @@ def build(verbose: bool = False, jobs: int = 8) -> str:
         for out in ex.map(run, jobs_list):
             if verbose and out.strip():
                 print(out)
-    relink = bool(jobs_list) or not os.path.exists(LIB)
+    relink = bool(jobs_list) or not os.path.exists(lib_path)
     if relink:
-        tmp = LIB + ".tmp"
-        cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
+        tmp = lib_path + ".tmp"
+        cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"] + (SANITIZE_FLAGS if sanitize else [])
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

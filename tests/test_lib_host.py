@@ -306,6 +306,7 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
 
     def no_build(*args, **kwargs):
         raise RuntimeError("nvcc unavailable")
+    monkeypatch.delenv("DELIMIT_LIB", raising=False)
     monkeypatch.setattr(L, "_lib", None)
     monkeypatch.setattr(_build, "LIB", str(tmp_path / "libdelimit.so"))
     monkeypatch.setattr(_build, "build", no_build)
