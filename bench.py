@@ -522,7 +522,10 @@ def main():
                            "sh_order": cfg.order, "c_in": cfg.c_in, "c_out": cfg.c_out, "kernel_points": ch.geom.K,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "kernels": kernels, "per_call": per_call_roof, "clocks": clk,
-                "gpu_launches": int(launches)}
+                "gpu_launches": int(launches),
+                "device": {"gpu": torch.cuda.get_device_name(local),
+                           "sms": torch.cuda.get_device_properties(local).multi_processor_count,
+                           "host_cores": os.cpu_count()}}
         line.update({k: v for k, v in extras.items() if k in ("e2e", "cpu_baseline")})
         line["fp32"] = extras.get("fp32")
         line["fp32_cuda_cores"] = extras.get("fp32_cuda_cores")
