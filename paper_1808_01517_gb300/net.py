@@ -20,6 +20,7 @@ S_b = S_1000^(b/1000).
 from __future__ import annotations
 
 import math
+import os
 import time
 from dataclasses import dataclass, field
 
@@ -155,17 +156,43 @@ class TrainLog:
     batch: int = 0
 
 
+def save_checkpoint(path: str, net: torch.nn.Module, opt, sched, gen: torch.Generator, next_step: int):
+    """What a resumed run needs to continue bit for bit: the weights, the optimizer's
+    moments, the learning-rate schedule, the batch sampler's generator state and the
+    next step.  Written to a temporary file and renamed, so a crash mid-write leaves the
+    previous checkpoint intact."""
+    state = {"net": net.state_dict(), "opt": opt.state_dict(), "sched": sched.state_dict(),
+             "gen": gen.get_state(), "next_step": int(next_step)}
+    tmp = path + ".tmp"
+    torch.save(state, tmp)
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str, net: torch.nn.Module, opt, sched, gen: torch.Generator) -> int:
+    """Restores what save_checkpoint wrote into freshly built objects; returns the next step."""
+    state = torch.load(path, map_location="cpu", weights_only=True)
+    net.load_state_dict(state["net"])
+    opt.load_state_dict(state["opt"])
+    sched.load_state_dict(state["sched"])
+    gen.set_state(state["gen"])
+    return int(state["next_step"])
+
+
 def train(net: SphericalNet, data: Data, steps: int, batch: int, lr: float = 2e-3, seed: int = 0,
-          log_every: int = 100) -> TrainLog:
+          log_every: int = 100, checkpoint: str = "", checkpoint_every: int = 0, resume: str = "") -> TrainLog:
+    """Adam with a cosine schedule on random batches of ``data``.  checkpoint /
+    checkpoint_every: write a checkpoint every that many steps; resume: continue from
+    one (the same steps, batch and lr as the run that wrote it)."""
     opt = torch.optim.Adam(net.parameters(), lr=lr)
     sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, T_max=max(1, steps))
     gen = torch.Generator(device=data.x.device)
     gen.manual_seed(seed)
+    start = load_checkpoint(resume, net, opt, sched, gen) if resume else 0
     n = data.x.shape[1]
-    log = TrainLog(steps=steps, batch=batch)
+    log = TrainLog(steps=steps - start, batch=batch)  # the steps this call runs
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for step in range(steps):
+    for step in range(start, steps):
         idx = torch.randint(0, n, (batch,), generator=gen, device=data.x.device)
         pred = net(data.x[:, idx])
         loss = torch.mean((pred.float() - data.y[:, idx].float()) ** 2)
@@ -175,6 +202,8 @@ def train(net: SphericalNet, data: Data, steps: int, batch: int, lr: float = 2e-
         sched.step()
         if step % log_every == 0 or step == steps - 1:
             log.losses.append((step, float(loss)))
+        if checkpoint and checkpoint_every > 0 and (step + 1) % checkpoint_every == 0:
+            save_checkpoint(checkpoint, net, opt, sched, gen, step + 1)
     torch.cuda.synchronize()
     log.seconds = time.perf_counter() - t0
     return log
@@ -213,6 +242,9 @@ def main():
     ap.add_argument("--test-voxels", type=int, default=1_000_000)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--save", default="")
+    ap.add_argument("--checkpoint", default="", help="checkpoint file written during training")
+    ap.add_argument("--checkpoint-every", type=int, default=0)
+    ap.add_argument("--resume", default="", help="continue from this checkpoint")
     args = ap.parse_args()
     cfg = NetConfig()
     dirs, bvals, sel = tables(cfg)
@@ -220,10 +252,11 @@ def main():
     fb = Fallback(cfg, dirs[sel], dirs, bvals)
     tr = make_data(cfg, args.train_voxels, seed=cfg.seed)
     te = make_data(cfg, args.test_voxels, seed=cfg.seed + 1)
-    log = train(net, tr, args.steps, args.batch, args.lr)
+    log = train(net, tr, args.steps, args.batch, args.lr, checkpoint=args.checkpoint,
+                checkpoint_every=args.checkpoint_every, resume=args.resume)
     res = evaluate(net, fb, te)
     res.update({"steps": args.steps, "batch": args.batch, "train_seconds": log.seconds,
-                "train_voxels_per_s": args.steps * args.batch / log.seconds, "loss_first_last": [log.losses[0],
+                "train_voxels_per_s": log.steps * args.batch / log.seconds, "loss_first_last": [log.losses[0],
                                                                                              log.losses[-1]]})
     if args.save:
         torch.save({"state": net.state_dict(), "cfg": cfg.__dict__, "result": res}, args.save)
