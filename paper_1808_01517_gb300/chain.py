@@ -58,10 +58,9 @@ class Chain:
         self.basis_in = self.basis if cfg.l_in == cfg.order else L.SHBasis(dirs, bvals, cfg.l_in, cfg.lam)
         self.geom = L.LSCGeometry(self.basis, cfg.l_in, self.basis.n_shells, np.deg2rad(cfg.radius_deg), cfg.rings,
                                   cfg.sectors, cfg.window, neighbours=not cfg.resample)
-        V, S, nd = cfg.n_vox, self.basis.n_shells, self.basis.n_dirs
-        N, N_in = self.basis.n_coef, self.basis_in.n_coef
+        V, S = cfg.n_vox, self.basis.n_shells
         ci, co = cfg.c_in, cfg.c_out
-        self.rows = dict(s_in=ci * nd, c_in=S * ci * N_in, c_out=S * co * N, s_out=co * nd)
+        self.rows = self.row_counts(cfg, self.basis, self.basis_in)
         mk = lambda r: layers.empty_act(r, V, dtype, device)  # noqa: E731
         self.s_in, self.c_in_buf = mk(self.rows["s_in"]), mk(self.rows["c_in"])
         self.c_out_buf, self.s_out = mk(self.rows["c_out"]), mk(self.rows["s_out"])
@@ -77,6 +76,14 @@ class Chain:
         self._ws = torch.empty(max(self.ws_f, self.ws_b) + 256, dtype=torch.uint8, device=device)
         self.ws = (self._ws.data_ptr() + 255) // 256 * 256
         self.lib = L.get()
+
+    @staticmethod
+    def row_counts(cfg: ChainConfig, basis, basis_in) -> dict:
+        """Feature rows of the chain's activations: signals (channels x directions) and SH
+        (shells x channels x coefficients), input and output side."""
+        S, nd = basis.n_shells, basis.n_dirs
+        return dict(s_in=cfg.c_in * nd, c_in=S * cfg.c_in * basis_in.n_coef, c_out=S * cfg.c_out * basis.n_coef,
+                    s_out=cfg.c_out * nd)
 
     def set_inputs(self, s_in: torch.Tensor, ds_out: torch.Tensor, w: torch.Tensor, b: torch.Tensor):
         self.s_in.copy_(s_in)
