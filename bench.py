@@ -195,6 +195,18 @@ def chain_inputs(cfg, dirs, bvals, dtype, rank=0):
     return s_in, ds_out, w, b
 
 
+def guarded(name, fn, *args, **kwargs):
+    """Runs one optional leg of the bench.  A failure is printed to stderr and reported as
+    {"unavailable": reason} in that leg's entry, so that the JSON line of the timed step is
+    still printed."""
+    try:
+        return fn(*args, **kwargs)
+    except Exception as e:  # noqa: BLE001 - any failure of an optional leg is reported, not raised
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"unavailable": f"{name}: {type(e).__name__}: {str(e)[:300]}"}
+
+
 def time_tables(cfg, dirs, bvals, repeats=3):
     """Host FP64 table build (Sec. 2.2, 2.3; built once per gradient table, outside every timed
     step): the per-shell basis and regularised pseudo-inverse, then the LSC geometry (kernel
@@ -489,28 +501,37 @@ def main():
 
     extras = {}
     if rank == 0 and not args.no_extras and args.precision == "bf16":
+        # every leg below is optional: a failure is reported in its own entry, not fatal
         # ---- accuracy on sampled voxels vs the FP64 oracle ----
         idx = synth.voxel_subset(V, 32, seed=cfg.seed + 99)
-        extras["err_vs_oracle_bf16"] = sampled_errors(ch, cfg, dirs, bvals, idx)
+        extras["err_vs_oracle_bf16"] = guarded("err_vs_oracle_bf16", sampled_errors, ch, cfg, dirs, bvals, idx)
         # ---- FP32 path: tensor cores through three-part BF16 splits (default), CUDA cores ----
-        extras["fp32"] = run_fp32_leg(ch, cfg, dirs, bvals, idx, max(3, args.fp32_steps), True)
-        extras["fp32_cuda_cores"] = run_fp32_leg(ch, cfg, dirs, bvals, idx, args.fp32_steps, False)
+        extras["fp32"] = guarded("fp32", run_fp32_leg, ch, cfg, dirs, bvals, idx, max(3, args.fp32_steps), True)
+        extras["fp32_cuda_cores"] = guarded("fp32_cuda_cores", run_fp32_leg, ch, cfg, dirs, bvals, idx,
+                                            args.fp32_steps, False)
         # ---- end to end through host buffers ----
-        extras["e2e"] = run_e2e(ch, args.e2e_steps)
+        extras["e2e"] = guarded("e2e", run_e2e, ch, args.e2e_steps)
         # ---- mixed SH orders (4 -> 8) with every input shell mixed into every output shell ----
         from dataclasses import replace
-        extras["mixed_orders_all_shells"] = run_chain_leg(replace(cfg, order_in=4, window="all"), dirs, bvals)
-        extras["resampling_free"] = run_chain_leg(replace(cfg, resample=False), dirs, bvals)
+        extras["mixed_orders_all_shells"] = guarded("mixed_orders_all_shells", run_chain_leg,
+                                                    replace(cfg, order_in=4, window="all"), dirs, bvals)
+        extras["resampling_free"] = guarded("resampling_free", run_chain_leg, replace(cfg, resample=False), dirs,
+                                            bvals)
         # ---- stand-alone transforms at 1,048,576 voxels (FP32 and BF16-in / FP32-out) ----
-        extras["transforms"] = run_transforms(cfg, dirs, bvals, args.transform_vox, hbm)
-        extras["transforms"]["cpu_baseline"] = time_oracle_transforms(cfg, dirs, bvals)
+        tr = guarded("transforms", run_transforms, cfg, dirs, bvals, args.transform_vox, hbm)
+        if "unavailable" not in tr:
+            tr["cpu_baseline"] = guarded("transforms cpu_baseline", time_oracle_transforms, cfg, dirs, bvals)
+        extras["transforms"] = tr
         # ---- FP64 table build on the host (once per gradient table) ----
-        extras["tables"] = time_tables(cfg, dirs, bvals)
+        extras["tables"] = guarded("tables", time_tables, cfg, dirs, bvals)
+
         # ---- oracle on the host cores ----
-        vps, nv, tw = time_oracle(cfg, dirs, bvals, args.cpu_seconds)
-        extras["cpu_baseline"] = {"value": vps, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                                  "sample": f"{nv} voxels of the same workload in 64-voxel chunks, "
-                                            f"{tw:.1f} s of FP64 numpy oracle work"}
+        def cpu_leg():
+            vps, nv, tw = time_oracle(cfg, dirs, bvals, args.cpu_seconds)
+            return {"value": vps, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                    "sample": f"{nv} voxels of the same workload in 64-voxel chunks, "
+                              f"{tw:.1f} s of FP64 numpy oracle work"}
+        extras["cpu_baseline"] = guarded("cpu_baseline", cpu_leg)
         extras["cpu_baseline_single_thread"] = time_oracle_single_thread()
 
     if rank == 0:

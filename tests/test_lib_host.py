@@ -318,3 +318,10 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     if not torch.cuda.is_available():
         with pytest.raises(Exception):
             layers.transform("signal2sh", basis, torch.zeros((30, 64)), 1)
+
+
+def test_bench_optional_legs_report_failures_instead_of_raising():
+    import bench
+    assert bench.guarded("leg", lambda a, b=0: a + b, 1, b=2) == 3
+    rec = bench.guarded("leg", lambda: 1 / 0)
+    assert rec == {"unavailable": "leg: ZeroDivisionError: division by zero"}
