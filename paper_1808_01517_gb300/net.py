@@ -256,8 +256,8 @@ def main():
                 checkpoint_every=args.checkpoint_every, resume=args.resume)
     res = evaluate(net, fb, te)
     res.update({"steps": args.steps, "batch": args.batch, "train_seconds": log.seconds,
-                "train_voxels_per_s": log.steps * args.batch / log.seconds, "loss_first_last": [log.losses[0],
-                                                                                             log.losses[-1]]})
+                "train_voxels_per_s": log.steps * args.batch / max(log.seconds, 1e-9),
+                "loss_first_last": [log.losses[0], log.losses[-1]] if log.losses else []})
     if args.save:
         torch.save({"state": net.state_dict(), "cfg": cfg.__dict__, "result": res}, args.save)
     print(json.dumps(res))
