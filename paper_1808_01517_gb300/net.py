@@ -80,13 +80,11 @@ class SphericalNet(torch.nn.Module):
                 g = torch.Generator().manual_seed(cfg.seed + 17 * i)
                 lsc.weight.copy_(torch.randn(lsc.weight.shape, generator=g) * (gain / math.sqrt(fan)))
                 # weights outside the shell window are unused: keep them zero
-                win = torch.from_numpy(np.array(lsc.geom.tables(0)["window"])).bool()
                 if not first:
                     m = torch.zeros(S, S, dtype=torch.bool)
                     for s in range(S):
                         m[s] = torch.from_numpy(lsc.geom.tables(s)["window"]).bool()
                     lsc.weight.mul_(m[None, :, None, :, None].float())
-                del win
             self.lscs.append(lsc)
         self.act = layers.LeakyReLU(cfg.slope)
         self.sh2s = layers.SH2Signal(cfg.order, target_dirs, bvals=target_bvals)
