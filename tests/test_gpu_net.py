@@ -11,7 +11,7 @@ from oracle import lsc as olsc  # noqa: E402
 from oracle import sh as osh  # noqa: E402
 from paper_1808_01517_gb300 import net as N  # noqa: E402
 from paper_1808_01517_gb300 import synth  # noqa: E402
-from tests._layout import rel_l2, rows_to_sh, sh_to_rows  # noqa: E402
+from tests._layout import rel_l2  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
