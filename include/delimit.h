@@ -116,13 +116,17 @@ delimit_status delimit_sh_basis_tables(const delimit_sh_basis* basis, int shell,
 
 /* Signal2SH (Sec. 2.2): sh[(s,c,:), v] = P_s sig[(s,c,:), v] for every shell s,
  * channel c < channels and voxel v < n_vox.  in_t/out_t: F32 or BF16 each.
- * sig: signal rows, sh: SH rows (layout above). */
+ * sig: signal rows, sh: SH rows (layout above).  n_vox = 0 does nothing.
+ * Errors: INVALID_ARG (NULL basis or pointer, n_vox < 0, channels outside
+ * 1..65535, ld < n_vox, a host-only or evaluation-only basis, a basis made on
+ * another device), ALIGNMENT (16-byte rule), CUDA (launch failure). */
 delimit_status delimit_signal2sh(const delimit_sh_basis* basis, const void* sig, void* sh, int64_t n_vox,
                                  int channels, int64_t ld_sig, int64_t ld_sh, delimit_dtype in_t,
                                  delimit_dtype out_t, void* stream);
 
 /* SH2Signal (Sec. 2.2): sig[(s,c,:), v] = B_s sh[(s,c,:), v] on the basis' own
- * directions (create a basis on the "resampled" directions to evaluate there). */
+ * directions (create a basis on the "resampled" directions to evaluate there).
+ * Errors as delimit_signal2sh, an evaluation-only basis being allowed here. */
 delimit_status delimit_sh2signal(const delimit_sh_basis* basis, const void* sh, void* sig, int64_t n_vox,
                                  int channels, int64_t ld_sh, int64_t ld_sig, delimit_dtype in_t,
                                  delimit_dtype out_t, void* stream);
@@ -145,7 +149,9 @@ delimit_status delimit_signal2sh_gather(const delimit_sh_basis* basis, const voi
                                         void* sh, int64_t ld_sh, int channels, delimit_dtype in_t,
                                         delimit_dtype out_t, void* stream);
 
-/* Adjoints used by back-propagation: d_sig = P_s^T d_sh and d_sh = B_s^T d_sig. */
+/* Adjoints used by back-propagation: d_sig = P_s^T d_sh and d_sh = B_s^T d_sig, same
+ * layouts, dtypes and errors as the forward calls (the Signal2SH adjoint needs the
+ * pseudo-inverse, so it refuses an evaluation-only basis). */
 delimit_status delimit_signal2sh_backward(const delimit_sh_basis* basis, const void* d_sh, void* d_sig,
                                           int64_t n_vox, int channels, int64_t ld_sh, int64_t ld_sig,
                                           delimit_dtype in_t, delimit_dtype out_t, void* stream);
