@@ -275,7 +275,12 @@ size_t delimit_lsc_workspace_size(const delimit_lsc_geometry* geom, int64_t n_vo
  * FP64 about 1e-6 at 65,536 voxels, 16 -> 64 channels); with
  * delimit_set_tensor_cores(0) F32 runs as FP32 FMA on CUDA cores.  The F32
  * workspace includes the split copies (3 x 2 bytes per element of sh_in, the
- * operator and, backward, d_out). */
+ * operator and, backward, d_out).
+ * Errors: INVALID_ARG (NULL geometry or w, a host-only geometry or one made on
+ * another device, n_vox < 0, c_in or c_out outside 1..4096, ld < n_vox),
+ * WORKSPACE (ws_bytes below the size above; checked before anything else runs,
+ * also for n_vox = 0, which then does nothing), ALIGNMENT (workspace not 256-byte
+ * aligned, or an activation breaking the 16-byte rule), CUDA (launch failure). */
 delimit_status delimit_lsc_forward(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
                                    const float* b, void* sh_out, int64_t n_vox, int c_in, int c_out,
                                    int64_t ld_in, int64_t ld_out, delimit_dtype act_t, unsigned flags,
@@ -289,7 +294,10 @@ delimit_status delimit_lsc_forward(const delimit_lsc_geometry* geom, const void*
  *   geometry, sizes, dtype and w built in this workspace (b is not needed here).
  * All outputs are overwritten (not accumulated).  Reductions over voxels are
  * deterministic (fixed split and order).
- *   workspace >= delimit_lsc_workspace_size(..., 1) bytes, 256-byte aligned. */
+ *   workspace >= delimit_lsc_workspace_size(..., 1) bytes, 256-byte aligned.
+ * n_vox = 0 writes zeros to dw and db.  w is needed only for d_in, sh_in only for
+ * dw or db.  Errors as delimit_lsc_forward, with d_out, sh_in and d_in checked
+ * like its activations. */
 delimit_status delimit_lsc_backward(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
                                     const void* d_out, void* d_in, float* dw, float* db, int64_t n_vox,
                                     int c_in, int c_out, int64_t ld_in, int64_t ld_out, delimit_dtype act_t,
