@@ -95,3 +95,48 @@ def test_bf16_storage_model_of_the_benchmark_chain():
     e_s, e_d = _rel(got_s, ref_s), _rel(got_d, ref_d)
     # a handful of BF16 roundings (unit roundoff 2^-8) in series: a few 1e-3, well below 1e-2
     assert 2e-3 < e_s < 7e-3 and 2e-3 < e_d < 7e-3, (e_s, e_d)
+
+
+def chain_fp32_forward(ob, og, sig, w, b):
+    """The forward chain with every operand and every operation in float32 (numpy's float32
+    BLAS accumulates in float32): the error level of FP32 arithmetic itself."""
+    f = np.float32
+    S = ob.n_shells
+    M, q = og.collapse_mats()
+    P, B = [p.astype(f) for p in ob.P], [x.astype(f) for x in ob.B]
+    M, q = [m.astype(f) for m in M], [x.astype(f) for x in q]
+    sig, w, b = sig.astype(f), w.astype(f), b.astype(f)
+    V, Co = sig.shape[0], w.shape[0]
+    c_in = np.stack([sig[:, :, rows] @ P[s].T for s, rows in enumerate(ob.rows)], axis=2)
+    c_out = np.zeros((V, Co, S, ob.n_coef), f)
+    for s in range(S):
+        acc = np.zeros((V, Co * ob.n_coef), f)
+        for p in range(S):
+            if og.win[s, p]:
+                W = np.einsum("ack,kxy->axcy", w[:, s, :, p, :], M[s]).astype(f)
+                acc += c_in[:, :, p, :].reshape(V, -1) @ W.reshape(Co * ob.n_coef, -1).T
+        c_out[:, :, s, :] = acc.reshape(V, Co, -1) + b[None, :, s, None] * q[s][None, None, :]
+    s_out = np.empty((V, Co, sig.shape[2]), f)
+    for s, rows in enumerate(ob.rows):
+        s_out[:, :, rows] = c_out[:, :, s, :] @ B[s].T
+    return s_out.astype(np.float64)
+
+
+def test_fp32_arithmetic_error_level():
+    """FP32 storage alone costs ~1e-7 here; FP32 accumulation of the long sums (K up to
+    2,160 per LSC output) brings FP32 arithmetic to a few 1e-7, the level of the
+    library's FP32 paths (about 1e-6), an order of magnitude below the 1e-5 tolerance."""
+    dirs, bvals = synth.multishell_table([90, 90, 90], [1000, 2000, 3000], seed=1808)
+    ob = osh.SHBasisOracle(dirs, bvals, 8, 0.006)
+    og = olsc.LSCOracle(ob, 8, 3, np.deg2rad(25), 4, 12, "adjacent")
+    V, Ci, Co = 64, 16, 64
+    f32 = lambda x: np.asarray(x, np.float32).astype(np.float64)  # noqa: E731
+    sig = f32(synth.fibre_signal(dirs, bvals, V * Ci, seed=1808).reshape(Ci, V, -1).transpose(1, 0, 2))
+    w = f32(synth.gaussian((Co, 3, Ci, 3, og.K), 0.1, seed=1808))
+    b = f32(synth.gaussian((Co, 3), 0.1, seed=1809))
+    ds = f32(synth.gaussian((V, Co, 270), 0.1, seed=1808, tag="grads"))
+    ref_s, _ = chain(ob, og, sig, w, b, ds, exact)
+    st_s, _ = chain(ob, og, sig, w, b, ds, f32)
+    assert _rel(st_s, ref_s) < 3e-7
+    e = _rel(chain_fp32_forward(ob, og, sig, w, b), ref_s)
+    assert 5e-8 < e < 3e-6, e
