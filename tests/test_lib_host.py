@@ -236,26 +236,6 @@ def test_binding_constants_match_header():
     assert vals["DELIMIT_LSC_OPERATOR_READY"] == L.OPERATOR_READY
 
 
-def test_bench_times_the_host_table_build():
-    """The bench's `tables` entry: the FP64 host build of the basis and the LSC geometry on
-    host-only handles (no device needed), once per gradient table."""
-    import bench
-    from dataclasses import replace
-    cfg = replace(bench.workload_config(256), dirs_per_shell=(30, 30), bvals=(1000.0, 2000.0), rings=2, sectors=6)
-    dirs, bvals = bench.table(cfg)
-    rec = bench.time_tables(cfg, dirs, bvals, repeats=1)
-    assert rec["sh_basis_ms"] > 0 and rec["lsc_geometry_ms"] > 0 and rec["precision"] == "f64"
-
-
-def test_bench_times_the_oracle_on_one_thread():
-    """The bench's single-thread oracle leg: a child interpreter with the BLAS pools held to
-    one thread runs the reference arm and its rate is reported."""
-    import bench
-    rec = bench.time_oracle_single_thread(steps=1, warm=0, timeout_s=120)
-    assert "unavailable" not in rec, rec
-    assert rec["value"] > 0 and rec["cores"] == 1
-
-
 def test_every_entry_point_refuses_null_pointers_with_a_reason():
     """Each compute or table entry point, given NULL pointers (and non-zero sizes), returns
     INVALID_ARG and leaves a message in delimit_last_error, without touching a device."""
@@ -288,15 +268,6 @@ def test_every_entry_point_refuses_null_pointers_with_a_reason():
     assert lib.delimit_lsc_workspace_size(None, 64, 1, 1, L.BF16, 0) == 0
 
 
-def test_bench_times_the_oracle_transforms():
-    import bench
-    from dataclasses import replace
-    cfg = replace(bench.workload_config(256), dirs_per_shell=(30, 30), bvals=(1000.0, 2000.0))
-    dirs, bvals = bench.table(cfg)
-    rec = bench.time_oracle_transforms(cfg, dirs, bvals, n_vox=512, reps=1)
-    assert rec["signal2sh_voxels_per_s"] > 0 and rec["sh2signal_voxels_per_s"] > 0 and rec["kind"] == "oracle"
-
-
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     """No fallback: with the shared library absent and its build failing, loading raises,
     and a layer call on host tensors raises instead of computing anything on the CPU."""
@@ -318,10 +289,3 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     if not torch.cuda.is_available():
         with pytest.raises(Exception):
             layers.transform("signal2sh", basis, torch.zeros((30, 64)), 1)
-
-
-def test_bench_optional_legs_report_failures_instead_of_raising():
-    import bench
-    assert bench.guarded("leg", lambda a, b=0: a + b, 1, b=2) == 3
-    rec = bench.guarded("leg", lambda: 1 / 0)
-    assert rec == {"unavailable": "leg: ZeroDivisionError: division by zero"}
