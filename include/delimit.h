@@ -29,6 +29,11 @@
  * running kernel (a bounded device-side wait that ran out) are reported by
  * delimit_device_error().  All entry points are thread-safe for distinct
  * handles; delimit_last_error() is per thread.
+ * Per-device state: the library resolves some device addresses once per device
+ * and keeps them for the life of the process (the device error word, and the
+ * scratch array of delimit_lsc_forward_noalloc).  Neither they nor any handle
+ * survive cudaDeviceReset() or the destruction of the device's primary context:
+ * do not use the library on a device after resetting it.
  *
  * Shells: rows of a gradient table are grouped by b-value rounded to an
  * integer, shells in ascending b, rows of a shell in input order

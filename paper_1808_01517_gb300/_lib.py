@@ -246,6 +246,18 @@ def device_error(stream_ptr: int = 0):
     return st, code.value
 
 
+def check_device_error(where: str, stream_ptr: int | None = None):
+    """Synchronises the stream and raises DelimitError if a kernel recorded an error in the
+    device error word (a bounded wait that ran out, a gather index out of range): such a
+    kernel returns with its output partly written, so results computed after it are not
+    trusted.  Default stream: torch's current one."""
+    if stream_ptr is None:
+        import torch
+        stream_ptr = torch.cuda.current_stream().cuda_stream
+    st, _ = device_error(stream_ptr)
+    check(st, where)
+
+
 def trace_enable(on: bool):
     check(get().delimit_trace_enable(1 if on else 0), "delimit_trace_enable")
 

@@ -1128,7 +1128,9 @@ int env_int(const char* name, int dflt) {
 }
 
 // CTAs per cluster of one GEMM: DELIMIT_GEMM_CLUSTER (1 or 2) overrides the
-// per-GEMM default (2 = operator tile multicast).
+// per-GEMM default.  2 = a CTA pair issuing 2-SM tcgen05 MMAs (cta_group::2): each
+// CTA loads its own half of the operands by TMA (no TMA multicast anywhere), one
+// thread of the even CTA issues the MMAs for both; 1 = single-CTA MMAs.
 int gemm_cluster(int dflt) {
   const int v = env_int("DELIMIT_GEMM_CLUSTER", dflt);
   return v == 1 ? 1 : 2;

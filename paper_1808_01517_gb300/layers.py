@@ -120,7 +120,8 @@ def lsc_forward(geom: L.LSCGeometry, x: torch.Tensor, w: torch.Tensor, b: torch.
     _, wsp, ws_n = workspace if workspace is not None else lsc_workspace(geom, n_vox, c_in, c_out, x.dtype, False,
                                                                          x.device)
     w = w.detach().contiguous().float()
-    bp = b.detach().contiguous().float().data_ptr() if b is not None else None
+    bf = b.detach().contiguous().float() if b is not None else None  # lives until after the launch
+    bp = bf.data_ptr() if bf is not None else None
     L.check(L.get().delimit_lsc_forward(geom.handle, x.data_ptr(), w.data_ptr(), bp, out.data_ptr(), n_vox, c_in,
                                         c_out, x.stride(0), out.stride(0), _code(x), 0, wsp, ws_n, _stream()),
             "delimit_lsc_forward")

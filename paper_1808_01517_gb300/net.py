@@ -27,6 +27,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
+from . import _lib as L
 from . import layers, synth
 
 
@@ -152,6 +153,7 @@ class TrainLog:
     seconds: float = 0.0
     steps: int = 0
     batch: int = 0
+    device_error_checks: int = 0  # clean reads of the device error word during the run
 
 
 def save_checkpoint(path: str, net: torch.nn.Module, opt, sched, gen: torch.Generator, next_step: int):
@@ -199,11 +201,17 @@ def train(net: SphericalNet, data: Data, steps: int, batch: int, lr: float = 2e-
         opt.step()
         sched.step()
         if step % log_every == 0 or step == steps - 1:
-            log.losses.append((step, float(loss)))
+            log.losses.append((step, float(loss.detach())))
+            # the loss read has synchronised already; a kernel that gave up leaves partial
+            # outputs, so training stops here instead of going on with them
+            L.check_device_error(f"training step {step}")
+            log.device_error_checks += 1
         if checkpoint and checkpoint_every > 0 and (step + 1) % checkpoint_every == 0:
             save_checkpoint(checkpoint, net, opt, sched, gen, step + 1)
     torch.cuda.synchronize()
     log.seconds = time.perf_counter() - t0
+    L.check_device_error("end of training")
+    log.device_error_checks += 1
     return log
 
 
@@ -220,6 +228,7 @@ def evaluate(net: SphericalNet, fb: Fallback, data: Data) -> dict:
     torch.cuda.synchronize()
     t_net = time.perf_counter() - t0
     p_fb = predict(fb, data.x)
+    L.check_device_error("evaluation")
     m = net.cfg.dirs_per_shell[0]
     out = {"rel_l2_net": rel_l2(p_net, data.clean), "rel_l2_fallback": rel_l2(p_fb, data.clean),
            "voxels": int(data.x.shape[1]), "net_inference_voxels_per_s": data.x.shape[1] / t_net}
@@ -255,7 +264,8 @@ def main():
     res = evaluate(net, fb, te)
     res.update({"steps": args.steps, "batch": args.batch, "train_seconds": log.seconds,
                 "train_voxels_per_s": log.steps * args.batch / max(log.seconds, 1e-9),
-                "loss_first_last": [log.losses[0], log.losses[-1]] if log.losses else []})
+                "loss_first_last": [log.losses[0], log.losses[-1]] if log.losses else [],
+                "device_error_word": f"clean at {log.device_error_checks} checks and after evaluation"})
     if args.save:
         torch.save({"state": net.state_dict(), "cfg": cfg.__dict__, "result": res}, args.save)
     print(json.dumps(res))

@@ -103,6 +103,9 @@ def run(subjects, chunk: int = 1 << 18):
                         "delimit_scatter_voxels")
     e1.record()
     torch.cuda.synchronize()
+    # outside the timed region: a kernel that gave up (or a gather index out of range)
+    # leaves partial outputs, so the run fails here instead of returning them
+    L.check_device_error("volume inference")
     return outs, e0.elapsed_time(e1) * 1e-3, total
 
 
@@ -137,7 +140,7 @@ def main():
            "weights": "random-init" if args.random_init else args.model,
            "table_seconds_total": sum(s.table_seconds for s in subs), "setup_seconds": setup,
            "finite": bool(torch.isfinite(o[:, m]).all()), "outside_zero": bool((o[:, ~m] == 0).all()),
-           "mean_b1000_inside": float(o[:90, m].mean())}
+           "mean_b1000_inside": float(o[:90, m].mean()), "device_error_word": "clean after the run"}
     print(json.dumps(res))
 
 
