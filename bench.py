@@ -424,6 +424,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # the timed chain must run on the tensor cores: under TC_REQUIRE a call that has no
+    # tensor-core kernel for its shape is refused instead of running on the CUDA cores
+    L.set_tensor_cores(L.TC_REQUIRE)
+    fallbacks0 = L.cuda_core_fallbacks()
     for _ in range(max(3, args.warmup)):
         ch.step()
     barrier()
@@ -447,7 +451,11 @@ def main():
     launches = L.get().delimit_kernel_launches() - launches0
     trace = L.trace_summary()
     L.trace_enable(False)
+    L.set_tensor_cores(L.TC_PREFER)
     clk = clocks.stop()
+    cuda_core_kernels = sorted(n for n in trace if "simt" in n)
+    if cuda_core_kernels or L.cuda_core_fallbacks() != fallbacks0:
+        raise RuntimeError(f"timed chain ran CUDA-core GEMM kernels: {cuda_core_kernels}")
     ms = reduce_max_ms(t_start.elapsed_time(t_stop) / K, dist, "cuda")
     value = job_throughput(V, world, ms)
     per_call = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]))
@@ -466,8 +474,15 @@ def main():
         peak_src = "measured"
     except Exception:
         peak_src = "fallback"
+    tf_burst = float(peaks.get("bf16_tflops", 1900.0))
     tf_sust = float(peaks.get("bf16_tflops_sustained", 1700.0))
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # the peak for the clock the step ran at: the burst figure (a GEMM timed alone at the
+    # maximum clock) when the SM clock sampled during the timed region stayed at its
+    # maximum, else the sustained figure (a GEMM loop held to the power cap)
+    at_max = bool(clk.get("sm_mhz") and clk.get("sm_max_mhz") and clk["sm_mhz"] >= 0.97 * clk["sm_max_mhz"])
+    tf_peak = tf_burst if at_max else tf_sust
+    tf_name = "bf16_tflops (burst: SM clock at its maximum)" if at_max else "bf16_tflops_sustained (SM clock below max)"
     fl, by = ch.flops(), ch.bytes()
     per_call_roof = {n: {"ms": per_call[n], "tflops": fl[n] / (per_call[n] * 1e-3) / 1e12,
                          "gbs": by[n] / (per_call[n] * 1e-3) / 1e9} for n in per_call}
@@ -486,18 +501,20 @@ def main():
     tensor_bound = "_gemm" in dom
     if tensor_bound and dom.endswith("_f32"):
         # six BF16 part products per FP32 product: the split path's ceiling is a sixth of BF16's
-        roofline = {"bound": "tensor", "achieved": kernels[dom]["tflops"], "peak": tf_sust / 6, "unit": "TFLOP/s",
-                    "frac": kernels[dom]["tflops"] / (tf_sust / 6),
-                    "peak_source": f"{peak_src} bf16_tflops_sustained / 6 (six BF16 products per FP32 product)"}
+        roofline = {"bound": "tensor", "achieved": kernels[dom]["tflops"], "peak": tf_peak / 6, "unit": "TFLOP/s",
+                    "frac": kernels[dom]["tflops"] / (tf_peak / 6),
+                    "frac_of_sustained": kernels[dom]["tflops"] / (tf_sust / 6),
+                    "peak_source": f"{peak_src} {tf_name} / 6 (six BF16 products per FP32 product)"}
     elif tensor_bound:
-        roofline = {"bound": "tensor", "achieved": kernels[dom]["tflops"], "peak": tf_sust, "unit": "TFLOP/s",
-                    "frac": kernels[dom]["tflops"] / tf_sust, "peak_source": f"{peak_src} bf16_tflops_sustained"}
+        roofline = {"bound": "tensor", "achieved": kernels[dom]["tflops"], "peak": tf_peak, "unit": "TFLOP/s",
+                    "frac": kernels[dom]["tflops"] / tf_peak, "frac_of_sustained": kernels[dom]["tflops"] / tf_sust,
+                    "peak_source": f"{peak_src} {tf_name}"}
     else:
         roofline = {"bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": hbm, "unit": "GB/s",
                     "frac": kernels[dom]["gbs"] / hbm, "peak_source": f"{peak_src} hbm_gbs"}
     roofline.update({"traffic": ncu_traffic(dom, V), "kernel": dom, "kernel_avg_ms": kernels[dom]["avg_ms"],
                      "step_tflops": sum(fl.values()) / (ms * 1e-3) / 1e12})
-    roofline["step_frac_of_tensor_peak"] = roofline["step_tflops"] / tf_sust
+    roofline["step_frac_of_tensor_peak"] = roofline["step_tflops"] / tf_peak
 
     extras = {}
     if rank == 0 and not args.no_extras and args.precision == "bf16":
@@ -556,9 +573,32 @@ def main():
         line["resampling_free"] = extras.get("resampling_free")
         line["tables"] = extras.get("tables")
         line["cpu_baseline_single_thread"] = extras.get("cpu_baseline_single_thread")
+        line["path"] = {"tensor_cores": "required in the timed region", "cuda_core_kernels": cuda_core_kernels}
+        line["summary"] = tail_summary(line)  # last, so that a truncated tail of the line still shows it
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def tail_summary(line: dict) -> dict:
+    """The headline figures of every leg in a few hundred characters: BF16 and FP32 chain
+    voxels/s and errors, the roofline fractions, the stand-alone transforms' HBM fractions."""
+    def g(d, *keys):
+        for k in keys:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return float(f"{d:.4g}") if isinstance(d, float) else d
+    out = {"bf16_vps": g(line, "value"), "bf16_err": [g(line, "err_vs_oracle_bf16", "s_out"),
+                                                      g(line, "err_vs_oracle_bf16", "ds_in")],
+           "gemm_frac": g(line, "roofline", "frac"), "step_frac": g(line, "roofline", "step_frac_of_tensor_peak"),
+           "fp32_vps": g(line, "fp32", "value"), "fp32_err": [g(line, "fp32", "err_vs_oracle", "s_out"),
+                                                              g(line, "fp32", "err_vs_oracle", "ds_in")]}
+    tr = line.get("transforms") or {}
+    for k in ("signal2sh_f32", "sh2signal_f32", "signal2sh_bf16_in", "sh2signal_bf16_in"):
+        if isinstance(tr.get(k), dict):
+            out[k] = [g(tr, k, "frac_hbm"), g(tr, k, "err_vs_oracle")]
+    return out
 
 
 def sampled_errors(ch, cfg, dirs, bvals, idx):

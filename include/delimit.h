@@ -377,12 +377,25 @@ delimit_status delimit_device_error(void* stream, int* code);
  * CUDA if the launch fails. */
 delimit_status delimit_selftest_wait_timeout(void* stream);
 
-/* Process-wide switch, default 1: BF16 steps, and the LSC GEMMs of F32 calls
- * (as three-part BF16 splits), run on the tcgen05 tensor-core kernels where
- * their shape rules allow, else on the CUDA-core kernels.  0 forces the
- * CUDA-core kernels (same results within the dtype's rounding; used to
- * cross-check the two).  Has no counterpart in the paper. */
-delimit_status delimit_set_tensor_cores(int enable);
+/* Process-wide tensor-core policy for the activation GEMMs (the transforms and
+ * the three LSC GEMMs); no counterpart in the paper.
+ *   1 (default): each call runs on the tcgen05 tensor-core kernels when one
+ *     takes its shape and dtype (BF16 directly, F32 as BF16 part splits), else
+ *     on the CUDA-core kernels; every such call is counted by
+ *     delimit_cuda_core_fallbacks().
+ *   2: tensor cores required: a call that would run on the CUDA cores returns
+ *     DELIMIT_ERR_UNSUPPORTED (with the step named in delimit_last_error())
+ *     before launching anything.
+ *   0: every step on the CUDA-core kernels (same results within the dtype's
+ *     rounding; used to cross-check the two).
+ * Other values: INVALID_ARG.  The weight-side kernels (operator build, weight-
+ * gradient reduction) and the gathered Signal2SH have CUDA-core kernels only
+ * and are not affected. */
+delimit_status delimit_set_tensor_cores(int mode);
+
+/* Number of activation-GEMM calls that ran on the CUDA cores under policy 1
+ * since the process started (host-side count).  No counterpart in the paper. */
+uint64_t delimit_cuda_core_fallbacks(void);
 
 /* Tracing: while enabled, every group of kernel launches made by a call is
  * bracketed by CUDA events recorded on the call's stream.  Enabling (or

@@ -82,6 +82,7 @@ SIGNATURES = {
     "delimit_device_error": (C.c_int, [_vp, _ip]),
     "delimit_set_tensor_cores": (C.c_int, [C.c_int]),
     "delimit_kernel_launches": (C.c_uint64, []),
+    "delimit_cuda_core_fallbacks": (C.c_uint64, []),
     "delimit_trace_enable": (C.c_int, [C.c_int]),
     "delimit_trace_summary": (C.c_int64, [C.c_char_p, C.c_size_t]),
     "delimit_status_string": (C.c_char_p, [C.c_int]),
@@ -236,8 +237,19 @@ class LSCGeometry:
             self.handle = None
 
 
-def set_tensor_cores(enable: bool):
-    check(get().delimit_set_tensor_cores(1 if enable else 0), "delimit_set_tensor_cores")
+TC_OFF, TC_PREFER, TC_REQUIRE = 0, 1, 2
+
+
+def set_tensor_cores(mode):
+    """False / TC_OFF: CUDA cores only; True / TC_PREFER: tensor cores where a kernel takes
+    the call (else CUDA cores, counted); TC_REQUIRE: a call without a tensor-core kernel
+    is refused with ERR_UNSUPPORTED."""
+    m = int(mode) if not isinstance(mode, bool) else (TC_PREFER if mode else TC_OFF)
+    check(get().delimit_set_tensor_cores(m), "delimit_set_tensor_cores")
+
+
+def cuda_core_fallbacks() -> int:
+    return int(get().delimit_cuda_core_fallbacks())
 
 
 def device_error(stream_ptr: int = 0):

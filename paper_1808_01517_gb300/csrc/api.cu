@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -49,6 +50,23 @@ int* error_word_for_current_device() {
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Tensor-core policy (delimit_set_tensor_cores): 0 CUDA cores only, 1 tensor cores where a
+// kernel exists for the call's shape and dtype (else CUDA cores, counted), 2 tensor cores
+// required (a call without a tensor-core kernel is refused).
+std::atomic<int> g_tc_mode{1};
+std::atomic<uint64_t> g_cuda_core_fallbacks{0};
+
+// Called where an activation GEMM is about to run on the CUDA-core kernels.
+delimit_status cuda_core_path(const char* what) {
+  const int mode = g_tc_mode.load();
+  if (mode == 2)
+    return fail(DELIMIT_ERR_UNSUPPORTED, std::string(what) +
+                                             ": tensor cores are required (delimit_set_tensor_cores(2)) and no "
+                                             "tensor-core kernel takes this shape and dtype");
+  if (mode == 1) g_cuda_core_fallbacks.fetch_add(1);
+  return DELIMIT_OK;
+}
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -112,10 +130,14 @@ int delimit_version(void) { return 100; }
 
 uint64_t delimit_kernel_launches(void) { return launch_count(); }
 
-delimit_status delimit_set_tensor_cores(int enable) {
-  tc_set_enabled(enable != 0);
+delimit_status delimit_set_tensor_cores(int mode) {
+  if (mode < 0 || mode > 2) return fail(DELIMIT_ERR_INVALID_ARG, "tensor-core mode must be 0, 1 or 2");
+  g_tc_mode.store(mode);
+  tc_set_enabled(mode != 0);
   return DELIMIT_OK;
 }
+
+uint64_t delimit_cuda_core_fallbacks(void) { return g_cuda_core_fallbacks.load(); }
 
 const char* delimit_last_error(void) { return g_last_error.c_str(); }
 
@@ -277,6 +299,7 @@ static delimit_status run_transform(const delimit_sh_basis* b, const void* X, vo
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core transform launch");
     return DELIMIT_OK;
   }
+  if ((st = cuda_core_path("transform")) != DELIMIT_OK) return st;
   TransformArgs a{};  // every member zero (or its default)
   int max_out = 0;
   for (int s = 0; s < S; ++s) {
@@ -750,6 +773,7 @@ delimit_status delimit_lsc_forward(const delimit_lsc_geometry* g, const void* sh
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core LSC forward launch");
     return DELIMIT_OK;
   }
+  if ((st = cuda_core_path("LSC forward")) != DELIMIT_OK) return st;
   RowGemmArgs a;
   std::memset(&a, 0, sizeof a);
   const int per_in = d.c_in * d.n_in, per_out = d.c_out * d.n_out;
@@ -838,6 +862,7 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
       e = tc_lsc_dgrad(d, d_out, W, wt_k ? Wt : nullptr, d_in, n_vox, ld_out, ld_in, g->err_word, cs);
       if (e != cudaSuccess) return cuda_fail(e, "tensor-core LSC input-gradient launch");
     } else {
+      if ((st = cuda_core_path("LSC input gradient")) != DELIMIT_OK) return st;
       RowGemmArgs a;
       std::memset(&a, 0, sizeof a);
       for (int sp = 0; sp < d.s_in; ++sp) {
@@ -889,6 +914,7 @@ delimit_status delimit_lsc_backward(const delimit_lsc_geometry* g, const void* s
       p_cs = p.ldpt;
       split_stride = ss_t;
     } else {
+      if ((st = cuda_core_path("LSC weight gradient")) != DELIMIT_OK) return st;
       WgradArgs a;
       std::memset(&a, 0, sizeof a);
       int maxN = 0;

@@ -34,3 +34,20 @@ def test_bench_optional_legs_report_failures_instead_of_raising():
     assert bench.guarded("leg", lambda a, b=0: a + b, 1, b=2) == 3
     rec = bench.guarded("leg", lambda: 1 / 0)
     assert rec == {"unavailable": "leg: ZeroDivisionError: division by zero"}
+
+
+def test_bench_tail_summary_is_short_and_complete():
+    """The summary closing the JSON line carries the headline of every leg and stays short
+    enough to survive a truncated tail of the line."""
+    import json
+    leg = {"ms": 0.3, "frac_hbm": 0.612345678, "err_vs_oracle": 1.23456e-7}
+    line = {"value": 13003702.74, "err_vs_oracle_bf16": {"s_out": 4.4e-3, "ds_in": 4.2e-3},
+            "roofline": {"frac": 0.8312345, "step_frac_of_tensor_peak": 0.61},
+            "fp32": {"value": 2.1e6, "err_vs_oracle": {"s_out": 1.3e-6, "ds_in": 1.1e-6}},
+            "transforms": {k: dict(leg) for k in ("signal2sh_f32", "sh2signal_f32", "signal2sh_bf16_in",
+                                                   "sh2signal_bf16_in")}}
+    s = bench.tail_summary(line)
+    assert s["bf16_vps"] == 13000000.0 and s["gemm_frac"] == 0.8312 and s["fp32_err"] == [1.3e-6, 1.1e-6]
+    assert s["signal2sh_f32"] == [0.6123, 1.235e-7]
+    assert len(json.dumps(s)) < 600
+    assert bench.tail_summary({"value": 1.0})["fp32_vps"] is None  # a missing leg reads as null

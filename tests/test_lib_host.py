@@ -241,7 +241,8 @@ def test_every_entry_point_refuses_null_pointers_with_a_reason():
     INVALID_ARG and leaves a message in delimit_last_error, without touching a device."""
     lib = L.get()
     device_calls = {"delimit_device_error", "delimit_selftest_wait_timeout"}
-    no_status = {"delimit_version", "delimit_kernel_launches", "delimit_status_string", "delimit_last_error",
+    no_status = {"delimit_version", "delimit_kernel_launches", "delimit_cuda_core_fallbacks",
+                 "delimit_status_string", "delimit_last_error",
                  "delimit_trace_enable", "delimit_trace_summary", "delimit_set_tensor_cores",
                  "delimit_lsc_workspace_size", "delimit_mask_compact_workspace_size",
                  "delimit_sh_basis_destroy", "delimit_lsc_geometry_destroy"}
@@ -289,3 +290,17 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     if not torch.cuda.is_available():
         with pytest.raises(Exception):
             layers.transform("signal2sh", basis, torch.zeros((30, 64)), 1)
+
+
+def test_tensor_core_policy_modes():
+    """delimit_set_tensor_cores takes 0 (CUDA cores), 1 (tensor cores where a kernel takes
+    the call) and 2 (tensor cores required) and refuses anything else."""
+    lib = L.get()
+    try:
+        for m in (0, 1, 2):
+            assert lib.delimit_set_tensor_cores(m) == L.OK
+        for m in (-1, 3):
+            assert lib.delimit_set_tensor_cores(m) == L.ERR_INVALID_ARG
+        assert isinstance(L.cuda_core_fallbacks(), int)
+    finally:
+        L.set_tensor_cores(True)
