@@ -234,7 +234,7 @@ def run_fp32_leg(ch, cfg, dirs, bvals, idx, steps, tensor_cores):
     import torch
     from paper_1808_01517_gb300 import _lib as L
     from paper_1808_01517_gb300.chain import Chain
-    L.set_tensor_cores(tensor_cores)
+    L.set_tensor_cores(L.TC_REQUIRE if tensor_cores else L.TC_OFF)
     try:
         ch32 = Chain(cfg, dirs, bvals, torch.float32)
         ch32.s_in.copy_(ch.s_in.float())
@@ -254,8 +254,8 @@ def run_fp32_leg(ch, cfg, dirs, bvals, idx, steps, tensor_cores):
         per_call = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(steps)]))
                     for i, name in enumerate(Chain.CALLS)}
         out = {"value": cfg.n_vox / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
-               "gemms": "tensor cores, three-part BF16 splits, six part products, FP32 accumulation" if tensor_cores
-               else "CUDA cores, FP32 FMA", "per_call_ms": per_call,
+               "gemms": "tensor cores (required), three-part BF16 splits, six part products, FP32 accumulation"
+               if tensor_cores else "CUDA cores, FP32 FMA", "per_call_ms": per_call,
                "err_vs_oracle": sampled_errors(ch32, cfg, dirs, bvals, idx)}
         del ch32
     finally:

@@ -122,6 +122,13 @@ delimit_status delimit_sh_basis_tables(const delimit_sh_basis* basis, int shell,
 /* Signal2SH (Sec. 2.2): sh[(s,c,:), v] = P_s sig[(s,c,:), v] for every shell s,
  * channel c < channels and voxel v < n_vox.  in_t/out_t: F32 or BF16 each.
  * sig: signal rows, sh: SH rows (layout above).  n_vox = 0 does nothing.
+ * Arithmetic (all four transforms): tcgen05 tensor cores with FP32 accumulation.
+ * BF16 input is multiplied as stored by the BF16 operator; F32 input is split in
+ * shared memory into three BF16 parts (x = x0 + x1 + x2 to 2^-27 |x|), the
+ * operator likewise on the host, and the six part products down to 2^-18 of the
+ * leading one are accumulated (FP32-level error).  Shapes beyond the tensor-core
+ * kernels (more than 256 directions or coefficients in a shell, more than 8
+ * shells) run on CUDA cores under the policy of delimit_set_tensor_cores.
  * Errors: INVALID_ARG (NULL basis or pointer, n_vox < 0, channels outside
  * 1..65535, ld < n_vox, a host-only or evaluation-only basis, a basis made on
  * another device), ALIGNMENT (16-byte rule), CUDA (launch failure). */
@@ -403,7 +410,7 @@ uint64_t delimit_cuda_core_fallbacks(void);
  * recorded events and writes JSON {"name": {"n": launches, "ms": total device
  * time}, ...} into buf (truncated to cap - 1 characters); it returns the full
  * length.  Names: signal2sh_tc, sh2signal_tc, signal2sh_bwd_tc,
- * sh2signal_bwd_tc, transform_simt, lsc_build_w, lsc_fwd_gemm, lsc_dgrad_gemm,
+ * sh2signal_bwd_tc (the _f32 suffix for FP32 input), transform_simt, lsc_build_w, lsc_fwd_gemm, lsc_dgrad_gemm,
  * lsc_wgrad_gemm (the _f32 suffix for split FP32 operands), lsc_rowsum (FP32 and
  * single-CTA paths), split_bf16x3, lsc_reduce_dw, lsc_gemm_simt, lsc_wgrad_simt.
  * No counterpart in the paper. */

@@ -167,8 +167,9 @@ class Chain:
             "signal2sh_bwd_tc": (fl["signal2sh_backward"], by["signal2sh_backward"]),
             "split_bf16x3": (0.0, 0.0),
         }
-        # FP32 activations: the same algorithmic work through the split-operand GEMMs
-        for k in ("lsc_fwd_gemm", "lsc_dgrad_gemm", "lsc_wgrad_gemm"):
+        # FP32 activations: the same algorithmic work through the split-operand kernels
+        for k in ("lsc_fwd_gemm", "lsc_dgrad_gemm", "lsc_wgrad_gemm", "signal2sh_tc", "sh2signal_tc",
+                  "sh2signal_bwd_tc", "signal2sh_bwd_tc"):
             out[k + "_f32"] = out[k]
         return out
 

@@ -207,6 +207,12 @@ delimit_status delimit_sh_basis_create(const double* dirs, const double* bvals, 
       delete b;
       return fail(DELIMIT_ERR_CUDA, "tensor-core tables: " + terr);
     }
+    if (tc_basis_tables_create_f32(b->h, b->tc, terr) != cudaSuccess) {
+      tc_basis_tables_destroy(b->tc);
+      cudaFree(b->d_mem);
+      delete b;
+      return fail(DELIMIT_ERR_CUDA, "tensor-core FP32 part tables: " + terr);
+    }
     b->on_device = true;
   }
   *out = b;
@@ -220,6 +226,7 @@ delimit_status delimit_sh_basis_destroy(delimit_sh_basis* b) {
     cudaGetDevice(&cur);
     if (cur != b->device) cudaSetDevice(b->device);
     cudaFree(b->d_mem);
+    tc_basis_tables_destroy_f32(b->tc);
     tc_basis_tables_destroy(b->tc);
     if (cur != b->device && cur >= 0) cudaSetDevice(cur);
   }
@@ -297,6 +304,13 @@ static delimit_status run_transform(const delimit_sh_basis* b, const void* X, vo
   if (in_t == DELIMIT_BF16 && tc_transform_supported(b->tc, kind, ldx, ldy, out_t)) {
     cudaError_t e = tc_transform_launch(b->tc, kind, X, Y, n_vox, C, ldx, ldy, out_t, b->err_word, cs);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core transform launch");
+    return DELIMIT_OK;
+  }
+  // FP32 input: three-part BF16 splits made in shared memory, six part products
+  if (in_t == DELIMIT_F32 && tc_transform_f32_supported(b->tc, kind)) {
+    cudaError_t e = tc_transform_f32_launch(b->tc, kind, static_cast<const float*>(X), Y, n_vox, C, ldx, ldy, out_t,
+                                            b->err_word, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core FP32 transform launch");
     return DELIMIT_OK;
   }
   if ((st = cuda_core_path("transform")) != DELIMIT_OK) return st;

@@ -18,15 +18,27 @@ struct TcBasisTables {
   int n_in[kMaxGroups][4] = {}, n_out[kMaxGroups][4] = {}, kpad[kMaxGroups][4] = {}, npad[kMaxGroups][4] = {};
   int m[kMaxGroups] = {}, dir_off[kMaxGroups] = {};
   bool ok = false;
+  // FP32 activations: three BF16 parts of every operator (T = T0 + T1 + T2), stacked as
+  // [3 x kpad][npad] per shell and kind at byte offset off3 in d_mem3
+  void* d_mem3 = nullptr;
+  size_t off3[kMaxGroups][4] = {};
+  bool ok3 = false;
 };
 
 cudaError_t tc_basis_tables_create(const BasisHost& h, TcBasisTables& t, std::string& err);
 void tc_basis_tables_destroy(TcBasisTables& t);
+cudaError_t tc_basis_tables_create_f32(const BasisHost& h, TcBasisTables& t, std::string& err);
+void tc_basis_tables_destroy_f32(TcBasisTables& t);
 
 // kind: 0 Signal2SH, 1 SH2Signal, 2 Signal2SH adjoint, 3 SH2Signal adjoint (BF16 input)
 bool tc_transform_supported(const TcBasisTables& t, int kind, int64_t ldx, int64_t ldy, int out_t);
 cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X, void* Y, int64_t n_vox, int C,
                                 int64_t ldx, int64_t ldy, int out_t, int* err_word, cudaStream_t st);
+// FP32 input (out_t: 0 = F32, 1 = BF16): each value split into three BF16 parts in shared
+// memory, six part products accumulated in FP32 on the tensor cores
+bool tc_transform_f32_supported(const TcBasisTables& t, int kind);
+cudaError_t tc_transform_f32_launch(const TcBasisTables& t, int kind, const float* X, void* Y, int64_t n_vox, int C,
+                                    int64_t ldx, int64_t ldy, int out_t, int* err_word, cudaStream_t st);
 
 // LSC GEMMs (BF16 activations, FP32 accumulation in TMEM).
 // FP32 activations: every operand is passed as three BF16 parts (split_bf16x3), part p

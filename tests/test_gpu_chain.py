@@ -104,7 +104,7 @@ def test_chain_full_size_sampled_vs_oracle(dtype, tol, n_vox):
     s_in = torch.rand((cfg.c_in * dirs.shape[0], cfg.n_vox), generator=g, device="cuda").to(dtype)
     ds_out = (0.1 * torch.randn((cfg.c_out * dirs.shape[0], cfg.n_vox), generator=g, device="cuda")).to(dtype)
     ch.set_inputs(s_in, ds_out, torch.from_numpy(w).float(), torch.from_numpy(b).float())
-    L.set_tensor_cores(L.TC_REQUIRE if dtype == torch.bfloat16 else L.TC_PREFER)
+    L.set_tensor_cores(L.TC_REQUIRE)  # no step of the chain may fall back to the CUDA cores
     try:
         ch.step()
         torch.cuda.synchronize()

@@ -3,8 +3,8 @@
 Order 0 (one coefficient per shell), order 2, an order-0 input beside an order-8
 output, a one-point ring (K = 2), the largest radius (pi/2: every direction a
 neighbour) and a shell of one direction.  The transforms (all four) and the LSC
-(forward, input, weight and bias gradients) run with tensor cores required for BF16
-and for the FP32 LSC GEMMs, so none of these shapes may fall back to the CUDA cores.
+(forward, input, weight and bias gradients) run with tensor cores required, in both
+precisions, so none of these shapes may fall back to the CUDA cores.
 """
 import numpy as np
 import pytest
@@ -63,7 +63,7 @@ def test_transforms_edge_cases(case, prec):
     dsig = synth.gaussian(sig.shape, 1.0, seed=5, tag="grads")
     S, N, m = ob.n_shells, ob.n_coef, ob.m
     out_dt = torch.float32
-    L.set_tensor_cores(L.TC_REQUIRE if prec == "bf16" else L.TC_PREFER)
+    L.set_tensor_cores(L.TC_REQUIRE)
     try:
         def run(kind, x_rows):
             y = layers.transform(kind, lb, _dev(x_rows, DT[prec]), C, out_dtype=out_dt)
