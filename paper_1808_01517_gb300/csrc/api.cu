@@ -307,7 +307,7 @@ static delimit_status run_transform(const delimit_sh_basis* b, const void* X, vo
     return DELIMIT_OK;
   }
   // FP32 input: three-part BF16 splits made in shared memory, six part products
-  if (in_t == DELIMIT_F32 && tc_transform_f32_supported(b->tc, kind)) {
+  if (in_t == DELIMIT_F32 && tc_transform_f32_supported(b->tc, kind, out_t)) {
     cudaError_t e = tc_transform_f32_launch(b->tc, kind, static_cast<const float*>(X), Y, n_vox, C, ldx, ldy, out_t,
                                             b->err_word, cs);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core FP32 transform launch");

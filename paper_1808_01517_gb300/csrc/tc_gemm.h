@@ -18,10 +18,12 @@ struct TcBasisTables {
   int n_in[kMaxGroups][4] = {}, n_out[kMaxGroups][4] = {}, kpad[kMaxGroups][4] = {}, npad[kMaxGroups][4] = {};
   int m[kMaxGroups] = {}, dir_off[kMaxGroups] = {};
   bool ok = false;
-  // FP32 activations: three BF16 parts of every operator (T = T0 + T1 + T2), stacked as
-  // [3 x kpad][npad] per shell and kind at byte offset off3 in d_mem3
+  // FP32 activations: three BF16 parts of every operator (T = T0 + T1 + T2) side by side
+  // along the output axis, [kpad][npad3] per shell and kind at byte offset off3 in d_mem3,
+  // part q from column q * npad3 / 3 (whole 64-column atoms)
   void* d_mem3 = nullptr;
   size_t off3[kMaxGroups][4] = {};
+  int npad3[kMaxGroups][4] = {};
   bool ok3 = false;
 };
 
@@ -36,7 +38,7 @@ cudaError_t tc_transform_launch(const TcBasisTables& t, int kind, const void* X,
                                 int64_t ldx, int64_t ldy, int out_t, int* err_word, cudaStream_t st);
 // FP32 input (out_t: 0 = F32, 1 = BF16): each value split into three BF16 parts in shared
 // memory, six part products accumulated in FP32 on the tensor cores
-bool tc_transform_f32_supported(const TcBasisTables& t, int kind);
+bool tc_transform_f32_supported(const TcBasisTables& t, int kind, int out_t);
 cudaError_t tc_transform_f32_launch(const TcBasisTables& t, int kind, const float* X, void* Y, int64_t n_vox, int C,
                                     int64_t ldx, int64_t ldy, int out_t, int* err_word, cudaStream_t st);
 

@@ -72,6 +72,36 @@ __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, vola
   }
 }
 
+// try_wait with a suspend-time hint: the thread sleeps until the phase completes or
+// about `hint_ns` pass, instead of returning at once (fewer issue slots while waiting).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+// wait_bounded for roles with many waiting threads: each try sleeps up to 20 us.
+__device__ __forceinline__ bool wait_bounded_sleep(uint32_t bar, uint32_t parity, volatile int* abort, int* err,
+                                                   int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait_hint(bar, parity, 20000u)) return true;
+    if (abort && *abort) return false;
+    if (global_ns() - t0 > kWaitLimitNs) {
+      if (err) atomicCAS(err, 0, code);
+      if (abort) *abort = 1;
+      return false;
+    }
+  }
+}
+
 // Waits ignoring the abort flag (used while draining in-flight work).
 __device__ __forceinline__ bool wait_drain(uint32_t bar, uint32_t parity, int* err, int code) {
   return wait_bounded(bar, parity, nullptr, err, code);

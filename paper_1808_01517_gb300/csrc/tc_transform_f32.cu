@@ -8,17 +8,19 @@
 // with i + j <= 2 (the three dropped ones are below 2^-26 of the leading one) are
 // accumulated in FP32 in TMEM, smallest first.
 //
-// Data path per 128-voxel tile: TMA copies FP32 input chunks of 32 rows x 128
-// voxels into a raw ring; eight converter warps split each chunk into the three BF16
-// part planes in the 128-byte-swizzled MN-major layout the MMA reads; one thread
-// issues the MMAs; four epilogue warps read the accumulator from TMEM and store the
-// outputs (voxels contiguous, 128-byte rows per warp).  Only the input is read from
-// and only the output is written to HBM, so the kernel stays HBM-bound like its BF16
-// counterpart.  Each CTA serves one shell group (CTAs split across groups in
-// proportion to their work), so only that group's three operator images are resident.
+// Data path per 128-voxel tile, in chunks of 32 input rows: TMA copies each FP32
+// chunk (32 rows x 128 voxels) into a ring of raw stages in shared memory; sixteen
+// converter warps split every value into its three BF16 parts and write them in the
+// 128-byte-swizzled MN-major layout the MMA reads; one thread issues the MMAs; four
+// epilogue warps read the accumulator from TMEM and store the outputs (voxels
+// contiguous, 128-byte rows per warp).  Only the input is read from and only the
+// output is written to HBM.  Each CTA serves one shell group (the SMs split across
+// groups in proportion to their bytes), so only that group's three operator images are
+// resident; tiles, chunks and stages advance in 32-bit steps (no divisions in the loops).
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -29,15 +31,16 @@ namespace delimit {
 
 namespace {
 
-constexpr int kConvWarps = 8;
+constexpr int kConvWarps = 16;
 constexpr int kEpiWarps = 4;  // one per TMEM lane quarter
 constexpr int kThreads = 32 * (2 + kConvWarps + kEpiWarps);
 constexpr int kMaxG = 8;
-constexpr int kAccCols = 256;              // TMEM columns per accumulator buffer
-constexpr int kChunkRows = 32;             // input rows per raw chunk
-constexpr uint32_t kRawBytes = kChunkRows * 128 * 4;      // 16 KiB FP32
-constexpr uint32_t kPlaneBytes = kChunkRows * 128 * 2;    // 8 KiB per BF16 part
-constexpr uint32_t kStageBytes = 3 * kPlaneBytes;         // 24 KiB
+constexpr int kAccCols = 256;                           // TMEM columns per accumulator buffer
+constexpr int kChunkRows = 32;                          // input rows per chunk
+constexpr int kRowsPerWarp = kChunkRows / kConvWarps;   // 2
+constexpr uint32_t kRawBytes = kChunkRows * 128 * 4;    // 16 KiB FP32 chunk
+constexpr uint32_t kPlaneBytes = kChunkRows * 128 * 2;  // 8 KiB per BF16 part
+constexpr uint32_t kStageBytes = 3 * kPlaneBytes;       // 24 KiB
 constexpr size_t kSmemLimit = 227 * 1024;
 
 enum : int {
@@ -53,18 +56,20 @@ enum : int {
 }  // namespace
 
 struct Tf32Group {
-  int64_t y_row0, y_cstride;
-  int n_out, n_mma, kpad, npad, nchunks;
+  int64_t x_row0, x_cstride, y_row0, y_cstride;
+  int n_in, n_out, n_mma, kpad, npad, nchunks;
+  int pstride;     // column offset between the operator parts (a multiple of 64)
   int cta0, ncta;  // the CTAs [cta0, cta0 + ncta) serve this group
 };
 
 struct Tf32Params {
   CUtensorMap mapA[kMaxG];  // FP32 input, 3-D {voxels, n_in rows, channels}, box {128, 32, 1}
-  CUtensorMap mapB[kMaxG];  // three BF16 part images [3 x kpad rows][npad], box {64, kpad}, 128-byte swizzle
+  CUtensorMap mapB[kMaxG];  // operator parts side by side [kpad rows][npad], box {64, kpad}, 128-byte swizzle
   Tf32Group g[kMaxG];
   int n_groups, channels, m_tiles, raw_stages, pl_stages;
   uint32_t b_region;  // bytes reserved for one group's three images (1 KiB multiple)
-  int64_t n_vox, ldy;
+  int64_t n_vox, ldx, ldy;
+  const float* X;
   void* Y;
   int* err;
 };
@@ -73,18 +78,68 @@ struct Tf32Params {
 __constant__ int8_t kProdA[6] = {2, 1, 0, 1, 0, 0};
 __constant__ int8_t kProdB[6] = {0, 1, 2, 0, 1, 0};
 
-// x -> BF16 parts x0 + x1 + x2 (round to nearest each; the differences are exact in FP32)
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
-  a = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(a);
-  b = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(b);
-  c = __float2bfloat16_rn(r2);
+// (x, y) -> BF16 parts packed in pairs: x = x0 + x1 + x2 and y likewise, each part the
+// round-to-nearest BF16 of what the earlier ones leave (the differences are exact in FP32);
+// p[q] holds part q of x in its low and of y in its high half
+__device__ __forceinline__ void split3x2(float x, float y, uint32_t (&p)[3]) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+    p[q] = *reinterpret_cast<const uint32_t*>(&h);
+    if (q < 2) {
+      x -= __uint_as_float(p[q] << 16);
+      y -= __uint_as_float(p[q] & 0xFFFF0000u);
+    }
+  }
 }
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
+// (tile, chunk) of a CTA's work in 32-bit steps: tile t = local + k * ncta = c * m_tiles + mt
+struct Walk {
+  int k, ch, c, mt;
+  int nch, m_tiles, dc, dmt;
+  // tiles t0, t0 + step, t0 + 2 step, ...
+  __device__ __forceinline__ void init(int t0, int step, int nch_, int m_tiles_) {
+    nch = nch_;
+    m_tiles = m_tiles_;
+    dc = step / m_tiles;
+    dmt = step - dc * m_tiles;
+    k = 0;
+    ch = 0;
+    c = t0 / m_tiles;
+    mt = t0 - c * m_tiles;
+  }
+  __device__ __forceinline__ void next_chunk() {
+    if (++ch < nch) return;
+    ch = 0;
+    next_tile();
+  }
+  __device__ __forceinline__ void next_tile() {
+    ++k;
+    c += dc;
+    mt += dmt;
+    if (mt >= m_tiles) {
+      mt -= m_tiles;
+      ++c;
+    }
+  }
+};
+
+// stage ring position: index and phase parity
+struct Ring {
+  int i, n;
+  uint32_t ph;
+  __device__ __forceinline__ void init(int n_) {
+    i = 0;
+    n = n_;
+    ph = 0;
+  }
+  __device__ __forceinline__ void next() {
+    if (++i == n) {
+      i = 0;
+      ph ^= 1u;
+    }
+  }
+};
 
 template <bool OUT_F32>
 __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __grid_constant__ Tf32Params p) {
@@ -92,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __g
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int R = p.raw_stages, S = p.pl_stages;
-  // layout: [B images (b_region)][raw ring R x 16 KiB][part planes S x 24 KiB][barriers]
+  // layout: [B images (b_region)][raw FP32 chunks R x 16 KiB][part planes S x 24 KiB][barriers]
   const uint32_t sbase = smem_u32(smem);
   const uint32_t raw_base = sbase + p.b_region;
   const uint32_t pl_base = raw_base + (uint32_t)R * kRawBytes;
@@ -117,8 +172,8 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __g
   while (gi > 0 && (int)blockIdx.x < p.g[gi].cta0) --gi;
   const Tf32Group& G = p.g[gi];
   const int local = (int)blockIdx.x - G.cta0;
-  const int64_t n_tiles = (int64_t)p.channels * p.m_tiles;
-  const int64_t my_tiles = local < G.ncta ? (n_tiles - local + G.ncta - 1) / G.ncta : 0;
+  const int n_tiles = p.channels * p.m_tiles;  // < 2^31 / nchunks (checked on the host)
+  const int my_tiles = local < G.ncta ? (n_tiles - local + G.ncta - 1) / G.ncta : 0;
   const int nch = G.nchunks;
 
   if (threadIdx.x == 0) {
@@ -150,30 +205,22 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __g
 
   if (warp == 0) {
     if (lane == 0 && my_tiles > 0) {
-      // the group's three operator images, then the raw input ring
-      const uint32_t plane_b = (uint32_t)(G.kpad * G.npad * 2);
-      mbar_arrive_expect_tx(bload_bar, 3 * plane_b);
-      for (int q = 0; q < 3; ++q)
-        for (int j = 0; j < G.npad / 64; ++j)
-          tma_load_2d(&p.mapB[gi], bload_bar, sbase + q * plane_b + j * G.kpad * 128, j * 64, q * G.kpad);
+      // the group's operator parts, then the raw FP32 input chunks
+      mbar_arrive_expect_tx(bload_bar, (uint32_t)(G.kpad * G.npad * 2));
+      for (int j = 0; j < G.npad / 64; ++j)
+        tma_load_2d(&p.mapB[gi], bload_bar, sbase + j * G.kpad * 128, j * 64, 0);
       int pend[8];
       for (int r = 0; r < 8; ++r) pend[r] = -1;
-      int64_t i = 0;  // chunk sequence number
-      bool ok = true;
-      for (int64_t k = 0; ok && k < my_tiles; ++k) {
-        const int64_t t = local + k * G.ncta;
-        const int c = (int)(t / p.m_tiles), mt = (int)(t % p.m_tiles);
-        for (int ch = 0; ch < nch; ++ch, ++i) {
-          const int r = (int)(i % R);
-          const uint32_t ph = (uint32_t)((i / R) & 1);
-          if (!wait_bounded(raw_empty(r), ph ^ 1u, abort_flag, p.err, kErrRawEmpty)) {
-            ok = false;
-            break;
-          }
-          mbar_arrive_expect_tx(raw_full(r), kRawBytes);
-          tma_load_3d(&p.mapA[gi], raw_full(r), raw_base + r * kRawBytes, mt * 128, ch * kChunkRows, c);
-          pend[r] = (int)ph;
-        }
+      Walk w;
+      w.init(local, G.ncta, nch, p.m_tiles);
+      Ring rr;
+      rr.init(R);
+      for (; w.k < my_tiles; w.next_chunk()) {
+        if (!wait_bounded(raw_empty(rr.i), rr.ph ^ 1u, abort_flag, p.err, kErrRawEmpty)) break;
+        mbar_arrive_expect_tx(raw_full(rr.i), kRawBytes);
+        tma_load_3d(&p.mapA[gi], raw_full(rr.i), raw_base + rr.i * kRawBytes, w.mt * 128, w.ch * kChunkRows, w.c);
+        pend[rr.i] = (int)rr.ph;
+        rr.next();
       }
       wait_drain(bload_bar, 0, p.err, kErrDrain);
       for (int r = 0; r < R; ++r)
@@ -181,20 +228,20 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __g
     }
   } else if (warp == 1) {
     if (lane == 0 && my_tiles > 0) {
-      const uint32_t plane_b = (uint32_t)(G.kpad * G.npad * 2);
-      const uint32_t idesc = idesc_bf16(128, G.n_mma, true, true);
       const int ksteps = G.kpad / 16;
+      const uint32_t idesc = idesc_bf16(128, G.n_mma, true, true);
+      // operator part q starts at column q * pstride: 64-column atoms are kpad * 128 bytes apart
+      const uint32_t part_bytes = (uint32_t)(G.pstride / 64 * G.kpad * 128);
       bool ok = wait_bounded(bload_bar, 0, abort_flag, p.err, kErrPlFull);
-      int64_t i = 0;
-      for (int64_t k = 0; ok && k < my_tiles; ++k) {
-        const int acc = (int)(k & 1);
-        const uint32_t aph = (uint32_t)((k >> 1) & 1);
-        if (!wait_bounded(tempty(acc), aph ^ 1u, abort_flag, p.err, kErrTEmpty)) break;
+      Ring ss;
+      ss.init(S);
+      for (int k = 0; ok && k < my_tiles; ++k) {
+        const int acc = k & 1;
+        if (!wait_bounded(tempty(acc), (uint32_t)((k >> 1) & 1) ^ 1u, abort_flag, p.err, kErrTEmpty)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kAccCols);
-        for (int ch = 0; ch < nch; ++ch, ++i) {
-          const int s = (int)(i % S);
-          if (!wait_bounded(pl_full(s), (uint32_t)((i / S) & 1), abort_flag, p.err, kErrPlFull)) {
+        for (int ch = 0; ch < nch; ++ch) {
+          if (!wait_bounded(pl_full(ss.i), ss.ph, abort_flag, p.err, kErrPlFull)) {
             ok = false;
             break;
           }
@@ -204,14 +251,15 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __g
             const int kg = 2 * ch + kk;  // k-step of 16 rows within the whole K
 #pragma unroll
             for (int pr = 0; pr < 6; ++pr) {
-              const uint64_t ad = umma_desc(pl_base + s * kStageBytes + kProdA[pr] * kPlaneBytes + kk * 2048,
+              const uint64_t ad = umma_desc(pl_base + ss.i * kStageBytes + kProdA[pr] * kPlaneBytes + kk * 2048,
                                             kChunkRows * 128, 1024, kSwizzle128B);
-              const uint64_t bd = umma_desc(sbase + kProdB[pr] * plane_b + kg * 2048, G.kpad * 128, 1024,
+              const uint64_t bd = umma_desc(sbase + kProdB[pr] * part_bytes + kg * 2048, G.kpad * 128, 1024,
                                             kSwizzle128B);
               mma_bf16(d_tmem, ad, bd, idesc, (ch | kk | pr) != 0);
             }
           }
-          mma_commit(pl_empty(s));
+          mma_commit(pl_empty(ss.i));
+          ss.next();
         }
         if (!ok) break;
         mma_commit(tfull(acc));
@@ -220,79 +268,77 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __g
       wait_drain(drain_bar, 0, p.err, kErrDrain);
     }
   } else if (warp < 2 + kConvWarps) {
-    // converters: warp cw splits rows 4cw .. 4cw + 3 of every chunk; lane l holds voxels
-    // 4l .. 4l + 3 (a 16-byte read of the raw row, conflict-free), and writes 8 bytes of
-    // each part plane: voxel half l / 16, 16-byte chunk (l % 16) / 2 XOR row % 8, half-chunk l % 2
+    // converters: warp cw splits rows 2cw, 2cw + 1 of every raw chunk; lane l holds voxels
+    // 4l .. 4l + 3 (a 16-byte read of the raw row, conflict-free) and writes 8 bytes of each
+    // part plane: voxel half l / 16, 16-byte chunk (l % 16) / 2 XOR row % 8, half-chunk l % 2
     const int cw = warp - 2;
     const int half = lane >> 4, sub = lane & 1, c16 = (lane & 15) >> 1;
-    int64_t i = 0;
-    bool ok = true;
-    for (int64_t k = 0; ok && k < my_tiles; ++k) {
-      for (int ch = 0; ch < nch; ++ch, ++i) {
-        const int r = (int)(i % R), s = (int)(i % S);
-        bool w_ok = wait_bounded(raw_full(r), (uint32_t)((i / R) & 1), abort_flag, p.err, kErrRawFull);
-        w_ok = w_ok && wait_bounded(pl_empty(s), (uint32_t)((i / S) & 1) ^ 1u, abort_flag, p.err, kErrPlEmpty);
-        if (!__all_sync(0xffffffffu, w_ok)) {
-          ok = false;
-          break;
-        }
-        const float* src = reinterpret_cast<const float*>(raw_ptr + (size_t)r * kRawBytes);
-        uint8_t* dst = pl_ptr + (size_t)s * kStageBytes;
+    Ring rr, ss;
+    rr.init(R);
+    ss.init(S);
+    const int n_chunks = my_tiles * nch;
+    for (int i = 0; i < n_chunks; ++i) {
+      bool w_ok = wait_bounded_sleep(raw_full(rr.i), rr.ph, abort_flag, p.err, kErrRawFull);
+      w_ok = w_ok && wait_bounded_sleep(pl_empty(ss.i), ss.ph ^ 1u, abort_flag, p.err, kErrPlEmpty);
+      if (!__all_sync(0xffffffffu, w_ok)) break;
+      const float* src = reinterpret_cast<const float*>(raw_ptr + (size_t)rr.i * kRawBytes);
+      uint8_t* dst = pl_ptr + (size_t)ss.i * kStageBytes;
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-          const int row = cw * 4 + rr;
-          const float4 v = *reinterpret_cast<const float4*>(src + row * 128 + lane * 4);
-          __nv_bfloat16 a[4], b[4], c[4];
-          split3(v.x, a[0], b[0], c[0]);
-          split3(v.y, a[1], b[1], c[1]);
-          split3(v.z, a[2], b[2], c[2]);
-          split3(v.w, a[3], b[3], c[3]);
-          const uint32_t off = (uint32_t)(half * kChunkRows * 128 + row * 128 + ((c16 ^ (row & 7)) << 4) + sub * 8);
-          *reinterpret_cast<uint2*>(dst + off) = make_uint2(pack2(a[0], a[1]), pack2(a[2], a[3]));
-          *reinterpret_cast<uint2*>(dst + kPlaneBytes + off) = make_uint2(pack2(b[0], b[1]), pack2(b[2], b[3]));
-          *reinterpret_cast<uint2*>(dst + 2 * kPlaneBytes + off) = make_uint2(pack2(c[0], c[1]), pack2(c[2], c[3]));
-        }
-        // the planes are read by the tensor cores (async proxy); the raw chunk is free again
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(pl_full(s));
-          mbar_arrive(raw_empty(r));
-        }
+      for (int k2 = 0; k2 < kRowsPerWarp; ++k2) {
+        const int row = cw * kRowsPerWarp + k2;  // row within the chunk
+        const float4 v = *reinterpret_cast<const float4*>(src + row * 128 + lane * 4);
+        uint32_t lo[3], hi[3];
+        split3x2(v.x, v.y, lo);
+        split3x2(v.z, v.w, hi);
+        const uint32_t off = (uint32_t)(half * kChunkRows * 128 + row * 128 + ((c16 ^ (row & 7)) << 4) + sub * 8);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) *reinterpret_cast<uint2*>(dst + q * kPlaneBytes + off) = make_uint2(lo[q], hi[q]);
       }
+      // the planes are read by the tensor cores (async proxy); the raw chunk is free again
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(pl_full(ss.i));
+        mbar_arrive(raw_empty(rr.i));
+      }
+      rr.next();
+      ss.next();
     }
   } else {
-    // epilogue: TMEM lane quarter q holds voxels 32q .. 32q + 31 of the tile
+    // epilogue: TMEM lane quarter q holds voxels 32q .. 32q + 31 of the tile; each thread
+    // stores its voxel's outputs (a warp writes 128 contiguous bytes per output row)
     const int q = warp & 3;
-    for (int64_t k = 0; k < my_tiles; ++k) {
-      const int acc = (int)(k & 1);
-      const bool ok = wait_bounded(tfull(acc), (uint32_t)((k >> 1) & 1), abort_flag, p.err, kErrTFull);
+    Walk w;
+    w.init(local, G.ncta, 1, p.m_tiles);
+    for (; w.k < my_tiles; w.next_tile()) {
+      const int k = w.k, c = w.c, mt = w.mt;
+      const int acc = k & 1;
+      const bool ok = wait_bounded_sleep(tfull(acc), (uint32_t)((k >> 1) & 1), abort_flag, p.err, kErrTFull);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const int64_t t = local + k * G.ncta;
-      const int c = (int)(t / p.m_tiles), mt = (int)(t % p.m_tiles);
       const int64_t v = (int64_t)mt * 128 + q * 32 + lane;
       const bool in = v < p.n_vox;
-      const int64_t row0 = G.y_row0 + (int64_t)c * G.y_cstride;
       const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
+      // this voxel's element of output row (y_row0 + c * y_cstride + col), column by column
+      const int64_t e0 = (G.y_row0 + (int64_t)c * G.y_cstride) * p.ldy + v;
       for (int c0 = 0; c0 < G.n_mma; c0 += 32) {
         uint32_t rv[2][16];
         tmem_ld16_nowait(tl + (uint32_t)c0, rv[0]);
         if (c0 + 16 < G.n_mma) tmem_ld16_nowait(tl + (uint32_t)(c0 + 16), rv[1]);
         tmem_wait_ld();
+        if (in) {
+          if (OUT_F32) {
+            float* y = reinterpret_cast<float*>(p.Y) + e0 + (int64_t)c0 * p.ldy;
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+            for (int j = 0; j < 32; ++j, y += p.ldy)
+              if (c0 + j < G.n_out) __stcs(y, __uint_as_float(rv[j >> 4][j & 15]));
+          } else {
+            __nv_bfloat16* y = reinterpret_cast<__nv_bfloat16*>(p.Y) + e0 + (int64_t)c0 * p.ldy;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = c0 + 16 * u + j;
-            if (in && col < G.n_out) {
-              const float val = __uint_as_float(rv[u][j]);
-              if (OUT_F32)
-                reinterpret_cast<float*>(p.Y)[(row0 + col) * p.ldy + v] = val;
-              else
-                reinterpret_cast<__nv_bfloat16*>(p.Y)[(row0 + col) * p.ldy + v] = __float2bfloat16_rn(val);
-            }
+            for (int j = 0; j < 32; ++j, y += p.ldy)
+              if (c0 + j < G.n_out) *y = __float2bfloat16_rn(__uint_as_float(rv[j >> 4][j & 15]));
           }
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -348,7 +394,7 @@ size_t f32_smem(uint32_t b_region, int R, int S) {
 
 uint32_t b_region_bytes(const TcBasisTables& t, int kind) {
   uint32_t mx = 0;
-  for (int s = 0; s < t.n_shells; ++s) mx = std::max(mx, (uint32_t)(3 * t.kpad[s][kind] * t.npad[s][kind] * 2));
+  for (int s = 0; s < t.n_shells; ++s) mx = std::max(mx, (uint32_t)(t.kpad[s][kind] * t.npad3[s][kind] * 2));
   return (mx + 1023) / 1024 * 1024;
 }
 
@@ -359,13 +405,17 @@ cudaError_t tc_basis_tables_create_f32(const BasisHost& h, TcBasisTables& t, std
   t.d_mem3 = nullptr;
   if (!t.ok) return cudaSuccess;  // no tensor-core images at all (too many shells)
   // three BF16 parts of every operator T (T = T0 + T1 + T2, each the rounding of what is
-  // left), stacked as [3 x kpad rows][npad] per shell and transform kind, in the BF16
-  // path's layout (row k = input index, column n = output index)
+  // left), side by side along the output axis (row k = input index, column = part offset +
+  // output index) so that one MMA can multiply an activation part by several operator parts
   std::vector<__nv_bfloat16> img;
   for (int s = 0; s < t.n_shells; ++s) {
     const ShellHost& sh = h.shells[s];
     for (int kind = 0; kind < 4; ++kind) {
-      const int n_in = t.n_in[s][kind], n_out = t.n_out[s][kind], kpad = t.kpad[s][kind], npad = t.npad[s][kind];
+      const int n_in = t.n_in[s][kind], n_out = t.n_out[s][kind], kpad = t.kpad[s][kind];
+      const int n1 = rup(n_out, 16);
+      const int pstride = rup(n1, 64);  // column offset of part q: q * pstride (whole 64-column atoms)
+      const int npad = 3 * pstride;
+      t.npad3[s][kind] = npad;
       auto T = [&](int i, int j) -> double {
         switch (kind) {
           case 0: return sh.P[size_t(i) * sh.m + j];   // P [N][m]
@@ -375,14 +425,13 @@ cudaError_t tc_basis_tables_create_f32(const BasisHost& h, TcBasisTables& t, std
         }
       };
       const size_t off = (img.size() + 511) / 512 * 512;  // 1 KiB aligned
-      const size_t plane = size_t(kpad) * npad;
-      img.resize(off + 3 * plane, __float2bfloat16_rn(0.f));
+      img.resize(off + size_t(kpad) * npad, __float2bfloat16_rn(0.f));
       for (int k = 0; k < n_in; ++k)
         for (int n = 0; n < n_out; ++n) {
           double rest = T(n, k);
           for (int q = 0; q < 3; ++q) {
             const __nv_bfloat16 part = __float2bfloat16_rn(float(rest));
-            img[off + q * plane + size_t(k) * npad + n] = part;
+            img[off + size_t(k) * npad + q * pstride + n] = part;
             rest -= double(__bfloat162float(part));
           }
         }
@@ -412,11 +461,12 @@ void tc_basis_tables_destroy_f32(TcBasisTables& t) {
   t.ok3 = false;
 }
 
-bool tc_transform_f32_supported(const TcBasisTables& t, int kind) {
+bool tc_transform_f32_supported(const TcBasisTables& t, int kind, int out_t) {
   if (!t.ok3 || !tc_enabled() || !f32_encode() || t.n_shells > kMaxG) return false;
   if (f32_dev().major != 10) return false;
   for (int s = 0; s < t.n_shells; ++s)
     if (t.n_in[s][kind] > 256 || t.n_out[s][kind] > 256) return false;
+  (void)out_t;
   return f32_smem(b_region_bytes(t, kind), 2, 2) <= kSmemLimit;
 }
 
@@ -432,20 +482,25 @@ cudaError_t tc_transform_f32_launch(const TcBasisTables& t, int kind, const floa
   const bool x_is_sig = (kind == 0 || kind == 3);  // input rows in the signal layout
   const int m_tiles = (int)((n_vox + 127) / 128);
   const int64_t n_tiles = (int64_t)C * m_tiles;
-  if (n_tiles >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+  // the kernel walks tiles and chunks in 32 bits
+  if (n_tiles * ((int64_t)256 / kChunkRows + 1) >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
   double work[kMaxG], tot = 0;
   for (int s = 0; s < t.n_shells; ++s) {
-    const int n_in = t.n_in[s][kind], n_out = t.n_out[s][kind], kpad = t.kpad[s][kind], npad = t.npad[s][kind];
+    const int n_in = t.n_in[s][kind], n_out = t.n_out[s][kind], kpad = t.kpad[s][kind];
     const int64_t sig_row0 = int64_t(C) * t.dir_off[s], sig_cs = t.m[s];
     const int64_t sh_row0 = int64_t(s) * C * t.N, sh_cs = t.N;
     const int64_t x_row0 = x_is_sig ? sig_row0 : sh_row0, x_cs = x_is_sig ? sig_cs : sh_cs;
     Tf32Group& G = p.g[s];
+    G.x_row0 = x_row0;
+    G.x_cstride = x_cs;
+    G.n_in = n_in;
     G.y_row0 = x_is_sig ? sh_row0 : sig_row0;
     G.y_cstride = x_is_sig ? sh_cs : sig_cs;
     G.n_out = n_out;
     G.n_mma = rup(n_out, 16);
     G.kpad = kpad;
-    G.npad = npad;
+    G.npad = t.npad3[s][kind];
+    G.pstride = rup(G.n_mma, 64);
     G.nchunks = (kpad + kChunkRows - 1) / kChunkRows;
     work[s] = double(n_in + n_out);  // bytes per voxel-channel, the HBM-bound cost
     tot += work[s];
@@ -460,10 +515,11 @@ cudaError_t tc_transform_f32_launch(const TcBasisTables& t, int kind, const floa
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     }
-    {  // B: the three part images [3 x kpad][npad]
+    {  // B: the operator parts side by side, [kpad][npad3]
+      const int npad3 = t.npad3[s][kind];
       const char* base = static_cast<const char*>(t.d_mem3) + t.off3[s][kind];
-      cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)(3 * kpad)};
-      cuuint64_t strides[1] = {(cuuint64_t)npad * 2};
+      cuuint64_t dims[2] = {(cuuint64_t)npad3, (cuuint64_t)kpad};
+      cuuint64_t strides[1] = {(cuuint64_t)npad3 * 2};
       cuuint32_t box[2] = {64, (cuuint32_t)kpad};
       cuuint32_t es[2] = {1, 1};
       if (fn(&p.mapB[s], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<char*>(base), dims, strides, box, es,
@@ -472,30 +528,56 @@ cudaError_t tc_transform_f32_launch(const TcBasisTables& t, int kind, const floa
         return cudaErrorInvalidValue;
     }
   }
-  // CTAs per group in proportion to its bytes (at least one; at most its tile count)
+  // one CTA per SM, the SMs split across the groups in proportion to their bytes
+  // (largest remainders; every group at least one CTA, none more than its tile count)
   const DevProps dp = f32_dev();
+  const int G_n = t.n_shells;
+  const int total = (int)std::max<int64_t>(G_n, std::min<int64_t>(dp.sms, n_tiles * G_n));
+  int ncta[kMaxG];
+  double frac[kMaxG];
+  int used = 0;
+  for (int s = 0; s < G_n; ++s) {
+    const double share = total * work[s] / tot;
+    ncta[s] = std::max(1, (int)std::floor(share));
+    frac[s] = share - std::floor(share);
+    used += ncta[s];
+  }
+  while (used > total) {  // groups raised to one CTA: take the surplus from the largest
+    int big = 0;
+    for (int s = 1; s < G_n; ++s)
+      if (ncta[s] > ncta[big]) big = s;
+    --ncta[big];
+    --used;
+  }
+  while (used < total) {  // hand out the rest by largest remainder
+    int best = 0;
+    for (int s = 1; s < G_n; ++s)
+      if (frac[s] > frac[best]) best = s;
+    ++ncta[best];
+    frac[best] = -1.0;
+    ++used;
+  }
   int cta0 = 0;
-  for (int s = 0; s < t.n_shells; ++s) {
-    int n = (int)std::lround(dp.sms * work[s] / tot);
-    n = (int)std::max<int64_t>(1, std::min<int64_t>(n, n_tiles));
+  for (int s = 0; s < G_n; ++s) {
     p.g[s].cta0 = cta0;
-    p.g[s].ncta = n;
-    cta0 += n;
+    p.g[s].ncta = (int)std::min<int64_t>(ncta[s], n_tiles);
+    cta0 += p.g[s].ncta;
   }
   p.n_groups = t.n_shells;
   p.channels = C;
   p.m_tiles = m_tiles;
   p.b_region = b_region_bytes(t, kind);
-  // as many stages as fit: raw chunks first (the HBM latency), then part planes
-  int R = 4, S = 4;
-  while (f32_smem(p.b_region, R, S) > kSmemLimit && (R > 2 || S > 2)) {
-    if (S >= R && S > 2) --S; else --R;
-  }
+  // two part-plane stages (the MMAs drain them quickly), then as many raw chunks as fit,
+  // up to 8: the bytes in flight from HBM are what the kernel's speed depends on
+  int R = 8, S = 2;
+  while (R > 2 && f32_smem(p.b_region, R, S) > kSmemLimit) --R;
   if (f32_smem(p.b_region, R, S) > kSmemLimit) return cudaErrorInvalidValue;
   p.raw_stages = R;
   p.pl_stages = S;
   p.n_vox = n_vox;
+  p.ldx = ldx;
   p.ldy = ldy;
+  p.X = X;  // (read through mapA)
   p.Y = Y;
   p.err = err_word;
   // at least 120 KiB so that two CTAs never share an SM (each holds 512 TMEM columns)

@@ -20,19 +20,43 @@ def _leaky(x, s):
     return np.where(x > 0, x, s * x)
 
 
-def test_net_gradients_match_oracle():
-    """A 4-LSC network (4 hidden channels, FP32 path) on 6 voxels: the weight and bias
-    gradients from autograd over the library's kernels equal the FP64 oracle's
-    hand-chained adjoints (Signal2SH, LSC, leaky ReLU, SH2Signal)."""
-    cfg = N.NetConfig(hidden=4, dirs_per_shell=(30, 30, 30), n_in_dirs=20, rings=2, sectors=6)
+# (precision, network, voxels, tolerance of the prediction, of the weight and bias gradients).
+# FP32: a small network, FP32-level agreement.  BF16: the trained network's widths (64 hidden
+# channels, 3 x 90 targets, 4 x 12 kernels); a BF16 storage model of this network (every
+# stored tensor and operator rounded to BF16, products exact) puts the prediction at 5.4e-3
+# and the weight gradients of the three deeper layers at 3.6-4.7e-2 from FP64 (the rounding
+# compounds through four layers of forward and backward), hence 1e-2 and 1e-1 here.
+NET_CASES = {
+    "f32_small": (torch.float32, dict(hidden=4, dirs_per_shell=(30, 30, 30), n_in_dirs=20, rings=2, sectors=6), 6,
+                  1e-4, 1e-4),
+    "bf16_c4_widths": (torch.bfloat16, dict(), 32, 1e-2, 1e-1),
+}
+
+
+@pytest.mark.parametrize("case", list(NET_CASES))
+def test_net_gradients_match_oracle(case):
+    """A 4-LSC network: the prediction and the weight and bias gradients from autograd over
+    the library's kernels against the FP64 oracle's hand-chained adjoints (Signal2SH, LSC,
+    leaky ReLU, SH2Signal), in FP32 on a small network and in BF16 at the trained
+    network's widths."""
+    dtype, kw, V, tol_pred, tol_grad = NET_CASES[case]
+    cfg = N.NetConfig(**kw)
     dirs, bvals, sel = N.tables(cfg)
-    net = N.SphericalNet(cfg, dirs[sel], dirs, bvals, dtype=torch.float32).cuda()
-    V = 6
-    x = synth.fibre_signal(dirs, bvals, V, seed=3).astype(np.float64)  # [V, 90]
-    G = synth.gaussian((V, 90), 1.0, seed=4, tag="grads")
+    net = N.SphericalNet(cfg, dirs[sel], dirs, bvals, dtype=dtype).cuda()
+    # biases away from zero, so that the bias path is exercised
+    with torch.no_grad():
+        for i, lsc in enumerate(net.lscs):
+            g = torch.Generator().manual_seed(100 + i)
+            lsc.bias.copy_(0.05 * torch.randn(lsc.bias.shape, generator=g))
+    n_t = sum(cfg.dirs_per_shell)
+    x = synth.fibre_signal(dirs, bvals, V, seed=3).astype(np.float64)  # [V, n_t]
+    G = synth.gaussian((V, n_t), 1.0, seed=4, tag="grads")
     xt = torch.from_numpy(np.ascontiguousarray(x[:, sel].T)).float().cuda()
+    if dtype == torch.bfloat16:  # the oracle sees the values the BF16 network reads
+        xt = xt.to(torch.bfloat16)
+        x[:, sel] = xt.float().cpu().numpy().T
     pred = net(xt)
-    loss = (pred * torch.from_numpy(np.ascontiguousarray(G.T)).float().cuda()).sum()
+    loss = (pred.float() * torch.from_numpy(np.ascontiguousarray(G.T)).float().cuda()).sum()
     loss.backward()
     # oracle forward
     ob_in = osh.SHBasisOracle(dirs[sel], np.full(len(sel), 1000.0), cfg.order_in, cfg.lam_in)
@@ -47,7 +71,7 @@ def test_net_gradients_match_oracle():
         z = og.forward(h[-1], ws[i], bs[i])
         h.append(_leaky(z, cfg.slope) if i < cfg.n_lsc - 1 else z)
     out = ob.sh2signal(h[-1])[:, 0, :]
-    np.testing.assert_allclose(pred.detach().cpu().numpy().T, out, rtol=0, atol=1e-4 * np.abs(out).max())
+    assert rel_l2(pred.detach().float().cpu().numpy().T, out) <= tol_pred
     # oracle backward
     d = ob.sh2signal_backward(G[:, None, :])
     for i in reversed(range(cfg.n_lsc)):
@@ -56,8 +80,8 @@ def test_net_gradients_match_oracle():
         d_in, dw, db = ogs[i].backward(h[i], ws[i], d)
         got_w = net.lscs[i].weight.grad.cpu().double().numpy()
         got_b = net.lscs[i].bias.grad.cpu().double().numpy()
-        assert rel_l2(got_w, dw) <= 1e-4, (i, rel_l2(got_w, dw))
-        assert rel_l2(got_b, db) <= 1e-4, (i, rel_l2(got_b, db))
+        assert rel_l2(got_w, dw) <= tol_grad, (i, rel_l2(got_w, dw))
+        assert rel_l2(got_b, db) <= tol_grad, (i, rel_l2(got_b, db))
         d = d_in
 
 
