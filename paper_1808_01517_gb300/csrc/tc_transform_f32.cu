@@ -9,8 +9,8 @@
 // accumulated in FP32 in TMEM, smallest first.
 //
 // Data path per 128-voxel tile, in chunks of 32 input rows: TMA copies each FP32
-// chunk (32 rows x 128 voxels) into a ring of raw stages in shared memory; sixteen
-// converter warps split every value into its three BF16 parts and write them in the
+// chunk (32 rows x 128 voxels, as four 128-byte-swizzled boxes of 32 voxels) into a ring
+// of raw stages in shared memory; four converter warps split every value into its three BF16 parts and write them in the
 // 128-byte-swizzled MN-major layout the MMA reads; one thread issues the MMAs; four
 // epilogue warps read the accumulator from TMEM and store the outputs (voxels
 // contiguous, 128-byte rows per warp).  Only the input is read from and only the
@@ -31,13 +31,13 @@ namespace delimit {
 
 namespace {
 
-constexpr int kConvWarps = 16;
+constexpr int kConvWarps = 4;
 constexpr int kEpiWarps = 4;  // one per TMEM lane quarter
 constexpr int kThreads = 32 * (2 + kConvWarps + kEpiWarps);
 constexpr int kMaxG = 8;
 constexpr int kAccCols = 256;                           // TMEM columns per accumulator buffer
 constexpr int kChunkRows = 32;                          // input rows per chunk
-constexpr int kRowsPerWarp = kChunkRows / kConvWarps;   // 2
+constexpr int kRowsPerWarp = kChunkRows / kConvWarps;   // rows each converter warp splits per chunk
 constexpr uint32_t kRawBytes = kChunkRows * 128 * 4;    // 16 KiB FP32 chunk
 constexpr uint32_t kPlaneBytes = kChunkRows * 128 * 2;  // 8 KiB per BF16 part
 constexpr uint32_t kStageBytes = 3 * kPlaneBytes;       // 24 KiB
@@ -63,7 +63,7 @@ struct Tf32Group {
 };
 
 struct Tf32Params {
-  CUtensorMap mapA[kMaxG];  // FP32 input, 3-D {voxels, n_in rows, channels}, box {128, 32, 1}
+  CUtensorMap mapA[kMaxG];  // FP32 input, 3-D {voxels, n_in rows, channels}, box {32, 32, 1}, 128-byte swizzle
   CUtensorMap mapB[kMaxG];  // operator parts side by side [kpad rows][npad], box {64, kpad}, 128-byte swizzle
   Tf32Group g[kMaxG];
   int n_groups, channels, m_tiles, raw_stages, pl_stages;
@@ -218,7 +218,11 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __g
       for (; w.k < my_tiles; w.next_chunk()) {
         if (!wait_bounded(raw_empty(rr.i), rr.ph ^ 1u, abort_flag, p.err, kErrRawEmpty)) break;
         mbar_arrive_expect_tx(raw_full(rr.i), kRawBytes);
-        tma_load_3d(&p.mapA[gi], raw_full(rr.i), raw_base + rr.i * kRawBytes, w.mt * 128, w.ch * kChunkRows, w.c);
+        // four boxes of 32 voxels x 32 rows, 128-byte swizzled: box b at b * 4 KiB
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          tma_load_3d(&p.mapA[gi], raw_full(rr.i), raw_base + rr.i * kRawBytes + b * (kRawBytes / 4), w.mt * 128 + 32 * b,
+                      w.ch * kChunkRows, w.c);
         pend[rr.i] = (int)rr.ph;
         rr.next();
       }
@@ -246,9 +250,10 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __g
             break;
           }
           tc_fence_after();
-          const int kk_n = min(2, ksteps - 2 * ch);
+          constexpr int kKs = kChunkRows / 16;  // k-steps of 16 rows per chunk
+          const int kk_n = min(kKs, ksteps - kKs * ch);
           for (int kk = 0; kk < kk_n; ++kk) {
-            const int kg = 2 * ch + kk;  // k-step of 16 rows within the whole K
+            const int kg = kKs * ch + kk;  // k-step of 16 rows within the whole K
 #pragma unroll
             for (int pr = 0; pr < 6; ++pr) {
               const uint64_t ad = umma_desc(pl_base + ss.i * kStageBytes + kProdA[pr] * kPlaneBytes + kk * 2048,
@@ -268,8 +273,8 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __g
       wait_drain(drain_bar, 0, p.err, kErrDrain);
     }
   } else if (warp < 2 + kConvWarps) {
-    // converters: warp cw splits rows 2cw, 2cw + 1 of every raw chunk; lane l holds voxels
-    // 4l .. 4l + 3 (a 16-byte read of the raw row, conflict-free) and writes 8 bytes of each
+    // converters: warp cw splits rows cw * kRowsPerWarp ... of every raw chunk; lane l holds voxels
+    // 4l .. 4l + 3 (a 16-byte read from the swizzled boxes, conflict-free) and writes 8 bytes of each
     // part plane: voxel half l / 16, 16-byte chunk (l % 16) / 2 XOR row % 8, half-chunk l % 2
     const int cw = warp - 2;
     const int half = lane >> 4, sub = lane & 1, c16 = (lane & 15) >> 1;
@@ -286,7 +291,9 @@ __global__ void __launch_bounds__(kThreads, 1) transform_tc_f32_kernel(const __g
 #pragma unroll
       for (int k2 = 0; k2 < kRowsPerWarp; ++k2) {
         const int row = cw * kRowsPerWarp + k2;  // row within the chunk
-        const float4 v = *reinterpret_cast<const float4*>(src + row * 128 + lane * 4);
+        // voxels 4l .. 4l + 3: box l / 8, 16-byte chunk (l % 8) XOR row % 8 of its 128-byte row
+        const float4 v = *reinterpret_cast<const float4*>(src + (lane >> 3) * (kChunkRows * 32) + row * 32 +
+                                                          (((lane & 7) ^ (row & 7)) << 2));
         uint32_t lo[3], hi[3];
         split3x2(v.x, v.y, lo);
         split3x2(v.z, v.w, hi);
@@ -508,10 +515,10 @@ cudaError_t tc_transform_f32_launch(const TcBasisTables& t, int kind, const floa
       const char* base = reinterpret_cast<const char*>(X) + x_row0 * ldx * 4;
       cuuint64_t dims[3] = {(cuuint64_t)n_vox, (cuuint64_t)n_in, (cuuint64_t)C};
       cuuint64_t strides[2] = {(cuuint64_t)ldx * 4, (cuuint64_t)(x_cs * ldx * 4)};
-      cuuint32_t box[3] = {128, (cuuint32_t)kChunkRows, 1};
+      cuuint32_t box[3] = {32, (cuuint32_t)kChunkRows, 1};
       cuuint32_t es[3] = {1, 1, 1};
       if (fn(&p.mapA[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<char*>(base), dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     }
