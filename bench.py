@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip fp32 / e2e / cpu / transform legs (profiling runs)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "f32"],
                     help="activations of the timed chain (f32: the split-operand tensor-core path)")
+    ap.add_argument("--learned-seconds", type=float, default=25.0,
+                    help="training budget of the learned-network leg (0 skips it)")
     ap.add_argument("--transform-vox", type=int, default=1 << 20,
                     help="voxels of the stand-alone transform leg (one channel, 3 x 90 directions)")
     return ap.parse_args()
@@ -262,6 +264,51 @@ def run_fp32_leg(ch, cfg, dirs, bvals, idx, steps, tensor_cores):
         L.set_tensor_cores(True)
     torch.cuda.empty_cache()
     return out
+
+
+def run_learned_leg(seconds=25.0, batch=8192, n_train=2_000_000, n_test=262_144, subjects=2, max_steps=20000):
+    """The learned part, time-bounded: the 4-LSC network at its trained widths (64 channels,
+    3 x 90 targets from 30 b=1000 inputs, 4 x 12 kernels, BF16) trained with the library's
+    kernels at batch 8,192 for about `seconds` on seeded fibre-model voxels (a checkpoint
+    written at the end); held-out voxels against the SH least-squares fallback; then
+    whole-volume inference of `subjects` synthetic 145 x 174 x 145 subjects (about 900,000
+    mask voxels each, per-subject perturbed tables, b0 division fused into the gathered
+    Signal2SH) with the weights of that checkpoint, against the noise-free signal."""
+    import tempfile
+    import torch
+    from paper_1808_01517_gb300 import net as N
+    from paper_1808_01517_gb300 import volume as VOL
+    cfg = N.NetConfig()
+    dirs, bvals, sel = N.tables(cfg)
+    tr = N.make_data(cfg, n_train, seed=cfg.seed)
+    te = N.make_data(cfg, n_test, seed=cfg.seed + 1)
+    # steps that fit the time budget, from a short run of a throwaway network
+    probe = N.SphericalNet(cfg, dirs[sel], dirs, bvals).cuda()
+    N.train(probe, tr, 10, batch, seed=2)
+    t_probe = N.train(probe, tr, 30, batch, seed=3).seconds / 30
+    del probe
+    steps = int(max(100, min(max_steps, seconds / max(t_probe, 1e-6))))
+    net = N.SphericalNet(cfg, dirs[sel], dirs, bvals).cuda()
+    fb = N.Fallback(cfg, dirs[sel], dirs, bvals)
+    with tempfile.TemporaryDirectory() as tmp:
+        ck_path = os.path.join(tmp, "net.pt")
+        log = N.train(net, tr, steps, batch, checkpoint=ck_path, checkpoint_every=steps)
+        held = N.evaluate(net, fb, te)
+        state = torch.load(ck_path, map_location="cuda", weights_only=True)["net"]
+    del net, tr, te
+    torch.cuda.empty_cache()
+    subs = [VOL.Subject(i, cfg, state) for i in range(subjects)]
+    outs, secs, vox = VOL.run(subs)
+    acc = VOL.evaluate(subs, outs)
+    del subs, outs
+    torch.cuda.empty_cache()
+    return {"train": {"steps": steps, "batch": batch, "seconds": log.seconds,
+                      "train_voxels_per_s": log.steps * batch / max(log.seconds, 1e-9),
+                      "loss_first_last": [log.losses[0], log.losses[-1]], "train_voxels": n_train,
+                      "device_error_checks": log.device_error_checks},
+            "heldout": held,
+            "volume": {"subjects": subjects, "voxels": vox, "seconds": secs, "voxels_per_s": vox / secs,
+                       "weights": "the checkpoint written by this leg's training", **acc}}
 
 
 def run_chain_leg(cfg, dirs, bvals, steps=10, warm=3):
@@ -541,6 +588,9 @@ def main():
         extras["transforms"] = tr
         # ---- FP64 table build on the host (once per gradient table) ----
         extras["tables"] = guarded("tables", time_tables, cfg, dirs, bvals)
+        # ---- the learned part: short training, held-out accuracy, volume inference ----
+        if args.learned_seconds > 0:
+            extras["learned"] = guarded("learned", run_learned_leg, args.learned_seconds)
 
         # ---- oracle on the host cores ----
         def cpu_leg():
@@ -572,6 +622,7 @@ def main():
         line["mixed_orders_all_shells"] = extras.get("mixed_orders_all_shells")
         line["resampling_free"] = extras.get("resampling_free")
         line["tables"] = extras.get("tables")
+        line["learned"] = extras.get("learned")
         line["cpu_baseline_single_thread"] = extras.get("cpu_baseline_single_thread")
         line["path"] = {"tensor_cores": "required in the timed region", "cuda_core_kernels": cuda_core_kernels}
         line["summary"] = tail_summary(line)  # last, so that a truncated tail of the line still shows it
@@ -594,6 +645,12 @@ def tail_summary(line: dict) -> dict:
            "gemm_frac": g(line, "roofline", "frac"), "step_frac": g(line, "roofline", "step_frac_of_tensor_peak"),
            "fp32_vps": g(line, "fp32", "value"), "fp32_err": [g(line, "fp32", "err_vs_oracle", "s_out"),
                                                               g(line, "fp32", "err_vs_oracle", "ds_in")]}
+    lr = line.get("learned") or {}
+    if isinstance(lr.get("heldout"), dict):
+        out["net_vs_fallback"] = [g(lr, "heldout", "rel_l2_net"), g(lr, "heldout", "rel_l2_fallback")]
+    if isinstance(lr.get("volume"), dict):
+        out["volume"] = [g(lr, "volume", "voxels_per_s"), g(lr, "volume", "rel_l2_net"),
+                         g(lr, "volume", "rel_l2_fallback")]
     tr = line.get("transforms") or {}
     for k in ("signal2sh_f32", "sh2signal_f32", "signal2sh_bf16_in", "sh2signal_bf16_in"):
         if isinstance(tr.get(k), dict):

@@ -45,9 +45,12 @@ def test_bench_tail_summary_is_short_and_complete():
             "roofline": {"frac": 0.8312345, "step_frac_of_tensor_peak": 0.61},
             "fp32": {"value": 2.1e6, "err_vs_oracle": {"s_out": 1.3e-6, "ds_in": 1.1e-6}},
             "transforms": {k: dict(leg) for k in ("signal2sh_f32", "sh2signal_f32", "signal2sh_bf16_in",
-                                                   "sh2signal_bf16_in")}}
+                                                   "sh2signal_bf16_in")},
+            "learned": {"heldout": {"rel_l2_net": 0.0912345, "rel_l2_fallback": 0.4987654},
+                        "volume": {"voxels_per_s": 5.0812345e6, "rel_l2_net": 0.0956789, "rel_l2_fallback": 0.51234}}}
     s = bench.tail_summary(line)
     assert s["bf16_vps"] == 13000000.0 and s["gemm_frac"] == 0.8312 and s["fp32_err"] == [1.3e-6, 1.1e-6]
     assert s["signal2sh_f32"] == [0.6123, 1.235e-7]
+    assert s["net_vs_fallback"] == [0.09123, 0.4988] and s["volume"] == [5081000.0, 0.09568, 0.5123]
     assert len(json.dumps(s)) < 600
     assert bench.tail_summary({"value": 1.0})["fp32_vps"] is None  # a missing leg reads as null
