@@ -245,7 +245,7 @@ def run_fp32_leg(ch, cfg, dirs, bvals, idx, steps, tensor_cores):
         ch32.b.copy_(ch.b)
         ch32.step()
         torch.cuda.synchronize()
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(steps)]
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(ch32.calls) + 1)] for _ in range(steps)]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for k in range(steps):
@@ -254,7 +254,7 @@ def run_fp32_leg(ch, cfg, dirs, bvals, idx, steps, tensor_cores):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         per_call = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(steps)]))
-                    for i, name in enumerate(Chain.CALLS)}
+                    for i, name in enumerate(ch32.calls)}
         out = {"value": cfg.n_vox / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
                "gemms": "tensor cores (required), three-part BF16 splits, six part products, FP32 accumulation"
                if tensor_cores else "CUDA cores, FP32 FMA", "per_call_ms": per_call,
@@ -311,17 +311,18 @@ def run_learned_leg(seconds=25.0, batch=8192, n_train=2_000_000, n_test=262_144,
                        "weights": "the checkpoint written by this leg's training", **acc}}
 
 
-def run_chain_leg(cfg, dirs, bvals, steps=10, warm=3):
+def run_chain_leg(cfg, dirs, bvals, steps=10, warm=3, fused=True):
     """Another chain configuration at full size (BF16): voxels/s, per-call times and
-    error on sampled voxels against the FP64 oracle."""
+    error on sampled voxels against the FP64 oracle.  fused=False: the LSC forward and
+    SH2Signal as two calls (c_out written and read back)."""
     import torch
     from paper_1808_01517_gb300 import synth
     from paper_1808_01517_gb300.chain import Chain
-    ch = Chain(cfg, dirs, bvals, torch.bfloat16)
+    ch = Chain(cfg, dirs, bvals, torch.bfloat16, fused=fused)
     ch.set_inputs(*chain_inputs(cfg, dirs, bvals, torch.bfloat16))
     for _ in range(warm):
         ch.step()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(ch.calls) + 1)] for _ in range(steps)]
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -331,10 +332,11 @@ def run_chain_leg(cfg, dirs, bvals, steps=10, warm=3):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     per_call = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(steps)]))
-                for i, name in enumerate(Chain.CALLS)}
+                for i, name in enumerate(ch.calls)}
     fl = ch.flops()
     idx = synth.voxel_subset(cfg.n_vox, 32, seed=cfg.seed + 97)
-    out = {"workload": cfg.name(), "value": cfg.n_vox / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+    out = {"workload": cfg.name(), "fused_lsc_sh2signal": ch.fused, "value": cfg.n_vox / (ms * 1e-3), "unit": UNIT,
+           "ms_per_step": ms,
            "steps": steps, "step_tflops": sum(fl.values()) / (ms * 1e-3) / 1e12,
            "lsc_forward_tflops": fl["lsc_forward"] / (per_call["lsc_forward"] * 1e-3) / 1e12,
            "per_call_ms": per_call, "err_vs_oracle": sampled_errors(ch, cfg, dirs, bvals, idx)}
@@ -481,7 +483,7 @@ def main():
 
     # ---- timed region ----
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(ch.calls) + 1)] for _ in range(K)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -506,9 +508,9 @@ def main():
     ms = reduce_max_ms(t_start.elapsed_time(t_stop) / K, dist, "cuda")
     value = job_throughput(V, world, ms)
     per_call = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]))
-                for i, name in enumerate(Chain.CALLS)}
+                for i, name in enumerate(ch.calls)}
     # each step alone, from the event before its first call to the one after its last
-    step_ms = [ev[k][0].elapsed_time(ev[k][len(Chain.CALLS)]) for k in range(K)]
+    step_ms = [ev[k][0].elapsed_time(ev[k][len(ch.calls)]) for k in range(K)]
     st, code = L.device_error(torch.cuda.current_stream().cuda_stream)
     if st != L.OK:
         raise RuntimeError(f"device error word set: {code:#x}")
@@ -575,6 +577,8 @@ def main():
                                             args.fp32_steps, False)
         # ---- end to end through host buffers ----
         extras["e2e"] = guarded("e2e", run_e2e, ch, args.e2e_steps)
+        # ---- the same step with the LSC forward and SH2Signal as two calls ----
+        extras["unfused"] = guarded("unfused", run_chain_leg, cfg, dirs, bvals, fused=False)
         # ---- mixed SH orders (4 -> 8) with every input shell mixed into every output shell ----
         from dataclasses import replace
         extras["mixed_orders_all_shells"] = guarded("mixed_orders_all_shells", run_chain_leg,
@@ -606,7 +610,8 @@ def main():
                 "warmup": max(3, args.warmup), "ms_per_step": ms,
                 "ms_per_step_median": float(np.median(step_ms)), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-                "config": {"workload": cfg.name(), "n_vox": V, "shells": list(cfg.dirs_per_shell),
+                "config": {"workload": cfg.name(), "fused_lsc_sh2signal": ch.fused, "n_vox": V,
+                           "shells": list(cfg.dirs_per_shell),
                            "sh_order": cfg.order, "c_in": cfg.c_in, "c_out": cfg.c_out, "kernel_points": ch.geom.K,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "kernels": kernels, "per_call": per_call_roof, "clocks": clk,
@@ -619,6 +624,7 @@ def main():
         line["fp32_cuda_cores"] = extras.get("fp32_cuda_cores")
         line["err_vs_oracle_bf16"] = extras.get("err_vs_oracle_bf16")
         line["transforms"] = extras.get("transforms")
+        line["unfused"] = extras.get("unfused")
         line["mixed_orders_all_shells"] = extras.get("mixed_orders_all_shells")
         line["resampling_free"] = extras.get("resampling_free")
         line["tables"] = extras.get("tables")
@@ -640,7 +646,8 @@ def tail_summary(line: dict) -> dict:
                 return None
             d = d[k]
         return float(f"{d:.4g}") if isinstance(d, float) else d
-    out = {"bf16_vps": g(line, "value"), "bf16_err": [g(line, "err_vs_oracle_bf16", "s_out"),
+    out = {"bf16_vps": g(line, "value"), "unfused_vps": g(line, "unfused", "value"),
+           "bf16_err": [g(line, "err_vs_oracle_bf16", "s_out"),
                                                       g(line, "err_vs_oracle_bf16", "ds_in")],
            "gemm_frac": g(line, "roofline", "frac"), "step_frac": g(line, "roofline", "step_frac_of_tensor_peak"),
            "fp32_vps": g(line, "fp32", "value"), "fp32_err": [g(line, "fp32", "err_vs_oracle", "s_out"),

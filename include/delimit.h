@@ -298,6 +298,32 @@ delimit_status delimit_lsc_forward(const delimit_lsc_geometry* geom, const void*
                                    int64_t ld_in, int64_t ld_out, delimit_dtype act_t, unsigned flags,
                                    void* workspace, size_t ws_bytes, void* stream);
 
+/* The LSC forward followed by SH2Signal on the output basis' directions, in one kernel
+ * (Sec. 2.3: the paper's LSC example pipes SH -> LSC -> SH2Signal; Sec. 2.2 for
+ * SH2Signal):
+ *   sig_out[(s,co,i), v] = sum_a B_s[i][a] c_out[(s,co,a), v],   c_out as delimit_lsc_forward,
+ * with B_s the SH basis of output shell s at its own directions (the geometry's output
+ * basis) and c_out rounded to BF16 where the unfused pair stores it.  c_out is never
+ * written to memory.
+ *   sig_out  device, signal rows (s, co, i) of the output basis (S_out shells, c_out
+ *            channels, m_s directions each) x n_vox, row stride ld_sig (16-byte rule)
+ *   other arguments as delimit_lsc_forward (workspace: delimit_lsc_workspace_size(..., 0);
+ *   DELIMIT_LSC_OPERATOR_READY likewise)
+ * Runs on the tcgen05 tensor cores only: BF16 activations, c_out a multiple of 4, at most
+ * 48 output coefficients (order 8), 96 directions per output shell and 4 output shells,
+ * c_in * N_in a multiple of 8.  Other requests return DELIMIT_ERR_UNSUPPORTED with the
+ * reason (check first with delimit_lsc_forward_sh2signal_supported) and callers run
+ * delimit_lsc_forward + delimit_sh2signal instead.  Errors otherwise as
+ * delimit_lsc_forward. */
+delimit_status delimit_lsc_forward_sh2signal(const delimit_lsc_geometry* geom, const void* sh_in, const float* w,
+                                             const float* b, void* sig_out, int64_t n_vox, int c_in, int c_out,
+                                             int64_t ld_in, int64_t ld_sig, delimit_dtype act_t, unsigned flags,
+                                             void* workspace, size_t ws_bytes, void* stream);
+/* OK when delimit_lsc_forward_sh2signal takes these sizes on this device, UNSUPPORTED
+ * (reason in delimit_last_error) when not, INVALID_ARG for invalid sizes. */
+delimit_status delimit_lsc_forward_sh2signal_supported(const delimit_lsc_geometry* geom, int64_t n_vox, int c_in,
+                                                       int c_out, delimit_dtype act_t);
+
 /* LSC backward for upstream gradient d_out (SH rows of the output):
  *   d_in  = adjoint of the forward in sh_in (same layout as sh_in), or NULL
  *   dw    = float32 [c_out, S_out, c_in, S_in, K] (zero outside the window), or NULL
@@ -411,7 +437,8 @@ uint64_t delimit_cuda_core_fallbacks(void);
  * time}, ...} into buf (truncated to cap - 1 characters); it returns the full
  * length.  Names: signal2sh_tc, sh2signal_tc, signal2sh_bwd_tc,
  * sh2signal_bwd_tc (the _f32 suffix for FP32 input), transform_simt, lsc_build_w, lsc_fwd_gemm, lsc_dgrad_gemm,
- * lsc_wgrad_gemm (the _f32 suffix for split FP32 operands), lsc_rowsum (FP32 and
+ * lsc_wgrad_gemm (the _f32 suffix for split FP32 operands), lsc_fwd_sh2signal (the
+ * fused LSC forward + SH2Signal), lsc_rowsum (FP32 and
  * single-CTA paths), split_bf16x3, lsc_reduce_dw, lsc_gemm_simt, lsc_wgrad_simt.
  * No counterpart in the paper. */
 delimit_status delimit_trace_enable(int enable);

@@ -71,6 +71,9 @@ SIGNATURES = {
                                       _vp, C.c_size_t, _vp]),
     "delimit_lsc_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64,
                                        C.c_int, C.c_uint, _vp, C.c_size_t, _vp]),
+    "delimit_lsc_forward_sh2signal": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, C.c_int, C.c_int, _i64, _i64,
+                                                C.c_int, C.c_uint, _vp, C.c_size_t, _vp]),
+    "delimit_lsc_forward_sh2signal_supported": (C.c_int, [_vp, _i64, C.c_int, C.c_int, C.c_int]),
     "delimit_leaky_relu": (C.c_int, [_vp, _vp, _i64, _i64, _i64, _i64, C.c_float, C.c_int, _vp]),
     "delimit_leaky_relu_backward": (C.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, C.c_float, C.c_int, _vp]),
     "delimit_mask_compact_workspace_size": (C.c_size_t, [_i64]),

@@ -50,8 +50,11 @@ class Chain:
     """Preallocated buffers + handles for one configuration and activation dtype."""
 
     CALLS = ("signal2sh", "lsc_forward", "sh2signal", "sh2signal_backward", "lsc_backward", "signal2sh_backward")
+    # with the LSC forward and SH2Signal fused into one kernel (BF16, where the kernel takes the sizes)
+    CALLS_FUSED = ("signal2sh", "lsc_forward_sh2signal", "sh2signal_backward", "lsc_backward", "signal2sh_backward")
 
-    def __init__(self, cfg: ChainConfig, dirs: np.ndarray, bvals: np.ndarray, dtype=torch.bfloat16, device="cuda"):
+    def __init__(self, cfg: ChainConfig, dirs: np.ndarray, bvals: np.ndarray, dtype=torch.bfloat16, device="cuda",
+                 fused: bool = True):
         self.cfg, self.dtype = cfg, dtype
         self.code = L.BF16 if dtype == torch.bfloat16 else L.F32
         self.basis = L.SHBasis(dirs, bvals, cfg.order, cfg.lam)  # output side (LSC projection, SH2Signal)
@@ -76,6 +79,10 @@ class Chain:
         self._ws = torch.empty(max(self.ws_f, self.ws_b) + 256, dtype=torch.uint8, device=device)
         self.ws = (self._ws.data_ptr() + 255) // 256 * 256
         self.lib = L.get()
+        # fused LSC forward + SH2Signal when asked for and the kernel takes the sizes (c_out is
+        # then never written: c_out_buf stays unused)
+        self.fused = bool(fused) and layers.lsc_forward_sh2signal_supported(self.geom, V, ci, co, dtype)
+        self.calls = self.CALLS_FUSED if self.fused else self.CALLS
 
     @staticmethod
     def row_counts(cfg: ChainConfig, basis, basis_in) -> dict:
@@ -92,8 +99,8 @@ class Chain:
         self.b.copy_(b)
 
     def step(self, stream: int | None = None, events=None):
-        """One forward + backward pass.  ``events``: optional list of 7 CUDA events
-        recorded between the six calls (per-call timing on the launch stream)."""
+        """One forward + backward pass.  ``events``: optional list of len(self.calls) + 1 CUDA
+        events recorded between the calls (per-call timing on the launch stream)."""
         lib, cfg, V = self.lib, self.cfg, self.cfg.n_vox
         st = torch.cuda.current_stream().cuda_stream if stream is None else stream
         bh, gh, t, ci, co, ws = self.basis.handle, self.geom.handle, self.code, cfg.c_in, cfg.c_out, self.ws
@@ -102,28 +109,41 @@ class Chain:
         rec(0)
         L.check(lib.delimit_signal2sh(bih, self.s_in.data_ptr(), self.c_in_buf.data_ptr(), V, ci, self.s_in.stride(0),
                                       self.c_in_buf.stride(0), t, t, st), "delimit_signal2sh")
-        rec(1)
-        L.check(lib.delimit_lsc_forward(gh, self.c_in_buf.data_ptr(), self.w.data_ptr(), self.b.data_ptr(),
-                                        self.c_out_buf.data_ptr(), V, ci, co, self.c_in_buf.stride(0),
-                                        self.c_out_buf.stride(0), t, 0, ws, self.ws_b, st), "delimit_lsc_forward")
-        rec(2)
-        L.check(lib.delimit_sh2signal(bh, self.c_out_buf.data_ptr(), self.s_out.data_ptr(), V, co,
-                                      self.c_out_buf.stride(0), self.s_out.stride(0), t, t, st), "delimit_sh2signal")
-        rec(3)
+        n = 1
+        rec(n)
+        if self.fused:
+            L.check(lib.delimit_lsc_forward_sh2signal(gh, self.c_in_buf.data_ptr(), self.w.data_ptr(),
+                                                      self.b.data_ptr(), self.s_out.data_ptr(), V, ci, co,
+                                                      self.c_in_buf.stride(0), self.s_out.stride(0), t, 0, ws,
+                                                      self.ws_b, st), "delimit_lsc_forward_sh2signal")
+        else:
+            L.check(lib.delimit_lsc_forward(gh, self.c_in_buf.data_ptr(), self.w.data_ptr(), self.b.data_ptr(),
+                                            self.c_out_buf.data_ptr(), V, ci, co, self.c_in_buf.stride(0),
+                                            self.c_out_buf.stride(0), t, 0, ws, self.ws_b, st), "delimit_lsc_forward")
+            n += 1
+            rec(n)
+            L.check(lib.delimit_sh2signal(bh, self.c_out_buf.data_ptr(), self.s_out.data_ptr(), V, co,
+                                          self.c_out_buf.stride(0), self.s_out.stride(0), t, t, st),
+                    "delimit_sh2signal")
+        n += 1
+        rec(n)
         L.check(lib.delimit_sh2signal_backward(bh, self.ds_out.data_ptr(), self.dc_out.data_ptr(), V, co,
                                                self.ds_out.stride(0), self.dc_out.stride(0), t, t, st),
                 "delimit_sh2signal_backward")
-        rec(4)
+        n += 1
+        rec(n)
         L.check(lib.delimit_lsc_backward(gh, self.c_in_buf.data_ptr(), self.w.data_ptr(), self.dc_out.data_ptr(),
                                          self.dc_in.data_ptr(), self.dw.data_ptr(), self.db.data_ptr(), V, ci, co,
                                          self.c_in_buf.stride(0), self.dc_out.stride(0), t, L.OPERATOR_READY, ws,
                                          self.ws_b, st),
                 "delimit_lsc_backward")
-        rec(5)
+        n += 1
+        rec(n)
         L.check(lib.delimit_signal2sh_backward(bih, self.dc_in.data_ptr(), self.ds_in.data_ptr(), V, ci,
                                                self.dc_in.stride(0), self.ds_in.stride(0), t, t, st),
                 "delimit_signal2sh_backward")
-        rec(6)
+        n += 1
+        rec(n)
 
     # algorithmic work per step (used for roofline figures)
     def _pairs(self) -> int:
@@ -131,7 +151,8 @@ class Chain:
         return int(sum(abs(s - p) <= 1 if w == "adjacent" else (s == p if w == "same" else True)
                        for s in range(S) for p in range(S)))
 
-    def flops(self) -> dict:
+    def flops(self, per_call: bool = True) -> dict:
+        """Algorithmic FLOPs per call (per_call=False: the six steps of the unfused chain)."""
         cfg, b = self.cfg, self.basis
         V, N, N_in, ci, co, K = cfg.n_vox, b.n_coef, self.basis_in.n_coef, cfg.c_in, cfg.c_out, self.geom.K
         pairs = self._pairs()
@@ -139,8 +160,11 @@ class Chain:
         build_w = 2.0 * pairs * co * ci * N * N_in * K
         s2sh = 2.0 * ci * b.n_dirs * N_in * V
         sh2s = 2.0 * co * b.n_dirs * N * V
-        return dict(signal2sh=s2sh, lsc_forward=lsc_gemm + build_w, sh2signal=sh2s, sh2signal_backward=sh2s,
-                    lsc_backward=2 * lsc_gemm + build_w + 2.0 * pairs * co * ci * N * N * K, signal2sh_backward=s2sh)
+        out = dict(signal2sh=s2sh, lsc_forward=lsc_gemm + build_w, sh2signal=sh2s, sh2signal_backward=sh2s,
+                   lsc_backward=2 * lsc_gemm + build_w + 2.0 * pairs * co * ci * N * N * K, signal2sh_backward=s2sh)
+        if self.fused and per_call:
+            out["lsc_forward_sh2signal"] = out.pop("lsc_forward") + out.pop("sh2signal")
+        return out
 
     def kernel_work(self) -> dict:
         """Algorithmic work per launch of each traced kernel group: (flops, compulsory HBM bytes)."""
@@ -152,8 +176,8 @@ class Chain:
         gemm = 2.0 * pairs * (co * N) * (ci * N_in) * V
         build = 2.0 * pairs * co * ci * N * N_in * K
         wbytes = 2.0 * e * r["c_out"] * r["c_in"]
-        fl = self.flops()
-        by = self.bytes()
+        fl = self.flops(per_call=False)
+        by = self.bytes(per_call=False)
         out = {
             "lsc_fwd_gemm": (gemm, e * V * (r["c_in"] + r["c_out"])),
             "lsc_dgrad_gemm": (gemm, e * V * (r["c_out"] + r["c_in"])),
@@ -166,6 +190,8 @@ class Chain:
             "sh2signal_bwd_tc": (fl["sh2signal_backward"], by["sh2signal_backward"]),
             "signal2sh_bwd_tc": (fl["signal2sh_backward"], by["signal2sh_backward"]),
             "split_bf16x3": (0.0, 0.0),
+            # fused LSC forward + SH2Signal: both products, the LSC input read and the signal written
+            "lsc_fwd_sh2signal": (gemm + 2.0 * co * b.n_dirs * N * V, e * V * (r["c_in"] + r["s_out"])),
         }
         # FP32 activations: the same algorithmic work through the split-operand kernels
         for k in ("lsc_fwd_gemm", "lsc_dgrad_gemm", "lsc_wgrad_gemm", "signal2sh_tc", "sh2signal_tc",
@@ -173,14 +199,19 @@ class Chain:
             out[k + "_f32"] = out[k]
         return out
 
-    def bytes(self) -> dict:
-        """Compulsory HBM bytes per call (activations read + written once)."""
+    def bytes(self, per_call: bool = True) -> dict:
+        """Compulsory HBM bytes per call (activations read + written once; per_call=False: the
+        six steps of the unfused chain)."""
         e = 2 if self.dtype == torch.bfloat16 else 4
         V, r = self.cfg.n_vox, self.rows
-        return dict(signal2sh=e * V * (r["s_in"] + r["c_in"]), lsc_forward=e * V * (r["c_in"] + r["c_out"]),
-                    sh2signal=e * V * (r["c_out"] + r["s_out"]), sh2signal_backward=e * V * (r["s_out"] + r["c_out"]),
-                    lsc_backward=e * V * (r["c_out"] + 2 * r["c_in"]),
-                    signal2sh_backward=e * V * (r["c_in"] + r["s_in"]))
+        out = dict(signal2sh=e * V * (r["s_in"] + r["c_in"]), lsc_forward=e * V * (r["c_in"] + r["c_out"]),
+                   sh2signal=e * V * (r["c_out"] + r["s_out"]), sh2signal_backward=e * V * (r["s_out"] + r["c_out"]),
+                   lsc_backward=e * V * (r["c_out"] + 2 * r["c_in"]),
+                   signal2sh_backward=e * V * (r["c_in"] + r["s_in"]))
+        if self.fused and per_call:
+            out.pop("lsc_forward"), out.pop("sh2signal")
+            out["lsc_forward_sh2signal"] = e * V * (r["c_in"] + r["s_out"])
+        return out
 
 
 class HostPipeline:

@@ -115,6 +115,7 @@ struct delimit_lsc_geometry {
   const float* d_q = nullptr;  // [S_out][N_out]
   int* err_word = nullptr;
   LscDims dims_template;  // without channel counts
+  FusedTables fused;      // B_s^T of the output basis for the LSC forward with SH2Signal fused
 };
 
 static std::vector<double> transpose(const std::vector<double>& a, int rows, int cols) {
@@ -508,6 +509,12 @@ delimit_status delimit_lsc_geometry_create(const delimit_sh_basis* ob, int order
     g->d_M = g->d_mem + om;
     g->d_Mt = g->d_mem + omt;
     g->d_q = g->d_mem + oqq;
+    std::string ferr;
+    if (fused_tables_create(ob->h, g->fused, ferr) != cudaSuccess) {
+      cudaFree(g->d_mem);
+      delete g;
+      return fail(DELIMIT_ERR_OOM, "fused SH2Signal operator: " + ferr);
+    }
     g->on_device = true;
   }
   *out = g;
@@ -521,6 +528,7 @@ delimit_status delimit_lsc_geometry_destroy(delimit_lsc_geometry* g) {
     cudaGetDevice(&cur);
     if (cur != g->device) cudaSetDevice(g->device);
     cudaFree(g->d_mem);
+    fused_tables_destroy(g->fused);
     if (cur != g->device && cur >= 0) cudaSetDevice(cur);
   }
   delete g;
@@ -810,6 +818,49 @@ delimit_status delimit_lsc_forward(const delimit_lsc_geometry* g, const void* sh
   a.n_vox = n_vox;
   e = launch_row_gemm_simt(a, d.s_out, per_out, int(act_t), cs);
   if (e != cudaSuccess) return cuda_fail(e, "LSC forward launch");
+  return DELIMIT_OK;
+}
+
+delimit_status delimit_lsc_forward_sh2signal_supported(const delimit_lsc_geometry* g, int64_t n_vox, int c_in,
+                                                       int c_out, delimit_dtype act_t) {
+  LscPlan p;
+  if (!g) return fail(DELIMIT_ERR_INVALID_ARG, "geometry is NULL");
+  if (!g->on_device) return fail(DELIMIT_ERR_INVALID_ARG, "geometry was created with DELIMIT_HOST_ONLY");
+  if (!make_plan(g, n_vox, c_in, c_out, act_t, p))
+    return fail(DELIMIT_ERR_INVALID_ARG, "need n_vox >= 0, 1 <= c_in, c_out <= 4096 and a valid dtype");
+  if (act_t != DELIMIT_BF16) return fail(DELIMIT_ERR_UNSUPPORTED, "the fused LSC + SH2Signal takes BF16 activations");
+  if (const char* why = tc_lsc_fused_unsupported(p.d, g->fused, std::max<int64_t>(n_vox, 1)))
+    return fail(DELIMIT_ERR_UNSUPPORTED, std::string("fused LSC + SH2Signal: ") + why);
+  return DELIMIT_OK;
+}
+
+delimit_status delimit_lsc_forward_sh2signal(const delimit_lsc_geometry* g, const void* sh_in, const float* w,
+                                             const float* b, void* sig_out, int64_t n_vox, int c_in, int c_out,
+                                             int64_t ld_in, int64_t ld_sig, delimit_dtype act_t, unsigned flags,
+                                             void* ws, size_t ws_bytes, void* stream) {
+  LscPlan p;
+  delimit_status st = lsc_common_checks(g, n_vox, c_in, c_out, act_t, ws, ws_bytes, false, p);
+  if (st != DELIMIT_OK) return st;
+  if (!w) return fail(DELIMIT_ERR_INVALID_ARG, "w is NULL");
+  if (n_vox == 0) return DELIMIT_OK;
+  if ((st = delimit_lsc_forward_sh2signal_supported(g, n_vox, c_in, c_out, act_t)) != DELIMIT_OK) return st;
+  if ((st = check_act(sh_in, ld_in, n_vox, act_t, "sh_in")) != DELIMIT_OK) return st;
+  if ((st = check_act(sig_out, ld_sig, n_vox, act_t, "sig_out")) != DELIMIT_OK) return st;
+  const LscDims& d = p.d;
+  if (!tc_gemm_supported(d, n_vox, ld_in, ld_sig))
+    return fail(DELIMIT_ERR_UNSUPPORTED, "fused LSC + SH2Signal: the tensor-core GEMMs do not take these sizes");
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  void* W = base + p.off_W;
+  void* Wt = base + p.off_Wt;
+  float* bias = reinterpret_cast<float*>(base + p.off_bias);
+  cudaError_t e = cudaSuccess;
+  if (!(flags & DELIMIT_LSC_OPERATOR_READY)) {
+    e = build_operator(d, g, p, w, b, W, Wt, bias, act_t, true, base, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "LSC operator build launch");
+  }
+  e = tc_lsc_forward_sh2signal(d, g->fused, sh_in, W, bias, sig_out, n_vox, ld_in, ld_sig, g->err_word, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "fused LSC + SH2Signal launch");
   return DELIMIT_OK;
 }
 

@@ -82,6 +82,23 @@ cudaError_t transpose_bf16(const void* in, int64_t rows, int64_t cols, int64_t l
 cudaError_t split_bf16x3(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* out, int64_t ldo,
                          int64_t part_stride, cudaStream_t st);
 
+// The LSC forward with SH2Signal in its epilogue (tc_fused.cu): B_s^T of the output basis'
+// shells as the K-major BF16 operator [S][96 directions][64 coefficients], zero-padded.
+struct FusedTables {
+  void* d_b2 = nullptr;
+  int shells = 0, m[4] = {}, dir_off[4] = {};
+  bool ok = false;  // false: the basis has no fused form (more than 4 shells, 96 directions or 48 coefficients)
+};
+cudaError_t fused_tables_create(const BasisHost& out_basis, FusedTables& f, std::string& err);
+void fused_tables_destroy(FusedTables& f);
+// NULL when the fused kernel takes these sizes, else the reason it does not
+const char* tc_lsc_fused_unsupported(const LscDims& d, const FusedTables& f, int64_t n_vox);
+// S[(s,co,i), v] = sum_a B_s[i][a] bf16(sum_k W[(s,co,a)][k] X[k, v] + bias[(s,co,a)]), BF16 X, W and S;
+// W is the K-major collapsed operator (no per-shell padding), S in the signal row layout
+cudaError_t tc_lsc_forward_sh2signal(const LscDims& d, const FusedTables& f, const void* X, const void* W,
+                                     const float* bias, void* S, int64_t n_vox, int64_t ldx, int64_t lds, int* err,
+                                     cudaStream_t st);
+
 // one CTA waiting on an mbarrier nothing arrives at, through the kernels' bounded wait:
 // after the limit (2 s) the error word gets `code` and the kernel returns
 cudaError_t launch_wait_probe(int* err, int code, cudaStream_t st);

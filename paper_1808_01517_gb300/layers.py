@@ -128,6 +128,31 @@ def lsc_forward(geom: L.LSCGeometry, x: torch.Tensor, w: torch.Tensor, b: torch.
     return out
 
 
+def lsc_forward_sh2signal_supported(geom: L.LSCGeometry, n_vox: int, c_in: int, c_out: int, dtype) -> bool:
+    """Whether the fused LSC forward + SH2Signal kernel takes these sizes (else run
+    lsc_forward and transform("sh2signal", ...) one after the other)."""
+    return L.get().delimit_lsc_forward_sh2signal_supported(geom.handle, n_vox, c_in, c_out, _DT[dtype]) == L.OK
+
+
+def lsc_forward_sh2signal(geom: L.LSCGeometry, x: torch.Tensor, w: torch.Tensor, b: torch.Tensor | None, c_in: int,
+                          c_out: int, out: torch.Tensor | None = None, workspace=None) -> torch.Tensor:
+    """The LSC forward followed by SH2Signal on the geometry's output directions, one kernel:
+    returns signal rows [c_out * total directions, n_vox] (the output SH never leaves the chip)."""
+    x = as_act(x)
+    n_vox = x.shape[1]
+    if out is None:
+        out = empty_act(c_out * geom.out_basis.n_dirs, n_vox, x.dtype, x.device)
+    _, wsp, ws_n = workspace if workspace is not None else lsc_workspace(geom, n_vox, c_in, c_out, x.dtype, False,
+                                                                         x.device)
+    w = w.detach().contiguous().float()
+    bf = b.detach().contiguous().float() if b is not None else None  # lives until after the launch
+    L.check(L.get().delimit_lsc_forward_sh2signal(geom.handle, x.data_ptr(), w.data_ptr(),
+                                                  bf.data_ptr() if bf is not None else None, out.data_ptr(), n_vox,
+                                                  c_in, c_out, x.stride(0), out.stride(0), _code(x), 0, wsp, ws_n,
+                                                  _stream()), "delimit_lsc_forward_sh2signal")
+    return out
+
+
 def lsc_backward(geom: L.LSCGeometry, x: torch.Tensor, w: torch.Tensor, d_out: torch.Tensor, c_in: int, c_out: int,
                  need_input: bool = True, need_weight: bool = True, need_bias: bool = True, workspace=None,
                  operator_ready: bool = False):

@@ -85,9 +85,10 @@ def test_chain_full_size_sampled_vs_oracle(dtype, tol, n_vox):
     4 x 12 kernel) in the launch configuration the benchmark times, at 65,536 voxels and at
     a ragged 65,376: s_out and ds_in of one voxel in every 256-voxel tile and of every voxel
     of the last tile against the FP64 oracle chain, globally and voxel by voxel; the bias
-    gradient (a plain reduction over all voxels) in full.  For BF16, every stored tensor of
-    the step is also checked against the BF16 storage model of its own stage (the same
-    operator, rounded to BF16, applied in FP64 to the BF16 input the kernel read, then
+    gradient (a plain reduction over all voxels) in full.  The BF16 chain runs the fused
+    LSC forward + SH2Signal; it must agree with the unfused chain on the same inputs, whose
+    stored tensors are each checked against the BF16 storage model of their own stage (the
+    same operator, rounded to BF16, applied in FP64 to the BF16 input the kernel read, then
     rounded to BF16): only FP32 accumulation separates the two."""
     from oracle import lsc as olsc
     from oracle import sh as osh
@@ -137,6 +138,21 @@ def test_chain_full_size_sampled_vs_oracle(dtype, tol, n_vox):
     assert rel(ch.db.cpu().numpy(), ref_db) <= tol
     if dtype != torch.bfloat16:
         return
+    # the BF16 chain fuses the LSC forward with SH2Signal (c_out never stored); the unfused
+    # chain on the same inputs gives the same s_out and exposes c_out for the model below
+    assert ch.fused
+    ch2 = Chain(cfg, dirs, bvals, dtype, fused=False)
+    ch2.set_inputs(ch.s_in, ch.ds_out, torch.from_numpy(w).float(), torch.from_numpy(b).float())
+    L.set_tensor_cores(L.TC_REQUIRE)
+    try:
+        ch2.step()
+        torch.cuda.synchronize()
+    finally:
+        L.set_tensor_cores(True)
+    assert float((ch.s_out == ch2.s_out).float().mean()) >= 0.999
+    assert torch.equal(ch.ds_in, ch2.ds_in) and torch.equal(ch.dw, ch2.dw) and torch.equal(ch.db, ch2.db)
+    ch = ch2
+    got_s = rows(ch.s_out, cfg.c_out)
     # BF16 storage model, stage by stage, from the kernels' own BF16 inputs
     r = _bf16
     P = [r(p) for p in ob.P]
