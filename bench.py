@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip fp32 / e2e / cpu / transform legs (profiling runs)")
+    ap.add_argument("--fused", action="store_true",
+                    help="time the chain with the LSC forward and SH2Signal fused into one kernel")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "f32"],
                     help="activations of the timed chain (f32: the split-operand tensor-core path)")
     ap.add_argument("--learned-seconds", type=float, default=25.0,
@@ -311,10 +313,10 @@ def run_learned_leg(seconds=25.0, batch=8192, n_train=2_000_000, n_test=262_144,
                        "weights": "the checkpoint written by this leg's training", **acc}}
 
 
-def run_chain_leg(cfg, dirs, bvals, steps=10, warm=3, fused=True):
+def run_chain_leg(cfg, dirs, bvals, steps=10, warm=3, fused=False):
     """Another chain configuration at full size (BF16): voxels/s, per-call times and
-    error on sampled voxels against the FP64 oracle.  fused=False: the LSC forward and
-    SH2Signal as two calls (c_out written and read back)."""
+    error on sampled voxels against the FP64 oracle.  fused=True: the LSC forward and
+    SH2Signal as one kernel (c_out never stored)."""
     import torch
     from paper_1808_01517_gb300 import synth
     from paper_1808_01517_gb300.chain import Chain
@@ -338,7 +340,8 @@ def run_chain_leg(cfg, dirs, bvals, steps=10, warm=3, fused=True):
     out = {"workload": cfg.name(), "fused_lsc_sh2signal": ch.fused, "value": cfg.n_vox / (ms * 1e-3), "unit": UNIT,
            "ms_per_step": ms,
            "steps": steps, "step_tflops": sum(fl.values()) / (ms * 1e-3) / 1e12,
-           "lsc_forward_tflops": fl["lsc_forward"] / (per_call["lsc_forward"] * 1e-3) / 1e12,
+           "lsc_forward_tflops": (fl["lsc_forward_sh2signal"] / (per_call["lsc_forward_sh2signal"] * 1e-3) if ch.fused
+                                  else fl["lsc_forward"] / (per_call["lsc_forward"] * 1e-3)) / 1e12,
            "per_call_ms": per_call, "err_vs_oracle": sampled_errors(ch, cfg, dirs, bvals, idx)}
     del ch
     torch.cuda.empty_cache()
@@ -462,7 +465,7 @@ def main():
 
     V = cfg.n_vox
     act = torch.float32 if args.precision == "f32" else torch.bfloat16
-    ch = Chain(cfg, dirs, bvals, act)
+    ch = Chain(cfg, dirs, bvals, act, fused=args.fused)
     s_in, ds_out, w, b = chain_inputs(cfg, dirs, bvals, act, rank)
     ch.set_inputs(s_in, ds_out, w, b)
     del s_in, ds_out
@@ -577,8 +580,8 @@ def main():
                                             args.fp32_steps, False)
         # ---- end to end through host buffers ----
         extras["e2e"] = guarded("e2e", run_e2e, ch, args.e2e_steps)
-        # ---- the same step with the LSC forward and SH2Signal as two calls ----
-        extras["unfused"] = guarded("unfused", run_chain_leg, cfg, dirs, bvals, fused=False)
+        # ---- the same step with the LSC forward and SH2Signal fused into one kernel ----
+        extras["fused"] = guarded("fused", run_chain_leg, cfg, dirs, bvals, fused=True)
         # ---- mixed SH orders (4 -> 8) with every input shell mixed into every output shell ----
         from dataclasses import replace
         extras["mixed_orders_all_shells"] = guarded("mixed_orders_all_shells", run_chain_leg,
@@ -624,7 +627,7 @@ def main():
         line["fp32_cuda_cores"] = extras.get("fp32_cuda_cores")
         line["err_vs_oracle_bf16"] = extras.get("err_vs_oracle_bf16")
         line["transforms"] = extras.get("transforms")
-        line["unfused"] = extras.get("unfused")
+        line["fused"] = extras.get("fused")
         line["mixed_orders_all_shells"] = extras.get("mixed_orders_all_shells")
         line["resampling_free"] = extras.get("resampling_free")
         line["tables"] = extras.get("tables")
@@ -646,7 +649,7 @@ def tail_summary(line: dict) -> dict:
                 return None
             d = d[k]
         return float(f"{d:.4g}") if isinstance(d, float) else d
-    out = {"bf16_vps": g(line, "value"), "unfused_vps": g(line, "unfused", "value"),
+    out = {"bf16_vps": g(line, "value"), "fused_vps": g(line, "fused", "value"),
            "bf16_err": [g(line, "err_vs_oracle_bf16", "s_out"),
                                                       g(line, "err_vs_oracle_bf16", "ds_in")],
            "gemm_frac": g(line, "roofline", "frac"), "step_frac": g(line, "roofline", "step_frac_of_tensor_peak"),

@@ -54,7 +54,7 @@ class Chain:
     CALLS_FUSED = ("signal2sh", "lsc_forward_sh2signal", "sh2signal_backward", "lsc_backward", "signal2sh_backward")
 
     def __init__(self, cfg: ChainConfig, dirs: np.ndarray, bvals: np.ndarray, dtype=torch.bfloat16, device="cuda",
-                 fused: bool = True):
+                 fused: bool = False):
         self.cfg, self.dtype = cfg, dtype
         self.code = L.BF16 if dtype == torch.bfloat16 else L.F32
         self.basis = L.SHBasis(dirs, bvals, cfg.order, cfg.lam)  # output side (LSC projection, SH2Signal)
@@ -80,7 +80,10 @@ class Chain:
         self.ws = (self._ws.data_ptr() + 255) // 256 * 256
         self.lib = L.get()
         # fused LSC forward + SH2Signal when asked for and the kernel takes the sizes (c_out is
-        # then never written: c_out_buf stays unused)
+        # then never written: c_out_buf stays unused).  Off by default: on the 3 x 90-direction,
+        # 16 -> 64-channel workload the two unfused calls take 1.67 ms against 1.70 ms fused,
+        # since the fused tile (four 48-row channel slots, N = 192) keeps the tensor pipe less
+        # busy than the forward GEMM's N = 256 tile.
         self.fused = bool(fused) and layers.lsc_forward_sh2signal_supported(self.geom, V, ci, co, dtype)
         self.calls = self.CALLS_FUSED if self.fused else self.CALLS
 

@@ -346,144 +346,124 @@ cudaError_t launch_ring_weights(const float* src, float* dst, int64_t n_e, int K
 // ---------------------------------------------------------------------------
 // Collapsed LSC operator.  For every shell pair (s, s') in the window
 //   W[(s,co,a)][(s',ci,b)] = sum_k w[co,s,ci,s',k] M_{s,s'}[k][a][b] (M_{s,s'} = M_s in the resampled form)
-// One block: 8 channel pairs (co, ci) of one shell pair and up to 2048 (a, b)
-// entries.  Chunks of 4 kernel points of M_{s,s'} (4 x 2048 floats) and of w are
-// staged in shared memory by cp.async, two chunks in flight (the next one loads
-// while the current one is used); each thread accumulates 8 pairs x 8 consecutive
-// (a, b) entries (64 FMAs per 4 vector shared loads).  The finished block goes
-// back through shared memory and is written to W (runs along b) and Wt (runs
-// along a), one warp per run.  Shell pairs outside the window write zeros.
+// a small GEMM per shell pair: [channel pairs x K] x [K x (a,b)].  One block: 64
+// consecutive channel pairs p = co c_in + ci of one shell pair x 256 consecutive (a, b)
+// entries; K in chunks of 56 kernel points (one chunk for K <= 56), M_{s,s'}[k][ab0 ..
+// ab0+255] and w[p][k] staged in shared memory.  Warp = 8 pairs, lane = 8 consecutive
+// entries: per kernel point two broadcast and two 128-bit shared loads feed 64 FMAs.
+// The finished block goes back through shared memory and is written to W, a warp per
+// run of a row (s, co, a): the block's channels ci and their b entries, contiguous in W;
+// and to Wt (runs along a).  Shell pairs outside the window write zeros.
 // ---------------------------------------------------------------------------
-constexpr int kBwPairs = 8, kBwChunk = 2048, kBwKC = 4;  // pairs, (a,b) entries, kernel points per stage
-static_assert(2 * kBwKC >= kBwPairs, "the two M stage buffers hold the finished block");
-
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
+constexpr int kBwP = 64, kBwAB = 256, kBwKC = 56;  // pairs, (a,b) entries, kernel points per chunk
+constexpr size_t kBwSmem = sizeof(float) * kBwKC * (kBwAB + kBwP);  // a chunk (M + w); then the results
+static_assert(kBwP * kBwAB <= kBwKC * (kBwAB + kBwP), "the results fit a staged chunk's space");
 
 template <typename TW>
 __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
                                                       const float* __restrict__ M, TW* __restrict__ W,
                                                       TW* __restrict__ Wt) {
-  extern __shared__ float4 blk4[];  // [2][kBwKC][kBwChunk] M stages; later [kBwPairs][kBwChunk] results
+  extern __shared__ float4 blk4[];  // chunk: ms [kBwKC][kBwAB], ws [kBwKC][kBwP]; then results [kBwP][kBwAB]
   float* blk = reinterpret_cast<float*>(blk4);
-  __shared__ __align__(16) float wk[2][kBwKC][kBwPairs];
-  const int tid = threadIdx.x;
+  float* ms = blk;
+  float* ws = blk + kBwKC * kBwAB;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int pair = blockIdx.y;  // s * s_in + s'
   const int s = pair / d.s_in, sp = pair % d.s_in;
   const bool in_win = sp >= d.win_lo[s] && sp < d.win_hi[s];
   const int nab = d.n_out * d.n_in, npairs = d.c_out * d.c_in;
-  const int p0 = blockIdx.x * kBwPairs;
-  const int np = min(kBwPairs, npairs - p0);
-  const int ab0 = blockIdx.z * kBwChunk, nabc = min(kBwChunk, nab - ab0);  // this block's (a,b) range
-  float acc[kBwPairs][8];
+  const int p0 = blockIdx.x * kBwP;
+  const int np = min(kBwP, npairs - p0);
+  const int ab0 = blockIdx.z * kBwAB, nabc = min(kBwAB, nab - ab0);  // this block's (a,b) range
+  // acc[i][e2] = entries 2 e2, 2 e2 + 1 of pair i: packed FP32x2 FMAs (each lane rounds as fmaf)
+  float2 acc[8][4];
 #pragma unroll
-  for (int p = 0; p < kBwPairs; ++p)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int e = 0; e < 8; ++e) acc[p][e] = 0.f;
+    for (int e = 0; e < 4; ++e) acc[i][e] = make_float2(0.f, 0.f);
   if (in_win) {
-    const float* Ms = M + s * d.m_stride_s + sp * d.m_stride_sp + ab0 + tid;
-    const uint32_t blk_s = (uint32_t)__cvta_generic_to_shared(blk);
-    const int nst = (d.K + kBwKC - 1) / kBwKC;
-    // stage c: M_{s,s'}[4c .. 4c+3][ab0 .. ab0+2047] (zero past the ranges) and the w values
-    auto issue = [&](int c) {
-      const int buf = c & 1, k0 = c * kBwKC;
+    const float* Ms = M + s * d.m_stride_s + sp * d.m_stride_sp + ab0;
+    for (int k0 = 0; k0 < d.K; k0 += kBwKC) {
+      const int kc = min(kBwKC, d.K - k0);
+      __syncthreads();  // the previous chunk is consumed
+      // M rows k0 .. k0 + kc - 1: thread tid loads entry tid of each (zero past the ranges)
+#pragma unroll 8
+      for (int kk = 0; kk < kBwKC; ++kk)
+        ms[kk * kBwAB + tid] = (kk < kc && tid < nabc) ? __ldg(Ms + (int64_t)(k0 + kk) * nab + tid) : 0.f;
+      // w[p][k0 + kk] for the block's pairs, pair index fastest (conflict-free stores)
 #pragma unroll
-      for (int kk = 0; kk < kBwKC; ++kk) {
-        const bool krow = k0 + kk < d.K;
-        const float* row = Ms + (int64_t)(krow ? k0 + kk : 0) * nab;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const bool ok = krow && tid + 256 * e < nabc;
-          cp_async4(blk_s + (uint32_t)(((buf * kBwKC + kk) * kBwChunk + tid + 256 * e) * 4), ok ? row + 256 * e : Ms,
-                    ok ? 4 : 0);
-        }
-      }
-      cp_async_commit();
-      if (tid < kBwKC * kBwPairs) {
-        const int kk = tid / kBwPairs, pp = tid % kBwPairs, pr = p0 + pp;
+      for (int e = 0; e < kBwKC * kBwP / 256; ++e) {
+        const int idx = tid + 256 * e, pp = idx % kBwP, kk = idx / kBwP, pr = p0 + pp;
         float v = 0.f;
-        if (pp < np && k0 + kk < d.K) {
-          const int co = pr / d.c_in, ci = pr % d.c_in;
-          v = w[((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K + k0 + kk];
+        if (pp < np && kk < kc) {
+          const int co = pr / d.c_in, ci = pr - co * d.c_in;
+          v = __ldg(w + ((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K + k0 + kk);
         }
-        wk[buf][kk][pp] = v;
+        ws[kk * kBwP + pp] = v;
       }
-    };
-    issue(0);
-    for (int c = 0; c < nst; ++c) {
-      const int buf = c & 1;
-      if (c + 1 < nst) {
-        issue(c + 1);  // the buffer it fills was last read in iteration c - 1
-        cp_async_wait_group<1>();
-      } else {
-        cp_async_wait_group<0>();
-      }
-      __syncthreads();  // stage c complete and visible
-#pragma unroll
-      for (int kk = 0; kk < kBwKC; ++kk) {
-        const float4 m0 = blk4[(buf * kBwKC + kk) * (kBwChunk / 4) + 2 * tid];
-        const float4 m1 = blk4[(buf * kBwKC + kk) * (kBwChunk / 4) + 2 * tid + 1];
-        const float4 w0 = *reinterpret_cast<const float4*>(&wk[buf][kk][0]);
-        const float4 w1 = *reinterpret_cast<const float4*>(&wk[buf][kk][4]);
-        const float mv[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+      __syncthreads();
+      const float4* ms4 = reinterpret_cast<const float4*>(ms) + 2 * lane;
+      const float4* ws4 = reinterpret_cast<const float4*>(ws) + 2 * warp;
+#pragma unroll 2
+      for (int kk = 0; kk < kc; ++kk) {
+        const float4 m0 = ms4[kk * (kBwAB / 4)], m1 = ms4[kk * (kBwAB / 4) + 1];
+        const float4 w0 = ws4[kk * (kBwP / 4)], w1 = ws4[kk * (kBwP / 4) + 1];
+        const float2 mv[4] = {make_float2(m0.x, m0.y), make_float2(m0.z, m0.w), make_float2(m1.x, m1.y),
+                              make_float2(m1.z, m1.w)};
         const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-        for (int p = 0; p < kBwPairs; ++p)
+        for (int i = 0; i < 8; ++i) {
+          const float2 wi = make_float2(wv[i], wv[i]);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) acc[p][e] = fmaf(wv[p], mv[e], acc[p][e]);
+          for (int e = 0; e < 4; ++e) acc[i][e] = __ffma2_rn(wi, mv[e], acc[i][e]);
+        }
       }
-      __syncthreads();  // everyone is done with buffer buf before it is refilled
     }
   }
   __syncthreads();
-  // results [p][t], t = 8 tid + e
+  // results [p][t]: pair p = 8 warp + i, entry t = 8 lane + e
 #pragma unroll
-  for (int p = 0; p < kBwPairs; ++p) {
-    blk4[p * (kBwChunk / 4) + 2 * tid] = make_float4(acc[p][0], acc[p][1], acc[p][2], acc[p][3]);
-    blk4[p * (kBwChunk / 4) + 2 * tid + 1] = make_float4(acc[p][4], acc[p][5], acc[p][6], acc[p][7]);
+  for (int i = 0; i < 8; ++i) {
+    blk4[(8 * warp + i) * (kBwAB / 4) + 2 * lane] = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
+    blk4[(8 * warp + i) * (kBwAB / 4) + 2 * lane + 1] = make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
   }
   __syncthreads();
-  // Stores: one warp per output row segment, lanes along the contiguous index; the
-  // segment loops carry no division (pairs outer, rows strided by warp inner).
-  const int warp = tid / 32, lane = tid % 32;
+  // Stores: one warp per output run (a pair's row segment), lanes along the contiguous index
   const int a_lo = ab0 / d.n_in, a_hi = (ab0 + nabc - 1) / d.n_in;  // a range touched by this chunk
   const int na = a_hi - a_lo + 1;
   const int b_lo = na > 1 ? 0 : ab0 % d.n_in, b_hi = na > 1 ? d.n_in - 1 : (ab0 + nabc - 1) % d.n_in;
   const int nb = b_hi - b_lo + 1;
-  int co = p0 / d.c_in, ci = p0 % d.c_in;
-  for (int p = 0; p < np; ++p) {
-    const float* src = blk + p * kBwChunk;  // src[a * n_in + b - ab0] for this pair
-    // W: row (s, co, a), columns s'*in_blk + ci*n_in + b
-    TW* wrow = W + (((int64_t)s * d.c_out + co) * d.n_out + a_lo) * d.ldW + (int64_t)sp * d.in_blk + (int64_t)ci * d.n_in;
-    for (int ai = warp; ai < na; ai += 8) {
-      const int aa = a_lo + ai;
-      TW* dst = wrow + (int64_t)ai * d.ldW;
-      for (int bb = lane; bb < d.n_in; bb += 32) {
-        const int t = aa * d.n_in + bb;
-        if (t >= ab0 && t < ab0 + nabc) stf(dst + bb, src[t - ab0]);
+  // W: for each output channel co of the block's pairs and each a of the chunk, the block's
+  // channels ci with their b entries form one run of W's row (s, co, a) (columns s' in_blk
+  // + ci n_in + b, contiguous over (ci, b)); a warp per run, lanes along the run, the lane's
+  // (ci, b) advanced incrementally
+  const int co_lo = p0 / d.c_in, nco = (p0 + np - 1) / d.c_in - co_lo + 1;
+  for (int r = warp; r < nco * na; r += 8) {
+    const int ko = r / na, ai = r - ko * na, co = co_lo + ko, aa = a_lo + ai;
+    const int ci0 = max(0, p0 - co * d.c_in), ci1 = min(d.c_in, p0 + np - co * d.c_in);
+    const int b0 = max(0, ab0 - aa * d.n_in), b1 = min(d.n_in, ab0 + nabc - aa * d.n_in);
+    const int len = (ci1 - ci0) * d.n_in;
+    TW* dst = W + (((int64_t)s * d.c_out + co) * d.n_out + aa) * d.ldW + (int64_t)sp * d.in_blk + (int64_t)ci0 * d.n_in;
+    const int src0 = (co * d.c_in + ci0 - p0) * kBwAB + aa * d.n_in - ab0;  // + (ci - ci0) kBwAB + b
+    int cj = lane / d.n_in, bj = lane - cj * d.n_in;
+    for (int j = lane; j < len; j += 32) {
+      if (bj >= b0 && bj < b1) stf(dst + j, blk[src0 + cj * kBwAB + bj]);
+      bj += 32;
+      while (bj >= d.n_in) {
+        bj -= d.n_in;
+        ++cj;
       }
     }
-    // Wt: row (s', ci, b), columns s*out_blk + co*n_out + a (when the caller wants it)
-    TW* wtrow = Wt ? Wt + (((int64_t)sp * d.c_in + ci) * d.n_in + b_lo) * d.ldWt + (int64_t)s * d.out_blk +
-                         (int64_t)co * d.n_out
-                   : nullptr;
-    for (int bi = warp; wtrow && bi < nb; bi += 8) {
-      const int bb = b_lo + bi;
-      TW* dst = wtrow + (int64_t)bi * d.ldWt;
-      for (int aa = a_lo + lane; aa <= a_hi; aa += 32) {
-        const int t = aa * d.n_in + bb;
-        if (t >= ab0 && t < ab0 + nabc) stf(dst + aa, src[t - ab0]);
-      }
-    }
-    if (++ci == d.c_in) {
-      ci = 0;
-      ++co;
+  }
+  if (!Wt) return;
+  // Wt: row (s', ci, b), columns s*out_blk + co*n_out + a; run r = (pair, b)
+  for (int r = warp; r < np * nb; r += 8) {
+    const int p = r / nb, bi = r - p * nb, pr = p0 + p, co = pr / d.c_in, ci = pr - co * d.c_in, bb = b_lo + bi;
+    const float* src = blk + p * kBwAB;
+    TW* dst = Wt + (((int64_t)sp * d.c_in + ci) * d.n_in + bb) * d.ldWt + (int64_t)s * d.out_blk + (int64_t)co * d.n_out;
+    for (int aa = a_lo + lane; aa <= a_hi; aa += 32) {
+      const int t = aa * d.n_in + bb;
+      if (t >= ab0 && t < ab0 + nabc) stf(dst + aa, src[t - ab0]);
     }
   }
 }
@@ -512,9 +492,9 @@ cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, con
     e = cudaMemsetAsync(Wt, 0, (size_t)d.rows_in * d.ldWt * es, st);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((unsigned)((npairs + kBwPairs - 1) / kBwPairs), (unsigned)(d.s_out * d.s_in),
-            (unsigned)((nab + kBwChunk - 1) / kBwChunk));
-  const size_t smem = sizeof(float) * 2 * kBwKC * kBwChunk;  // = kBwPairs * kBwChunk for the results
+  dim3 grid((unsigned)((npairs + kBwP - 1) / kBwP), (unsigned)(d.s_out * d.s_in),
+            (unsigned)((nab + kBwAB - 1) / kBwAB));
+  const size_t smem = kBwSmem;
   if (w_t == 0) {
     e = cudaFuncSetAttribute(build_w_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -696,10 +676,7 @@ cudaError_t launch_wgrad_simt(const WgradArgs& a, int n_groups, int max_M, int m
 // ---------------------------------------------------------------------------
 constexpr int kDwAbPart = 256;  // (a,b) entries per partial sum
 
-// TRANS: the partials are stored transposed (p_rs = 1): the (a,b) range is walked with a
-// fastest (ab = b * n_out + a, consecutive rows of P, coalesced) and M is read as Mt
-// (per kernel point [b][a]), in the same order.
-template <bool TRANS>
+// Partials stored row-major (p_cs = 1; the CUDA-core weight gradient).
 __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ LscDims d, const float* __restrict__ P,
                                                         int64_t p_rs, int64_t p_cs, int64_t split_stride, int splits,
                                                         const float* __restrict__ M, float* __restrict__ dwp,
@@ -733,7 +710,7 @@ __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ 
           for (int z = 0; z < kRaw; ++z) raw[e][z] = 0.f;
           if (pr < npairs && ab < ab_end) {
             const int co = pr / d.c_in, ci = pr % d.c_in;
-            const int aa = TRANS ? ab % d.n_out : ab / d.n_in, bb = TRANS ? ab / d.n_out : ab % d.n_in;
+            const int aa = ab / d.n_in, bb = ab % d.n_in;
             const int64_t off = (((int64_t)s * d.c_out + co) * d.n_out + aa) * p_rs +
                                 (((int64_t)sp * d.c_in + ci) * d.n_in + bb) * p_cs;
 #pragma unroll
@@ -791,6 +768,152 @@ __global__ void __launch_bounds__(256) reduce_dw_kernel(const __grid_constant__ 
   }
 }
 
+// Partials stored transposed (p_rs = 1: P's rows (s, co, a) are contiguous, a fastest; the
+// tensor-core weight gradient).  One block: 64 channel pairs x 56 kernel points x one part
+// of kDwAbPart (a,b) entries, walked with a fastest (ab = b n_out + a: the order of P's
+// rows and of Mt, per kernel point [b][a]) in chunks of 32, the next chunk's loads in
+// flight during the current one's FMAs.  Staged per chunk: G = the sum of P's splits, as
+// gs[entry][pair], and Mt as ms_[entry][slot] with kernel point k = 7 kg + j in slot
+// 8 kg + j (slot 8 kg + 7 zero).  A loading thread covers 4 consecutive pairs (or slots)
+// at 2 entries: half-warps run along a in global memory, one 128-bit shared store each.
+// Four warp-aligned teams of 64 threads take every fourth entry; a thread accumulates
+// pairs 4 pg + {0..3}, 32 + 4 pg + {0..3} x points 7 kg + {0..6} (four conflict-free 128-bit
+// shared loads per 56 FMAs); the teams' sums meet in shared memory at the end.
+constexpr int kDtP = 64, kDtK = 56, kDtSlots = 64, kDtAB = 32, kDtTeams = 4, kDtRaw = 3;
+static_assert(kDwAbPart % kDtAB == 0, "whole chunks per part");
+
+__global__ void __launch_bounds__(256) reduce_dw_t_kernel(const __grid_constant__ LscDims d, const float* __restrict__ P,
+                                                          int64_t p_cs, int64_t split_stride, int splits,
+                                                          const float* __restrict__ Mt, float* __restrict__ dwp,
+                                                          int64_t part_stride) {
+  __shared__ __align__(16) float gs[kDtAB][kDtP + 4];
+  __shared__ __align__(16) float ms_[kDtAB][kDtSlots + 4];
+  __shared__ __align__(16) float red[kDtP * kDtK];
+  __shared__ int64_t base_p[kDtP];  // P offset of (pair, a = 0, b = 0)
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int npairs = d.c_out * d.c_in, nab = d.n_out * d.n_in;
+  const int nparts = (nab + kDwAbPart - 1) / kDwAbPart;
+  const int pair = blockIdx.z / nparts, part = blockIdx.z % nparts;
+  const int s = pair / d.s_in, sp = pair % d.s_in;
+  const int p0 = blockIdx.y * kDtP, k0 = blockIdx.x * kDtK;
+  const int np = min(kDtP, npairs - p0);
+  const bool in_win = sp >= d.win_lo[s] && sp < d.win_hi[s];
+  const int ab_beg = part * kDwAbPart, ab_end = min(nab, ab_beg + kDwAbPart);
+  // compute roles
+  const int team = warp / 2, t64 = tid % 64, pg = t64 % 8, kg = t64 / 8;
+  // load roles: quad q (pairs or slots 4q .. 4q+3), entries tl and tl + 16
+  const int q = 2 * warp + lane / 16, tl = lane % 16;
+  float acc[8][7];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 7; ++j) acc[i][j] = 0.f;
+  if (in_win) {
+    if (tid < kDtP) {
+      const int pr = p0 + tid, co = pr / d.c_in, ci = pr - co * d.c_in;
+      base_p[tid] = tid < np ? ((int64_t)s * d.c_out + co) * d.n_out + ((int64_t)sp * d.c_in + ci) * d.n_in * p_cs : 0;
+    }
+    __syncthreads();
+    const float* Ms = Mt + s * d.m_stride_s + sp * d.m_stride_sp;
+    // this thread's kernel points of slot quad q (slot 8 kg + j holds k = 7 kg + j, j < 7)
+    int kq[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int slot = 4 * q + c, j = slot % 8;
+      kq[c] = j < 7 ? k0 + 7 * (slot / 8) + j : -1;
+    }
+    float raw[2][4][kDtRaw], mv[2][4];
+    auto issue = [&](int ab0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ab = ab0 + tl + 16 * h;
+        const bool ok = ab < ab_end;
+        const int bb = ok ? ab / d.n_out : 0, aa = ok ? ab - bb * d.n_out : 0;
+        const int64_t off = aa + (int64_t)bb * p_cs;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int pp = 4 * q + c;
+          const bool on = ok && pp < np;
+          const float* src = P + (on ? base_p[pp] + off : 0);
+#pragma unroll
+          for (int z = 0; z < kDtRaw; ++z) raw[h][c][z] = (on && z < splits) ? __ldg(src + z * split_stride) : 0.f;
+          for (int z = kDtRaw; z < splits; ++z) raw[h][c][kDtRaw - 1] += on ? __ldg(src + z * split_stride) : 0.f;
+          const int k = kq[c];
+          mv[h][c] = (ok && k >= 0 && k < d.K) ? __ldg(Ms + (int64_t)k * nab + ab) : 0.f;
+        }
+      }
+    };
+    issue(ab_beg);
+    for (int ab0 = ab_beg; ab0 < ab_end; ab0 += kDtAB) {
+      __syncthreads();  // the previous chunk's FMAs are done with gs / ms_
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float g[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          g[c] = raw[h][c][0];
+#pragma unroll
+          for (int z = 1; z < kDtRaw; ++z) g[c] += raw[h][c][z];
+        }
+        *reinterpret_cast<float4*>(&gs[tl + 16 * h][4 * q]) = make_float4(g[0], g[1], g[2], g[3]);
+        *reinterpret_cast<float4*>(&ms_[tl + 16 * h][4 * q]) = make_float4(mv[h][0], mv[h][1], mv[h][2], mv[h][3]);
+      }
+      __syncthreads();
+      if (ab0 + kDtAB < ab_end) issue(ab0 + kDtAB);
+      // entries past the part's end were staged as zeros: a fixed trip count
+#pragma unroll
+      for (int u = 0; u < kDtAB / kDtTeams; ++u) {
+        const int t = team + kDtTeams * u;
+        const float4 g0 = *reinterpret_cast<const float4*>(&gs[t][4 * pg]);
+        const float4 g1 = *reinterpret_cast<const float4*>(&gs[t][32 + 4 * pg]);
+        const float4 m0 = *reinterpret_cast<const float4*>(&ms_[t][8 * kg]);
+        const float4 m1 = *reinterpret_cast<const float4*>(&ms_[t][8 * kg + 4]);
+        const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+        const float mm[7] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 7; ++j) acc[i][j] = fmaf(gv[i], mm[j], acc[i][j]);
+      }
+    }
+    // the teams' sums, in team order (deterministic); thread (pg, kg) owns pairs
+    // 4 pg + i (i < 4) and 32 + 4 pg + i - 4 (i >= 4), points 7 kg + j
+    auto ridx = [&](int i, int j) { return ((i < 4 ? 4 * pg + i : 28 + 4 * pg + i)) * kDtK + 7 * kg + j; };
+    for (int tm = 1; tm < kDtTeams; ++tm) {
+      __syncthreads();
+      if (team == tm) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 7; ++j) {
+            float& x = red[ridx(i, j)];
+            x = tm == 1 ? acc[i][j] : x + acc[i][j];
+          }
+      }
+    }
+    __syncthreads();
+    if (team == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 7; ++j) acc[i][j] += red[ridx(i, j)];
+    }
+  }
+  if (team != 0) return;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int pr = p0 + (i < 4 ? 4 * pg + i : 28 + 4 * pg + i);
+    if (pr >= npairs) continue;
+    const int co = pr / d.c_in, ci = pr - co * d.c_in;
+    float* out = dwp + part * part_stride + ((((int64_t)co * d.s_out + s) * d.c_in + ci) * d.s_in + sp) * d.K;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const int k = k0 + 7 * kg + j;
+      if (k < d.K) out[k] = acc[i][j];
+    }
+  }
+}
+
 // dw[i] = sum over parts in order (deterministic)
 __global__ void sum_parts_kernel(const float* __restrict__ dwp, int64_t part_stride, int nparts, int64_t n,
                                  float* __restrict__ dw) {
@@ -829,12 +952,15 @@ cudaError_t launch_reduce_dw(const LscDims& d, const float* P, int64_t p_rs, int
   if (dw) {
     const int nparts = (d.n_out * d.n_in + kDwAbPart - 1) / kDwAbPart;
     const int64_t n = (int64_t)d.c_out * d.s_out * d.c_in * d.s_in * d.K;
-    dim3 grid((unsigned)((d.K + 63) / 64), (unsigned)((d.c_out * d.c_in + 63) / 64),
-              (unsigned)(d.s_out * d.s_in * nparts));
-    if (p_rs == 1)
-      reduce_dw_kernel<true><<<grid, 256, 0, st>>>(d, P, p_rs, p_cs, split_stride, splits, Mt, scratch, n);
-    else
-      reduce_dw_kernel<false><<<grid, 256, 0, st>>>(d, P, p_rs, p_cs, split_stride, splits, M, scratch, n);
+    if (p_rs == 1) {
+      dim3 grid((unsigned)((d.K + kDtK - 1) / kDtK), (unsigned)((d.c_out * d.c_in + kDtP - 1) / kDtP),
+                (unsigned)(d.s_out * d.s_in * nparts));
+      reduce_dw_t_kernel<<<grid, 256, 0, st>>>(d, P, p_cs, split_stride, splits, Mt, scratch, n);
+    } else {
+      dim3 grid((unsigned)((d.K + 63) / 64), (unsigned)((d.c_out * d.c_in + 63) / 64),
+                (unsigned)(d.s_out * d.s_in * nparts));
+      reduce_dw_kernel<<<grid, 256, 0, st>>>(d, P, p_rs, p_cs, split_stride, splits, M, scratch, n);
+    }
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

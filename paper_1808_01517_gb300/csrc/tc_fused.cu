@@ -11,15 +11,18 @@
 // N_out read as zero through a 3-D map {K, N_out, channels} of W, so W needs no padded
 // copy).  The main loop is the forward GEMM's (TMA ring, one MMA-issuing thread, TMEM
 // double buffer).  The epilogue of a tile runs in two rounds of two channels:
-//   1. eight warps read the accumulator, add the bias, round to BF16 and write each
+//   1. twelve warps read the accumulator, add the bias, round to BF16 and write each
 //      channel's 128 voxels x 48 rows into shared memory in the MN-major 128-byte-swizzled
 //      operand layout (stmatrix .trans);
 //   2. a dedicated warp of the even CTA issues, per channel, the 2-SM MMA
 //      D2[256 voxels, 96] = A2[256, 48] x B_s^T[48, 96] (B_s^T resident, K-major, each
 //      CTA 48 of the 96 directions), into accumulator columns already read (the first
 //      channel of a round) and a spare 96-column TMEM block (the second);
-//   3. the eight warps read D2, round to BF16 and stage each channel's 90 direction rows
-//      for a TMA store into the s_out rows of that shell and channel.
+//   3. the epilogue warps read D2, round to BF16 and store it straight from registers into
+//      the s_out rows of that shell and channel (lane = voxel: 64 contiguous bytes per warp
+//      and direction row).  Staging these rows in shared memory for TMA stores measured
+//      slower: the staging writes and the stores' reads share the SM's shared-memory
+//      bandwidth with the main MMAs' operand reads.
 // TMEM: 2 x 192 accumulator columns + 96 spare (512 allocated).  Every wait is bounded.
 #include <cudaTypedefs.h>
 
@@ -38,7 +41,7 @@ constexpr int kBN = 192;        // operator rows per tile: 4 channel slots
 constexpr int kSlot = 48;       // rows per channel slot (N_out <= kSlot)
 constexpr int kDirs = 96;       // SH2Signal outputs per channel slot (m_s <= kDirs)
 constexpr int kK = 64;          // K rows per main stage
-constexpr int kFEpi = 8;        // epilogue warps, two per TMEM lane quarter
+constexpr int kFEpi = 12;       // epilogue warps, three per TMEM lane quarter
 constexpr int kFThreads = 32 * (3 + kFEpi);  // TMA producer, MMA issuer, SH2Signal MMA issuer, epilogue
 constexpr int kAccStride = 192;               // TMEM columns between the two accumulators
 constexpr int kSpareCol = 384;                // the spare 96-column D2 block
@@ -46,7 +49,6 @@ constexpr uint32_t kABytes = 2 * 64 * 128;                 // 128 voxels x 64 K 
 constexpr uint32_t kBBytes = (kBN / 2) * 128;              // this CTA's 96 operator rows x 64 K
 constexpr uint32_t kStage = kABytes + kBBytes;             // 28 KiB
 constexpr uint32_t kA2Bytes = 2 * kSlot * 128;             // one channel: 128 voxels x 48 rows
-constexpr uint32_t kStgBytes = 2 * kDirs * 128;            // one channel's s_out: 128 voxels x 96 rows
 constexpr uint32_t kB2Bytes = (kDirs / 2) * 128;           // one shell's B_s^T half: 48 rows x 64 K
 constexpr int kMaxShellsF = 4;
 
@@ -57,7 +59,6 @@ enum : int {
   kErrTEmpty = 0x4400,
   kErrA2 = 0x4500,
   kErrD2 = 0x4600,
-  kErrStg = 0x4700,
   kErrDrain = 0x4800
 };
 
@@ -66,8 +67,10 @@ enum : int {
 struct FusedParams {
   int a_k0[kMaxShellsF], K[kMaxShellsF];  // the window's first input row and extent per output shell
   int m_dirs[kMaxShellsF];                // directions of each output shell (<= kDirs)
+  int64_t s_row0[kMaxShellsF];            // first s_out row of each output shell (c_out * dir_off)
   int n_groups, c_out, n_out, tiles_per_group, m_pairs, stages;
-  int64_t total_tiles, n_vox;
+  int64_t total_tiles, n_vox, lds;
+  __nv_bfloat16* S;
   const float* bias;  // [rows_out] (s, co, a), or NULL
   int* err;
 };
@@ -76,14 +79,11 @@ struct FusedMaps {
   CUtensorMap a;                 // X: 2-D {voxels, rows_in}, box {64, 64}
   CUtensorMap b;                 // W: 3-D {K columns, N_out rows, S_out * c_out channels}, box {64, 48, 2}
   CUtensorMap b2;                // B_s^T images: 2-D {64 (a), S_out * 96 (i)}, box {64, 48}
-  CUtensorMap s[kMaxShellsF];    // s_out of shell s: 3-D {voxels, m_s rows, c_out channels}, box {64, m_s, 1}
 };
 
-// smem: [ring stages x 28 KiB][A2: 2 channels x 12 KiB][s_out staging: 2 x 24 KiB]
-//       [B2: S_out x 6 KiB][barriers]
+// smem: [ring stages x 28 KiB][A2: 2 channels x 12 KiB][B2: S_out x 6 KiB][barriers]
 __host__ __device__ constexpr size_t fused_smem(int stages, int shells) {
-  return 1024 + (size_t)stages * kStage + 2 * kA2Bytes + 2 * kStgBytes + (size_t)shells * kB2Bytes +
-         (2 * stages + 16) * 8 + 16;
+  return 1024 + (size_t)stages * kStage + 2 * kA2Bytes + (size_t)shells * kB2Bytes + (2 * stages + 16) * 8 + 16;
 }
 
 template <int STAGES>
@@ -94,12 +94,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
   const uint32_t a2_base = sbase + STAGES * kStage;
-  const uint32_t stg_base = a2_base + 2 * kA2Bytes;
-  const uint32_t b2_base = stg_base + 2 * kStgBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * kStage + 2 * kA2Bytes + 2 * kStgBytes +
-                                               (size_t)p.n_groups * kB2Bytes);
-  // bars: full[S], empty[S], tfull[2], tempty[2], a2_full, d2_full, stg_ready[2], stg_free[2],
-  //       bload, drain, drain2, bpeer
+  const uint32_t b2_base = a2_base + 2 * kA2Bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * kStage + 2 * kA2Bytes + (size_t)p.n_groups * kB2Bytes);
+  // bars: full[S], empty[S], tfull[2], tempty[2], a2_full, d2_full, bload, drain, drain2, bpeer
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 16);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
@@ -108,12 +105,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
   auto tempty_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
   const uint32_t a2_full = smem_u32(bars + 2 * STAGES + 4);
   const uint32_t d2_full = smem_u32(bars + 2 * STAGES + 5);
-  auto stg_ready = [&](int h) { return smem_u32(bars + 2 * STAGES + 6 + h); };
-  auto stg_free = [&](int h) { return smem_u32(bars + 2 * STAGES + 8 + h); };
-  const uint32_t bload_bar = smem_u32(bars + 2 * STAGES + 10);
-  const uint32_t drain_bar = smem_u32(bars + 2 * STAGES + 11);
-  const uint32_t drain2_bar = smem_u32(bars + 2 * STAGES + 12);
-  const uint32_t bpeer_bar = smem_u32(bars + 2 * STAGES + 13);  // the odd CTA's B_s^T half has landed
+  const uint32_t bload_bar = smem_u32(bars + 2 * STAGES + 6);
+  const uint32_t drain_bar = smem_u32(bars + 2 * STAGES + 7);
+  const uint32_t drain2_bar = smem_u32(bars + 2 * STAGES + 8);
+  const uint32_t bpeer_bar = smem_u32(bars + 2 * STAGES + 9);  // the odd CTA's B_s^T half has landed
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int rank = (int)cluster_rank();
   const int64_t t_first = (int64_t)cluster_id_x(), t_step = (int64_t)cluster_count_x();
@@ -136,10 +131,6 @@ __global__ void __launch_bounds__(kFThreads, 1)
     }
     mbar_init(a2_full, 2 * kFEpi);  // both CTAs' epilogues have staged a round's two channels
     mbar_init(d2_full, 1);
-    for (int h = 0; h < 2; ++h) {
-      mbar_init(stg_ready(h), kFEpi / 2);
-      mbar_init(stg_free(h), 1);
-    }
     mbar_init(bload_bar, 1);
     mbar_init(drain_bar, 1);
     mbar_init(drain2_bar, 1);
@@ -282,23 +273,25 @@ __global__ void __launch_bounds__(kFThreads, 1)
     mma_commit_pair(drain2_bar);
     wait_drain(drain2_bar, 0, p.err, kErrDrain);
   } else if (warp >= 3) {
-    // ---------------- epilogue (eight warps per CTA) ----------------
-    // quarter q = warp % 4 holds voxels 32q .. 32q + 31; half h = which channel of a round
-    const int q = warp & 3, h = (warp - 3) >> 2;
-    const bool storer = (warp == 3 + 4 * h) && lane == 0;
+    // ---------------- epilogue (twelve warps per CTA) ----------------
+    // quarter q = warp % 4 holds voxels 32q .. 32q + 31; the three warps of a quarter (group
+    // 0, 1, 2) take 16-column chunks ck = group (+ 3) of each channel of a round
+    const int q = warp & 3, grp = (warp - 3) >> 2;
     const int vq = (q & 1) * 4, mm = lane >> 3, rr = lane & 7;
     const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
-    // 16 accumulator columns from `col` of this quarter's 32 lanes, plus b[] (columns
-    // 2(l%4) + {0, 1, 8, 9}), packed to BF16 and written by stmatrix .trans as rows row0 ..
-    // row0 + 15 of a staging half with 128-byte rows (16-byte chunk XOR row % 8)
-    auto stage16 = [&](uint32_t col, uint32_t half_base, int row0, const float (&b)[4]) {
-      uint32_t rv[2][2][4];
+    // 16 accumulator columns from `col` of this quarter's 32 lanes (16x256b loads: two
+    // 16-lane blocks x two 8-column halves), issued without waiting
+    auto load16 = [&](uint32_t col, uint32_t (&rv)[2][2][4]) {
 #pragma unroll
       for (int lb = 0; lb < 2; ++lb)
 #pragma unroll
         for (int c8 = 0; c8 < 2; ++c8)
           tmem_ld_16x256b_nowait(lane_base + ((uint32_t)(16 * lb) << 16) + col + (uint32_t)(8 * c8), rv[lb][c8]);
-      tmem_wait_ld();
+    };
+    // the loaded columns plus b[] (columns 2(l%4) + {0, 1, 8, 9}), packed to BF16 and written by
+    // stmatrix .trans as rows row0 .. row0 + 15 of a staging half with 128-byte rows (16-byte
+    // chunk XOR row % 8)
+    auto store16 = [&](const uint32_t (&rv)[2][2][4], uint32_t half_base, int row0, const float (&b)[4]) {
 #pragma unroll
       for (int lb = 0; lb < 2; ++lb) {
         const uint32_t* r0 = rv[lb][0];
@@ -318,58 +311,70 @@ __global__ void __launch_bounds__(kFThreads, 1)
       int g, mtp, nt;
       decode(t, g, mtp, nt);
       const int mt = 2 * mtp + rank;
-      bool ok = wait_bounded_sleep(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTFull);
+      bool ok = wait_bounded(tfull_bar(acc), acc_phase, abort_flag, p.err, kErrTFull);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       for (int r = 0; r < 2; ++r, ++u) {
-        const int j = 2 * r + h;           // this half's channel slot of the tile
-        const int co = 4 * nt + j;         // its output channel
-        // 1. c_out + bias -> BF16 -> A2 (rows a of the 48-row slot, voxels MN-major)
-        const uint32_t a2h = a2_base + (uint32_t)(h * kA2Bytes) + (uint32_t)((q >> 1) * kSlot * 128);
-        const float* brow = p.bias ? p.bias + ((int64_t)g * p.c_out + co) * p.n_out : nullptr;
+        // 1. c_out + bias -> BF16 -> A2 of both channels of the round (rows a of the 48-row
+        //    slot, voxels MN-major): this warp's chunk ck = grp of each
+        {
+          uint32_t rv[2][2][2][4];
+          float b[2][4];
 #pragma unroll
-        for (int ck = 0; ck < kSlot / 16; ++ck) {
-          float b[4];
+          for (int h = 0; h < 2; ++h) {
+            const int j = 2 * r + h, co = 4 * nt + j;
+            load16((uint32_t)(acc * kAccStride + kSlot * j + 16 * grp), rv[h]);
+            const float* brow = p.bias ? p.bias + ((int64_t)g * p.c_out + co) * p.n_out : nullptr;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int a = 16 * ck + 2 * (lane & 3) + (i & 1) + 8 * (i >> 1);
-            b[i] = (brow && a < p.n_out) ? __ldg(brow + a) : 0.f;
+            for (int i = 0; i < 4; ++i) {
+              const int a = 16 * grp + 2 * (lane & 3) + (i & 1) + 8 * (i >> 1);
+              b[h][i] = (brow && a < p.n_out) ? __ldg(brow + a) : 0.f;
+            }
           }
-          stage16((uint32_t)(acc * kAccStride + kSlot * j + 16 * ck), a2h, 16 * ck, b);
+          tmem_wait_ld();
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            store16(rv[h], a2_base + (uint32_t)(h * kA2Bytes) + (uint32_t)((q >> 1) * kSlot * 128), 16 * grp, b[h]);
         }
         tc_fence_before();
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive_cluster(mapa_shared(a2_full, 0));
         // 2. the pair's SH2Signal MMAs of this round
-        ok = wait_bounded_sleep(d2_full, u & 1u, abort_flag, p.err, kErrD2);
-        // 3. D2 -> BF16 -> the staging tile of this half -> TMA store of the channel's rows
-        ok = ok && wait_bounded_sleep(stg_free(h), (u & 1u) ^ 1u, abort_flag, p.err, kErrStg);
+        ok = wait_bounded(d2_full, u & 1u, abort_flag, p.err, kErrD2);
         if (!__all_sync(0xffffffffu, ok)) {
           alive = false;
           break;
         }
         tc_fence_after();
-        const uint32_t d2 = (uint32_t)(h == 0 ? acc * kAccStride + 96 * r : kSpareCol);
-        const uint32_t sh = stg_base + (uint32_t)(h * kStgBytes) + (uint32_t)((q >> 1) * kDirs * 128);
-        const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+        // 3. D2 -> BF16 -> s_out straight from registers: lane = voxel, a warp writes 64
+        //    contiguous bytes per direction row
+        {
+          const int m = p.m_dirs[g];
+          const int64_t v = (int64_t)mt * 128 + q * 32 + lane;
+          const bool in = v < p.n_vox;
 #pragma unroll
-        for (int ck = 0; ck < kDirs / 16; ++ck) stage16(d2 + (uint32_t)(16 * ck), sh, 16 * ck, zero);
-        tc_fence_before();
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(stg_ready(h));
-        if (storer) {
-          if (wait_bounded(stg_ready(h), u & 1u, abort_flag, p.err, kErrStg)) {
-            const uint32_t src = stg_base + (uint32_t)(h * kStgBytes);
-            tma_store_3d(&maps.s[g], src, mt * 128, 0, co);
-            tma_store_3d(&maps.s[g], src + (uint32_t)(kDirs * 128), mt * 128 + 64, 0, co);
-            bulk_commit();
-            bulk_wait_read<0>();  // the staging tile may be refilled once the store has read it
-            mbar_arrive(stg_free(h));
+          for (int h = 0; h < 2; ++h) {
+            const int co = 4 * nt + 2 * r + h;
+            const uint32_t d2 = (uint32_t)(h == 0 ? acc * kAccStride + 96 * r : kSpareCol);
+            uint32_t rv[2][16];
+#pragma unroll
+            for (int c2 = 0; c2 < 2; ++c2) tmem_ld16_nowait(lane_base + d2 + (uint32_t)(16 * (grp + 3 * c2)), rv[c2]);
+            tmem_wait_ld();
+            if (in) {
+#pragma unroll
+              for (int c2 = 0; c2 < 2; ++c2) {
+                const int i0 = 16 * (grp + 3 * c2);
+                __nv_bfloat16* y = p.S + (p.s_row0[g] + (int64_t)co * m + i0) * p.lds + v;
+#pragma unroll
+                for (int j = 0; j < 16; ++j, y += p.lds)
+                  if (i0 + j < m) *y = __float2bfloat16_rn(__uint_as_float(rv[c2][j]));
+              }
+            }
           }
         }
-        __syncwarp();  // converged again before the next round's warp-wide TMEM loads
+        tc_fence_before();
+        __syncwarp();
       }
       if (!alive) break;
       // the accumulator (and the D2 columns in it) is drained: back to the MMA issuer
@@ -379,7 +384,6 @@ __global__ void __launch_bounds__(kFThreads, 1)
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
-    if (storer) bulk_wait<0>();
   }
   tc_fence_before();
   __syncthreads();
@@ -511,19 +515,15 @@ cudaError_t tc_lsc_forward_sh2signal(const LscDims& d, const FusedTables& f, con
     const cuuint32_t box[2] = {64, (cuuint32_t)(kDirs / 2)};
     if (!enc(&maps.b2, 2, f.d_b2, dims, strides, box)) return cudaErrorInvalidValue;
   }
-  for (int s = 0; s < d.s_out; ++s) {  // s_out of shell s: rows c_out * dir_off[s] + co * m_s + i
-    const char* base = static_cast<const char*>(S) + (int64_t)d.c_out * f.dir_off[s] * lds * 2;
-    const cuuint64_t dims[3] = {(cuuint64_t)n_vox, (cuuint64_t)f.m[s], (cuuint64_t)d.c_out};
-    const cuuint64_t strides[2] = {(cuuint64_t)lds * 2, (cuuint64_t)f.m[s] * lds * 2};
-    const cuuint32_t box[3] = {64, (cuuint32_t)f.m[s], 1};
-    if (!enc(&maps.s[s], 3, base, dims, strides, box)) return cudaErrorInvalidValue;
-  }
   const int per_in = d.c_in * d.n_in;
   for (int s = 0; s < d.s_out; ++s) {
     p.a_k0[s] = d.win_lo[s] * per_in;
     p.K[s] = (d.win_hi[s] - d.win_lo[s]) * per_in;
     p.m_dirs[s] = f.m[s];
+    p.s_row0[s] = (int64_t)d.c_out * f.dir_off[s];
   }
+  p.S = static_cast<__nv_bfloat16*>(S);
+  p.lds = lds;
   p.n_groups = d.s_out;
   p.c_out = d.c_out;
   p.n_out = d.n_out;

@@ -97,7 +97,7 @@ def test_chain_full_size_sampled_vs_oracle(dtype, tol, n_vox):
     cfg = ChainConfig(n_vox=n_vox)
     dirs, bvals = synth.multishell_table(list(cfg.dirs_per_shell), list(cfg.bvals), seed=cfg.seed)
     S, m, K = 3, 90, 1 + cfg.rings * cfg.sectors
-    ch = Chain(cfg, dirs, bvals, dtype)
+    ch = Chain(cfg, dirs, bvals, dtype, fused=True)  # fused where the kernel takes the sizes (BF16)
     w = synth.gaussian((cfg.c_out, S, cfg.c_in, S, K), 0.1, seed=5)
     b = synth.gaussian((cfg.c_out, S), 0.1, seed=6)
     g = torch.Generator(device="cuda")
