@@ -34,13 +34,13 @@ UNIT = "voxels/s"
 # single-pass ncu capture of the bench command summarised in
 # profiles/chain_65536vox_launch_list.md (the `dram__bytes_*` metrics); valid only
 # while the kernel's sources hash to the value recorded with the capture.
-_GEMM = ("csrc/tc_gemm.cu", "csrc/tc_ptx.cuh"), "f932e85928aba808"
-_TF = ("csrc/tc_transform.cu", "csrc/tc_ptx.cuh"), "8dca8e7f1a0b2c2d"
+_GEMM = ("csrc/tc_gemm.cu", "csrc/tc_ptx.cuh"), "c1008f39dfc6ee63"
+_TF = ("csrc/tc_transform.cu", "csrc/tc_ptx.cuh"), "b83be9863d260faf"
 NCU_TRAFFIC = {
-    "lsc_fwd_gemm": {"bytes": 1.632e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
-    "lsc_dgrad_gemm": {"bytes": 2.436e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
-    "lsc_wgrad_gemm": {"bytes": 2.757e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
-    "signal2sh_tc": {"bytes": 0.8129e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
+    "lsc_fwd_gemm": {"bytes": 1.654e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "lsc_dgrad_gemm": {"bytes": 2.260e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "lsc_wgrad_gemm": {"bytes": 2.564e9, "n_vox": 65536, "sources": _GEMM[0], "sha256_16": _GEMM[1]},
+    "signal2sh_tc": {"bytes": 0.8136e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
     "sh2signal_tc": {"bytes": 3.333e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
     "sh2signal_bwd_tc": {"bytes": 3.358e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},
     "signal2sh_bwd_tc": {"bytes": 0.7845e9, "n_vox": 65536, "sources": _TF[0], "sha256_16": _TF[1]},

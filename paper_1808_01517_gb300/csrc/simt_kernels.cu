@@ -355,12 +355,12 @@ cudaError_t launch_ring_weights(const float* src, float* dst, int64_t n_e, int K
 // run of a row (s, co, a): the block's channels ci and their b entries, contiguous in W;
 // and to Wt (runs along a).  Shell pairs outside the window write zeros.
 // ---------------------------------------------------------------------------
-constexpr int kBwP = 64, kBwAB = 256, kBwKC = 56;  // pairs, (a,b) entries, kernel points per chunk
+constexpr int kBwP = 64, kBwAB = 128, kBwKC = 56;  // pairs, (a,b) entries, kernel points per chunk
 constexpr size_t kBwSmem = sizeof(float) * kBwKC * (kBwAB + kBwP);  // a chunk (M + w); then the results
 static_assert(kBwP * kBwAB <= kBwKC * (kBwAB + kBwP), "the results fit a staged chunk's space");
 
 template <typename TW>
-__global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
+__global__ void __launch_bounds__(256, 3) build_w_kernel(const __grid_constant__ LscDims d, const float* __restrict__ w,
                                                       const float* __restrict__ M, TW* __restrict__ W,
                                                       TW* __restrict__ Wt) {
   extern __shared__ float4 blk4[];  // chunk: ms [kBwKC][kBwAB], ws [kBwKC][kBwP]; then results [kBwP][kBwAB]
@@ -376,11 +376,11 @@ __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ Ls
   const int np = min(kBwP, npairs - p0);
   const int ab0 = blockIdx.z * kBwAB, nabc = min(kBwAB, nab - ab0);  // this block's (a,b) range
   // acc[i][e2] = entries 2 e2, 2 e2 + 1 of pair i: packed FP32x2 FMAs (each lane rounds as fmaf)
-  float2 acc[8][4];
+  float2 acc[8][2];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) acc[i][e] = make_float2(0.f, 0.f);
+    for (int e = 0; e < 2; ++e) acc[i][e] = make_float2(0.f, 0.f);
   if (in_win) {
     const float* Ms = M + s * d.m_stride_s + sp * d.m_stride_sp + ab0;
     for (int k0 = 0; k0 < d.K; k0 += kBwKC) {
@@ -388,8 +388,10 @@ __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ Ls
       __syncthreads();  // the previous chunk is consumed
       // M rows k0 .. k0 + kc - 1: thread tid loads entry tid of each (zero past the ranges)
 #pragma unroll 8
-      for (int kk = 0; kk < kBwKC; ++kk)
-        ms[kk * kBwAB + tid] = (kk < kc && tid < nabc) ? __ldg(Ms + (int64_t)(k0 + kk) * nab + tid) : 0.f;
+      for (int i = tid; i < kBwKC * kBwAB; i += 256) {
+        const int kk = i / kBwAB, t = i % kBwAB;
+        ms[i] = (kk < kc && t < nabc) ? __ldg(Ms + (int64_t)(k0 + kk) * nab + t) : 0.f;
+      }
       // w[p][k0 + kk] for the block's pairs, pair index fastest (conflict-free stores)
 #pragma unroll
       for (int e = 0; e < kBwKC * kBwP / 256; ++e) {
@@ -402,20 +404,19 @@ __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ Ls
         ws[kk * kBwP + pp] = v;
       }
       __syncthreads();
-      const float4* ms4 = reinterpret_cast<const float4*>(ms) + 2 * lane;
+      const float4* ms4 = reinterpret_cast<const float4*>(ms) + lane;
       const float4* ws4 = reinterpret_cast<const float4*>(ws) + 2 * warp;
 #pragma unroll 2
       for (int kk = 0; kk < kc; ++kk) {
-        const float4 m0 = ms4[kk * (kBwAB / 4)], m1 = ms4[kk * (kBwAB / 4) + 1];
+        const float4 m0 = ms4[kk * (kBwAB / 4)];
         const float4 w0 = ws4[kk * (kBwP / 4)], w1 = ws4[kk * (kBwP / 4) + 1];
-        const float2 mv[4] = {make_float2(m0.x, m0.y), make_float2(m0.z, m0.w), make_float2(m1.x, m1.y),
-                              make_float2(m1.z, m1.w)};
+        const float2 mv[2] = {make_float2(m0.x, m0.y), make_float2(m0.z, m0.w)};
         const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const float2 wi = make_float2(wv[i], wv[i]);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) acc[i][e] = __ffma2_rn(wi, mv[e], acc[i][e]);
+          for (int e = 0; e < 2; ++e) acc[i][e] = __ffma2_rn(wi, mv[e], acc[i][e]);
         }
       }
     }
@@ -424,8 +425,7 @@ __global__ void __launch_bounds__(256) build_w_kernel(const __grid_constant__ Ls
   // results [p][t]: pair p = 8 warp + i, entry t = 8 lane + e
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    blk4[(8 * warp + i) * (kBwAB / 4) + 2 * lane] = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
-    blk4[(8 * warp + i) * (kBwAB / 4) + 2 * lane + 1] = make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
+    blk4[(8 * warp + i) * (kBwAB / 4) + lane] = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
   }
   __syncthreads();
   // Stores: one warp per output run (a pair's row segment), lanes along the contiguous index
