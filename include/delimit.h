@@ -426,6 +426,16 @@ delimit_status delimit_selftest_wait_timeout(void* stream);
  * and are not affected. */
 delimit_status delimit_set_tensor_cores(int mode);
 
+/* Process-wide CTA-pair choice of the LSC tensor-core GEMMs (forward, input and
+ * weight gradients); no counterpart in the paper.
+ *   0 (default): each GEMM's own choice: CTA pairs issuing 2-SM MMAs where the
+ *     operator tiles split into two whole halves, else single CTAs.
+ *   2: CTA pairs wherever the tiles allow (as 0 for the shapes above);
+ *   1: single-CTA MMAs everywhere (the form the other shapes take; results equal
+ *     to the pairs' up to FP32 summation order).
+ * Other values: INVALID_ARG.  Takes effect at the next call. */
+delimit_status delimit_set_gemm_cluster(int ctas);
+
 /* Number of activation-GEMM calls that ran on the CUDA cores under policy 1
  * since the process started (host-side count).  No counterpart in the paper. */
 uint64_t delimit_cuda_core_fallbacks(void);

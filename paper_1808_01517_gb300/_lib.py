@@ -86,6 +86,7 @@ SIGNATURES = {
     "delimit_set_tensor_cores": (C.c_int, [C.c_int]),
     "delimit_kernel_launches": (C.c_uint64, []),
     "delimit_cuda_core_fallbacks": (C.c_uint64, []),
+    "delimit_set_gemm_cluster": (C.c_int, [C.c_int]),
     "delimit_trace_enable": (C.c_int, [C.c_int]),
     "delimit_trace_summary": (C.c_int64, [C.c_char_p, C.c_size_t]),
     "delimit_status_string": (C.c_char_p, [C.c_int]),
@@ -253,6 +254,12 @@ def set_tensor_cores(mode):
 
 def cuda_core_fallbacks() -> int:
     return int(get().delimit_cuda_core_fallbacks())
+
+
+def set_gemm_cluster(ctas: int):
+    """CTAs per cluster of the LSC tensor-core GEMMs: 0 = each GEMM's default, 1 = single
+    CTAs, 2 = CTA pairs with 2-SM MMAs where the tiles allow."""
+    check(get().delimit_set_gemm_cluster(int(ctas)), "delimit_set_gemm_cluster")
 
 
 def device_error(stream_ptr: int = 0):

@@ -140,6 +140,12 @@ delimit_status delimit_set_tensor_cores(int mode) {
 
 uint64_t delimit_cuda_core_fallbacks(void) { return g_cuda_core_fallbacks.load(); }
 
+delimit_status delimit_set_gemm_cluster(int ctas) {
+  if (ctas < 0 || ctas > 2) return fail(DELIMIT_ERR_INVALID_ARG, "GEMM cluster must be 0, 1 or 2");
+  tc_set_gemm_cluster(ctas);
+  return DELIMIT_OK;
+}
+
 const char* delimit_last_error(void) { return g_last_error.c_str(); }
 
 const char* delimit_status_string(delimit_status s) {

@@ -54,6 +54,17 @@ constexpr int kBoxBytes = 64 * 128;  // one 64 x 64 BF16 box, 128-byte rows
 void tc_set_enabled(bool on) { g_tc_on.store(on); }
 bool tc_enabled() { return g_tc_on.load(); }
 
+namespace {
+// CTAs per cluster of the LSC GEMMs: 0 = each GEMM's default, 1 or 2 forced
+// (delimit_set_gemm_cluster).  2 = a CTA pair issuing 2-SM tcgen05 MMAs
+// (cta_group::2): each CTA loads its own half of the operands by TMA (no TMA
+// multicast anywhere), one thread of the even CTA issues the MMAs for both;
+// 1 = single-CTA MMAs (the form shapes that do not split into pairs take).
+std::atomic<int> g_gemm_cluster{0};
+}  // namespace
+
+void tc_set_gemm_cluster(int cl) { g_gemm_cluster.store(cl); }
+
 // ---------------------------------------------------------------------------
 // forward / input-gradient GEMM
 // ---------------------------------------------------------------------------
@@ -1122,18 +1133,10 @@ constexpr size_t smem_bytes(int a_bytes, int b_bytes) {
   return 1024 + (size_t)STAGES * (a_bytes + b_bytes) + (2 * STAGES + 5) * 8 + 16;
 }
 
-int env_int(const char* name, int dflt) {
-  const char* v = getenv(name);
-  return (v && *v) ? atoi(v) : dflt;
-}
-
-// CTAs per cluster of one GEMM: DELIMIT_GEMM_CLUSTER (1 or 2) overrides the
-// per-GEMM default.  2 = a CTA pair issuing 2-SM tcgen05 MMAs (cta_group::2): each
-// CTA loads its own half of the operands by TMA (no TMA multicast anywhere), one
-// thread of the even CTA issues the MMAs for both; 1 = single-CTA MMAs.
+// CTAs per cluster of one GEMM: its default unless delimit_set_gemm_cluster forced one
 int gemm_cluster(int dflt) {
-  const int v = env_int("DELIMIT_GEMM_CLUSTER", dflt);
-  return v == 1 ? 1 : 2;
+  const int v = g_gemm_cluster.load();
+  return (v == 0 ? dflt : v) == 1 ? 1 : 2;
 }
 
 // Clusters of `cl` CTAs of `kern` (with `smem` bytes) that fit on the device at
@@ -1358,7 +1361,7 @@ cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const
   p.n_vox = n_vox;
   p.ldy = ldy;
   p.n_terms = parts.on() ? kSplitTerms : 1;
-  p.chunk_kb = parts.on() ? std::max(1, env_int("DELIMIT_F32_CHUNK_KB", kSplitChunkKb)) : (1 << 24);
+  p.chunk_kb = parts.on() ? kSplitChunkKb : (1 << 24);
   if (parts.on())
     p.Yf = reinterpret_cast<float*>(Y);
   else
@@ -1368,8 +1371,7 @@ cudaError_t tc_lsc_forward(const LscDims& d, const void* X, const void* W, const
   // forward tiles are short in K and wide in output: stage the epilogue through TMA stores
   int bn = pick_bn(Ns, d.s_out);
   if (bn == 256) bn = ((Ns[0] % 192) == 0) ? 192 : 128;
-  bn = env_int("DELIMIT_FWD_BN", bn);
-  return run_vox(ma, B, p, bn, env_int("DELIMIT_FWD_STAGED", 1) != 0, gemm_cluster(2), Y, ldy, st);
+  return run_vox(ma, B, p, bn, true, gemm_cluster(2), Y, ldy, st);
 }
 
 cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, const void* Wt, void* dX, int64_t n_vox,
@@ -1403,7 +1405,7 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, const 
   p.n_vox = n_vox;
   p.ldy = lddx;
   p.n_terms = parts.on() ? kSplitTerms : 1;
-  p.chunk_kb = parts.on() ? std::max(1, env_int("DELIMIT_F32_CHUNK_KB", kSplitChunkKb)) : (1 << 24);
+  p.chunk_kb = parts.on() ? kSplitChunkKb : (1 << 24);
   if (parts.on())
     p.Yf = reinterpret_cast<float*>(dX);
   else
@@ -1411,7 +1413,7 @@ cudaError_t tc_lsc_dgrad(const LscDims& d, const void* dY, const void* W, const 
   p.bias = nullptr;
   p.err = err;
   const int bn = kmajor ? kDgradBN : pick_bn(Ns, d.s_in);
-  return run_vox(ma, B, p, env_int("DELIMIT_DGRAD_BN", bn), env_int("DELIMIT_DGRAD_STAGED", 0) != 0,
+  return run_vox(ma, B, p, bn, false,
                  gemm_cluster(2), dX, lddx, st);
 }
 
@@ -1454,7 +1456,7 @@ cudaError_t tc_lsc_wgrad(const LscDims& d, const void* dY, const void* X, float*
   }
   p.n_groups = d.s_out;
   p.n_terms = parts.on() ? kSplitTerms : 1;
-  p.chunk_kb = parts.on() ? std::max(1, env_int("DELIMIT_F32_CHUNK_KB", kSplitChunkKb)) : (1 << 24);
+  p.chunk_kb = parts.on() ? kSplitChunkKb : (1 << 24);
   p.splits = splits;
   p.total_tiles = p.tiles_per_split * splits;
   p.vps = vps;

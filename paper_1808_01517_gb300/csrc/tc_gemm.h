@@ -106,5 +106,6 @@ cudaError_t launch_wait_probe(int* err, int code, cudaStream_t st);
 // process-wide switch (default on): when off every BF16 step runs on the CUDA-core kernels
 void tc_set_enabled(bool on);
 bool tc_enabled();
+void tc_set_gemm_cluster(int cl);  // 0 = each GEMM's default, 1 or 2 CTAs per cluster
 
 }  // namespace delimit

@@ -25,3 +25,13 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture
+def gemm_cluster():
+    """Sets the CTAs per cluster of the LSC tensor-core GEMMs for one test (1 or 2) and
+    restores each GEMM's default afterwards."""
+    from paper_1808_01517_gb300 import _lib as L
+
+    yield L.set_gemm_cluster
+    L.set_gemm_cluster(0)

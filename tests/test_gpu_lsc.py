@@ -78,10 +78,10 @@ def _gpu_lsc(lg, c, w, b, d, ci, co, prec):
 @pytest.mark.parametrize("prec,tc,cluster", [("f32", False, 2), ("f32", True, 2), ("f32", True, 1),
                                              ("bf16", True, 2), ("bf16", True, 1), ("bf16", False, 2)])
 @pytest.mark.parametrize("case", list(CASES))
-def test_lsc_vs_oracle(case, prec, tc, cluster, monkeypatch):
+def test_lsc_vs_oracle(case, prec, tc, cluster, gemm_cluster):
     # cluster: CTAs per cluster of the tensor-core GEMMs (2 = CTA pairs with 2-SM MMAs);
     # f32 with tc: FP32 activations through three-part BF16 splits on the tensor cores
-    monkeypatch.setenv("DELIMIT_GEMM_CLUSTER", str(cluster))
+    gemm_cluster(cluster)
     cfg = CASES[case]
     og, lg = _setup(cfg)
     c, w, b, d = _inputs(og, cfg)

@@ -42,8 +42,8 @@ def _setup(cfg, seed=11):
 @pytest.mark.parametrize("prec,tc,cluster", [("f32", False, 2), ("f32", True, 2), ("bf16", True, 2),
                                              ("bf16", True, 1), ("bf16", False, 2)])
 @pytest.mark.parametrize("case", list(CASES))
-def test_resampling_free_lsc_vs_oracle(case, prec, tc, cluster, monkeypatch):
-    monkeypatch.setenv("DELIMIT_GEMM_CLUSTER", str(cluster))
+def test_resampling_free_lsc_vs_oracle(case, prec, tc, cluster, gemm_cluster):
+    gemm_cluster(cluster)
     cfg = CASES[case]
     og, lg, _, _ = _setup(cfg)
     V, ci, co = cfg["V"], cfg["ci"], cfg["co"]

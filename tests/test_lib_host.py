@@ -304,3 +304,17 @@ def test_tensor_core_policy_modes():
         assert isinstance(L.cuda_core_fallbacks(), int)
     finally:
         L.set_tensor_cores(True)
+
+
+def test_gemm_cluster_setting():
+    """delimit_set_gemm_cluster takes 0 (each GEMM's default), 1 (single CTAs) and 2 (CTA
+    pairs) and refuses anything else with a message."""
+    lib = L.get()
+    try:
+        for n in (0, 1, 2):
+            assert lib.delimit_set_gemm_cluster(n) == L.OK
+        for n in (-1, 3, 4):
+            assert lib.delimit_set_gemm_cluster(n) == L.ERR_INVALID_ARG
+            assert b"cluster" in lib.delimit_last_error()
+    finally:
+        L.set_gemm_cluster(0)
