@@ -32,6 +32,11 @@ CASES = {
     # shells-as-channels (all input shells), mixed orders, 1 input shell -> 3 output shells
     "all_mixed": dict(m=[30, 30, 30], b=[1000, 2000, 3000], order_in=4, order_out=8, lam=0.006, V=300, ci=1, co=5,
                       rad=25, R=2, Sec=6, win="all", s_in=1),
+    # many kernel points (6 rings x 12 sectors, K = 73: the operator build and the weight-
+    # gradient reduction each take a second chunk of kernel points) and 5 x 7 = 35 channel
+    # pairs (a ragged pair block), two shells, mixed orders 6 -> 8
+    "many_points": dict(m=[40, 40], b=[1000, 2000], order_in=6, order_out=8, lam=0.006, V=600, ci=5, co=7,
+                        rad=30, R=6, Sec=12, win="adjacent"),
     # the paper's moving-average example (order 4, [5], pi/5)
     "paper_ma": dict(m=[60], b=[1000], order_in=4, order_out=4, lam=0.006, V=257, ci=1, co=1, rad=36, R=1, Sec=5,
                      win="same"),
