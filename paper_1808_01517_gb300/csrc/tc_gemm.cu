@@ -381,9 +381,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (STAGED) {
         // PASSES passes of HB columns through one staging tile, copied out to Y by the
         // epilogue warps themselves with streaming (evict-first) stores, so that the
-        // output passes L2 without displacing the operand tiles other CTAs still read;
-        // measured 1.16 ms per forward at 65,536 voxels against 1.18 ms with a TMA
-        // store of the tile.  Writing the output at all costs about 0.1 ms of it (1.07 ms
+        // output passes L2 without displacing the operand tiles other CTAs still read.
+        // Measured 1.16-1.18 ms per forward at 65,536 voxels, as with a TMA store of the
+        // tile (1.17-1.19); writing the output at all costs about 0.1 ms of it (1.07 ms
         // with the stores left out), by TMA or by the warps alike.
         for (int pass = 0; pass < PASSES; ++pass) {
           const int cbeg = pass * HB;
