@@ -116,6 +116,7 @@ struct delimit_lsc_geometry {
   int* err_word = nullptr;
   LscDims dims_template;  // without channel counts
   FusedTables fused;      // B_s^T of the output basis for the LSC forward with SH2Signal fused
+  BuildWTables bw;        // BF16 parts of M for the tensor-core operator build
 };
 
 static std::vector<double> transpose(const std::vector<double>& a, int rows, int cols) {
@@ -521,6 +522,12 @@ delimit_status delimit_lsc_geometry_create(const delimit_sh_basis* ob, int order
       delete g;
       return fail(DELIMIT_ERR_OOM, "fused SH2Signal operator: " + ferr);
     }
+    if (build_w_tables_create(g->dims_template, g->d_M, g->bw, ferr) != cudaSuccess) {
+      fused_tables_destroy(g->fused);
+      cudaFree(g->d_mem);
+      delete g;
+      return fail(DELIMIT_ERR_OOM, "operator-build tables: " + ferr);
+    }
     g->on_device = true;
   }
   *out = g;
@@ -535,6 +542,7 @@ delimit_status delimit_lsc_geometry_destroy(delimit_lsc_geometry* g) {
     if (cur != g->device) cudaSetDevice(g->device);
     cudaFree(g->d_mem);
     fused_tables_destroy(g->fused);
+    build_w_tables_destroy(g->bw);
     if (cur != g->device && cur >= 0) cudaSetDevice(cur);
   }
   delete g;
@@ -722,6 +730,11 @@ cudaError_t build_operator(const LscDims& d, const delimit_lsc_geometry* g, cons
                            const float* b, void* W, void* Wt, float* bias, delimit_dtype act_t, bool tc, char* base,
                            cudaStream_t cs) {
   const bool wt = needs_wt(d, tc, act_t);
+  if (tc && act_t == DELIMIT_BF16 && !wt && tc_build_w_supported(d, g->bw)) {
+    cudaError_t e = tc_build_w(d, g->bw, w, W, g->err_word, cs);
+    if (e != cudaSuccess || !bias) return e;
+    return launch_build_bias(d, b, g->d_q, bias, cs);
+  }
   cudaError_t e = launch_build_w(d, w, b, g->d_M, g->d_q, W, wt ? Wt : nullptr, bias, int(act_t), cs);
   if (e != cudaSuccess || !(tc && act_t == DELIMIT_F32)) return e;
   e = split_bf16x3(static_cast<const float*>(W), d.rows_out, d.ldW, d.ldW, base + p.off_W3, d.ldW, d.rows_out * d.ldW,

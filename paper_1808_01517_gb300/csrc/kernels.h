@@ -65,6 +65,8 @@ struct LscDims {
 // the padding), Wt = W^T (padded layouts above), bias_vec[(s,co,a)] = b[co,s] q[s][a] (0 when b == NULL).
 cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, const float* M, const float* q,
                            void* W, void* Wt, float* bias_vec, int w_t, cudaStream_t st);
+// bias_vec alone (the tensor-core operator build writes W itself)
+cudaError_t launch_build_bias(const LscDims& d, const float* b, const float* q, float* bias_vec, cudaStream_t st);
 
 // Grouped row-GEMM with the operator stored K-rows x R-columns:
 // Y[y_row0 + r, v] = sum_{k<K} At[(at_row0 + k) * ldat + at_col0 + r] X[(x_row0 + k), v] (+ bias[y_row0 + r])

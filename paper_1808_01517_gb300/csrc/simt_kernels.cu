@@ -506,6 +506,10 @@ cudaError_t launch_build_w(const LscDims& d, const float* w, const float* b, con
   }
   e = cudaGetLastError();
   if (e != cudaSuccess || !bias_vec) return e;
+  return launch_build_bias(d, b, q, bias_vec, st);
+}
+
+cudaError_t launch_build_bias(const LscDims& d, const float* b, const float* q, float* bias_vec, cudaStream_t st) {
   { build_bias_kernel<<<(unsigned)((d.rows_out + 255) / 256), 256, 0, st>>>(d, b, q, bias_vec); count_launch(); }
   return cudaGetLastError();
 }

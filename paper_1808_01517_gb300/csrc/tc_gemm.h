@@ -84,6 +84,22 @@ cudaError_t split_bf16x3(const float* x, int64_t rows, int64_t cols, int64_t ldx
 
 // The LSC forward with SH2Signal in its epilogue (tc_fused.cu): B_s^T of the output basis'
 // shells as the K-major BF16 operator [S][96 directions][64 coefficients], zero-padded.
+// Parts of the collapse matrices M_{s,s'} for the tensor-core operator build: three BF16
+// parts of every shell pair's [64 kernel points (zero past K)][ldm (a,b) entries] block,
+// part q at q * npg * 64 * ldm (ok false: K > 64 or rows too long for the staging tile;
+// the CUDA-core build is used).
+struct BuildWTables {
+  void* d_mp = nullptr;
+  int npg = 0, ldm = 0;
+  bool ok = false;
+};
+cudaError_t build_w_tables_create(const LscDims& dims_template, const float* d_M, BuildWTables& t, std::string& err);
+void build_w_tables_destroy(BuildWTables& t);
+// The BF16 operator W on the tensor cores (zeros outside the window and in the padding);
+// supported when K <= 64 and c_in divides 128.
+bool tc_build_w_supported(const LscDims& d, const BuildWTables& t);
+cudaError_t tc_build_w(const LscDims& d, const BuildWTables& t, const float* w, void* W, int* err, cudaStream_t st);
+
 struct FusedTables {
   void* d_b2 = nullptr;
   int shells = 0, m[4] = {}, dir_off[4] = {};
