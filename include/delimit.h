@@ -421,9 +421,10 @@ delimit_status delimit_selftest_wait_timeout(void* stream);
  *     before launching anything.
  *   0: every step on the CUDA-core kernels (same results within the dtype's
  *     rounding; used to cross-check the two).
- * Other values: INVALID_ARG.  The weight-side kernels (operator build, weight-
- * gradient reduction) and the gathered Signal2SH have CUDA-core kernels only
- * and are not affected. */
+ * Other values: INVALID_ARG.  The operator build runs on the tensor cores for
+ * BF16 activations when K <= 64 and c_in divides 128 (modes 1 and 2), else on
+ * the CUDA cores; it, the weight-gradient reduction and the gathered Signal2SH
+ * are not counted as fallbacks and never refused. */
 delimit_status delimit_set_tensor_cores(int mode);
 
 /* Process-wide CTA-pair choice of the LSC tensor-core GEMMs (forward, input and
