@@ -14,7 +14,7 @@
 //     the K-major 128-byte-swizzled operand layout; one thread loads the three M parts
 //     (MN-major, four 64-entry atoms x 64 k each) by TMA, issues the 24 MMAs (M = 128,
 //     N = 256, K = 16) and commits;
-//   - sixteen warps read the accumulator (four per TMEM lane quarter), round to BF16 and
+//   - 32 warps read the accumulator (eight per TMEM lane quarter), round to BF16 and
 //     scatter it into a staging tile in W's own order [co][a][ci][b] (in the freed
 //     operand space), so that every row run of W the tile covers, (s, co, a) with the
 //     tile's channels ci and their b entries, is contiguous there;
@@ -38,7 +38,7 @@ constexpr int kBwK = 64;                                // kernel points, zero-p
 constexpr uint32_t kBwABytes = kBwTP * kBwK * 2;         // one w part tile: 16 KiB
 constexpr uint32_t kBwBBytes = kBwTN * kBwK * 2;         // one M part tile: 4 atoms x 8 KiB
 constexpr uint32_t kBwOpBytes = 3 * (kBwABytes + kBwBBytes);  // 144 KiB
-constexpr int kBwThreads = 512;
+constexpr int kBwThreads = 1024;
 constexpr int kErrBwLoad = 0x4A00, kErrBwMma = 0x4B00;
 
 // the six part products, largest first: term t multiplies part pa(t) of w with part pb(t) of M
@@ -188,16 +188,17 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     ok = wait_bounded(done_bar, 0, abort_flag, err, kErrBwMma);
     tc_fence_after();
     // accumulator -> BF16 -> staging in W's order: warp w reads TMEM lanes 32 (w % 4) ..
-    // (pairs) and columns 64 (w / 4) .. + 63 in 16-column loads
+    // (pairs) and kCols columns from kCols (w / 4) in 16-column loads
     if (__all_sync(0xffffffffu, ok)) {
+      constexpr int kCols = kBwTN / (kBwThreads / 128);  // columns per warp
       const int quarter = warp & 3, cq = warp >> 2, prow = 32 * quarter + lane;
       const bool pv = prow < np;
       const int co_l = prow / d.c_in, ci = prow - co_l * d.c_in;
       const uint32_t tl = tmem_base + ((uint32_t)(32 * quarter) << 16);
       __nv_bfloat16* srow = stg + ((int64_t)co_l * na * d.c_in + ci) * d.n_in;  // + (a - a_lo) rowlen + b
 #pragma unroll 1
-      for (int c = 0; c < kBwTN / 4; c += 16) {
-        const int col = 64 * cq + c;
+      for (int c = 0; c < kCols; c += 16) {
+        const int col = kCols * cq + c;
         uint32_t r[16];
         tmem_ld16_nowait(tl + (uint32_t)col, r);
         tmem_wait_ld();
