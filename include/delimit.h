@@ -422,8 +422,8 @@ delimit_status delimit_selftest_wait_timeout(void* stream);
  *   0: every step on the CUDA-core kernels (same results within the dtype's
  *     rounding; used to cross-check the two).
  * Other values: INVALID_ARG.  The operator build runs on the tensor cores for
- * BF16 activations when K <= 64 and c_in divides 128 (modes 1 and 2), else on
- * the CUDA cores; it, the weight-gradient reduction and the gathered Signal2SH
+ * BF16 activations when K <= 64, c_in divides 128 and c_in * N_in is a multiple
+ * of 8 (modes 1 and 2), else on the CUDA cores; it, the weight-gradient reduction and the gathered Signal2SH
  * are not counted as fallbacks and never refused. */
 delimit_status delimit_set_tensor_cores(int mode);
 
@@ -447,7 +447,8 @@ uint64_t delimit_cuda_core_fallbacks(void);
  * recorded events and writes JSON {"name": {"n": launches, "ms": total device
  * time}, ...} into buf (truncated to cap - 1 characters); it returns the full
  * length.  Names: signal2sh_tc, sh2signal_tc, signal2sh_bwd_tc,
- * sh2signal_bwd_tc (the _f32 suffix for FP32 input), transform_simt, lsc_build_w, lsc_fwd_gemm, lsc_dgrad_gemm,
+ * sh2signal_bwd_tc (the _f32 suffix for FP32 input), transform_simt, lsc_build_w
+ * (lsc_build_w_tc on the tensor cores), lsc_fwd_gemm, lsc_dgrad_gemm,
  * lsc_wgrad_gemm (the _f32 suffix for split FP32 operands), lsc_fwd_sh2signal (the
  * fused LSC forward + SH2Signal), lsc_rowsum (FP32 and
  * single-CTA paths), split_bf16x3, lsc_reduce_dw, lsc_gemm_simt, lsc_wgrad_simt.

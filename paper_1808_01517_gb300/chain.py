@@ -186,6 +186,7 @@ class Chain:
             "lsc_dgrad_gemm": (gemm, e * V * (r["c_out"] + r["c_in"])),
             "lsc_wgrad_gemm": (gemm, e * V * (r["c_out"] + r["c_in"])),
             "lsc_build_w": (build, wbytes),
+            "lsc_build_w_tc": (build, wbytes),
             "lsc_reduce_dw": (build, 4.0 * r["c_out"] * r["c_in"]),
             "lsc_rowsum": (1.0 * r["c_out"] * V, e * V * r["c_out"]),
             "signal2sh_tc": (fl["signal2sh"], by["signal2sh"]),

@@ -315,7 +315,7 @@ bool tc_build_w_supported(const LscDims& d, const BuildWTables& t) {
 }
 
 cudaError_t tc_build_w(const LscDims& d, const BuildWTables& t, const float* w, void* W, int* err, cudaStream_t st) {
-  TraceScope trace("lsc_build_w", st);
+  TraceScope trace("lsc_build_w_tc", st);
   const int npg = d.s_out * d.s_in, nab = d.n_out * d.n_in;
   cudaError_t e;
   // padding columns between shell blocks stay zero

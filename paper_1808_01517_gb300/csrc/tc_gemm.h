@@ -96,7 +96,8 @@ struct BuildWTables {
 cudaError_t build_w_tables_create(const LscDims& dims_template, const float* d_M, BuildWTables& t, std::string& err);
 void build_w_tables_destroy(BuildWTables& t);
 // The BF16 operator W on the tensor cores (zeros outside the window and in the padding);
-// supported when K <= 64 and c_in divides 128.
+// supported when K <= 64 and c_in divides 128 (the caller takes it only where the
+// forward reads W, i.e. without padding between shell blocks).
 bool tc_build_w_supported(const LscDims& d, const BuildWTables& t);
 cudaError_t tc_build_w(const LscDims& d, const BuildWTables& t, const float* w, void* W, int* err, cudaStream_t st);
 

@@ -55,7 +55,7 @@ def test_flops_and_bytes_per_voxel(host_chain):
     assert by["sh2signal"] == by["sh2signal_backward"] == 51_840 * V
     # the operator build (once per step, not per voxel): 2 * 7 * 64 * 16 * 45 * 45 * 49 FLOP
     build = 2 * 7 * 64 * 16 * 45 * 45 * 49
-    assert kw["lsc_build_w"][0] == build
+    assert kw["lsc_build_w"][0] == build and kw["lsc_build_w_tc"] == kw["lsc_build_w"]
     # per call: the forward is one GEMM plus the build, the backward two GEMMs, the build
     # and the reduction of dW to the kernel points (the same size as the build)
     assert fl["lsc_forward"] == gemm * V + build
